@@ -1,0 +1,454 @@
+"""Benchmark of the batched Group-codec decode path on one GB300 (or N, as
+independent replicas).
+
+Workload (default): a synthetic inverted index of 1,000,000 posting lists
+over a 25M-document universe, rank-law (Zipf s = 1.1) lengths clipped to
+[1, 2^22] (1.5e9 docIDs), each list a sorted uniform sample. The index is
+encoded on the GPU with Group-Simple and Group-PFD (zeta = 0.1), both with
+the k = 32 vertical layout. One step decodes the whole index once per codec
+and restores docIDs (fused prefix sum): one CUDA-graph launch per codec.
+
+Prints one JSON line: decoded ints/s (all codecs, all ranks), the roofline of
+the decode kernel, the end-to-end rate through the C ABI with host buffers,
+the one-launch-per-list rate, the CPU oracle baseline and the SM clocks.
+`--impl reference` times the CPU oracle instead (the slow reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+UNIVERSE = 25_000_000
+CODECS = {"simple": (0, "Group-Simple"), "pfd": (3, "Group-PFD")}
+# DRAM bytes (read + write) per decode launch from one ncu capture, with the
+# hash of the kernel sources they were taken on; a stale hash reports null.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--nlists", type=int, default=1_000_000)
+    p.add_argument("--codecs", default="simple,pfd")
+    p.add_argument("--k", type=int, default=32)
+    p.add_argument("--zeta", type=float, default=0.10)
+    p.add_argument("--warps", type=int, default=0, help="warps per block (0 = library default)")
+    p.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = as many as fit)")
+    p.add_argument("--no-verify", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-per-list", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work budget per codec")
+    return p.parse_args()
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("gc_decode.cu", "gc_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1502_01916_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def workload(nlists: int):
+    import synth
+    gaps, off, lengths = synth.zipf_index(nlists, UNIVERSE, 0)
+    return gaps, off, lengths
+
+
+def workload_name(a) -> str:
+    return (f"zipf-index: {a.nlists} lists, universe {UNIVERSE}, Zipf(1.1) lengths in [1, 2^22], "
+            f"uniform docIDs; k={a.k}; batched persistent decode + docID prefix sum")
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def cpu_oracle_rate(lengths, kinds, k, zeta, seconds, seed=7):
+    """The CPU oracle (single-threaded C, as it stands) decoding and
+    restoring docIDs for a random sample of lists of the same workload.
+    Returns (ints/s, sample description)."""
+    import oracle as O
+    import synth
+    rng = np.random.default_rng(seed)
+    # about seconds * 13e6 ints per codec: lists drawn uniformly at random
+    budget = int(seconds * 13e6)
+    order = rng.permutation(len(lengths))
+    cum = np.cumsum(lengths[order].astype(np.int64))
+    m = int(np.searchsorted(cum, budget)) + 1
+    L = lengths[order[:m]]
+    gaps, off = synth.uniform_index(seed, L, UNIVERSE)
+    tot_ints, tot_s = 0, 0.0
+    for kind in kinds:
+        c = O.Codec(kind, k, zeta=zeta)
+        encs = [O.encode(c, gaps[off[i]:off[i + 1]]) for i in range(m)]
+        t0 = time.perf_counter()
+        for i, (cc, dd) in enumerate(encs):
+            O.prefix_sum(O.decode(c, cc, dd, int(L[i])))
+        tot_s += time.perf_counter() - t0
+        tot_ints += int(L.sum())
+    desc = (f"{m} lists drawn at random from the workload's length distribution "
+            f"({int(L.sum())} ints per codec, {len(kinds)} codec(s)), docIDs by the same recipe; "
+            f"oracle decode + prefix sum, 1 thread")
+    return tot_ints / tot_s, desc, tot_s
+
+
+def reference_arm(a, rank, world):
+    """--impl reference: the CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    import synth
+    lengths = synth.zipf_index_lengths(a.nlists, 0)
+    kinds = [CODECS[c][0] for c in a.codecs.split(",")]
+    per_step = max(1.0, min(8.0, 150.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        cpu_oracle_rate(lengths, kinds, a.k, a.zeta, per_step / len(kinds) / 4, seed=11)
+    rates, secs = [], []
+    desc = ""
+    for s in range(a.steps):
+        r, desc, sec = cpu_oracle_rate(lengths, kinds, a.k, a.zeta, per_step / len(kinds), seed=100 + s)
+        rates.append(r)
+        secs.append(sec)
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": "decoded uint32/s (batched index decode + docID prefix sum)",
+        "value": value, "unit": "ints/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "codecs": a.codecs, "k": a.k},
+        "cpu_baseline": {"value": value, "unit": "ints/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "ints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return reference_arm(a, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1502_01916_gb300 import build as gcbuild
+    gcbuild.build()
+    import paper_1502_01916_gb300 as gc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    t0 = time.time()
+    gaps, off, lengths = workload(a.nlists)
+    t_gen = time.time() - t0
+    total_ints = int(off[-1])
+    d_gaps = torch.from_numpy(gaps.view(np.int32)).to(dev)
+    kinds = [c for c in a.codecs.split(",")]
+    idxs = {}
+    t0 = time.time()
+    for name in kinds:
+        codec = gc.make_codec(CODECS[name][0], a.k, zeta=a.zeta)
+        idxs[name] = gc.encode_index(codec, d_gaps, lengths)
+    torch.cuda.synchronize()
+    t_enc = time.time() - t0
+    del d_gaps
+    torch.cuda.empty_cache()
+
+    out = torch.empty(total_ints, dtype=torch.int32, device=dev)
+    launch = gc.gc_launch(a.warps, a.bps) if a.warps else None
+    scratch = {n: torch.empty(gc.gc_decode_batch_scratch_size(i.nlists, i.max_tiles), dtype=torch.uint8,
+                              device=dev) for n, i in idxs.items()}
+    status = {n: gc.new_status(dev) for n in idxs}
+
+    # correctness at full size: every docID against the host's prefix sums
+    verified = None
+    if not a.no_verify:
+        cs = np.cumsum(gaps, dtype=np.uint32)
+        base = np.where(off[:-1] > 0, cs[np.maximum(off[:-1].astype(np.int64) - 1, 0)], 0).astype(np.uint32)
+        want = cs - np.repeat(base, lengths.astype(np.int64))
+        del cs
+        verified = True
+        for n, idx in idxs.items():
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch)
+            if not np.array_equal(gc.as_u32(out), want):
+                verified = False
+                print(f"VERIFY FAILED for {n}", file=sys.stderr)
+        del want
+        if not verified:
+            raise SystemExit("decoded docIDs differ from the input's prefix sums")
+
+    # one CUDA graph per codec: zero the queue, expand work items, decode
+    stream = torch.cuda.Stream(device=dev)
+    graphs, launches = {}, {}
+    for n, idx in idxs.items():
+        with torch.cuda.stream(stream):
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, check=False)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, check=False)
+        launches[n] = gc.gc_last_launch_count()
+        graphs[n] = g
+    torch.cuda.synchronize()
+
+    def step():
+        for n in idxs:
+            graphs[n].replay()
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    cur = torch.cuda.current_stream()
+    ev = {n: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.steps)] for n in idxs}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for s in range(a.steps):
+        for n in idxs:
+            ev[n][s][0].record(cur)
+            graphs[n].replay()
+            ev[n][s][1].record(cur)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    for n in idxs:
+        gc.check_status(status[n], f"decode {n}")
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ints_per_step = total_ints * len(idxs)
+    value = ints_per_step * a.steps * world / (elapsed_ms / 1e3)
+
+    # roofline of each codec's decode launch (algorithmic bytes / duration)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    per_codec = {}
+    for n, idx in idxs.items():
+        ms = float(np.mean([s.elapsed_time(e) for s, e in ev[n]]))
+        comp = idx.compressed_bytes()
+        alg = comp + idx.index_bytes() + 4 * total_ints
+        per_codec[n] = {"ms_per_launch": ms, "ints_per_s": total_ints / (ms / 1e3),
+                        "algorithmic_bytes": alg, "compressed_bytes": comp,
+                        "bits_per_int": 8.0 * comp / total_ints, "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                        "frac": alg / (ms / 1e3) / 1e9 / peak, "launches_per_graph": launches[n]}
+    dom = max(per_codec, key=lambda n: per_codec[n]["ms_per_launch"])
+    kh = kernel_hash()
+    traffic = NCU_TRAFFIC.get(dom)
+    traffic = traffic["bytes"] if traffic and traffic.get("hash") == kh else None
+    roofline = {"bound": "hbm", "kernel": f"k_decode<{CODECS[dom][1]}, k={a.k}, batched>",
+                "achieved": per_codec[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": per_codec[dom]["frac"], "traffic": traffic, "peak_source": peak_src,
+                "timed_as": "graph launch (queue memset + work expansion + decode kernel)"}
+
+    # end to end through the C ABI with host buffers: pinned index pools in,
+    # docIDs out, every step
+    e2e = None
+    if not a.no_e2e:
+        host = {}
+        h2d = 0
+        for n, idx in idxs.items():
+            pools = [idx.lists, idx.ctrl, idx.data, idx.tiles]
+            hp = [torch.empty(p.shape, dtype=p.dtype, pin_memory=True) for p in pools]
+            for h, p in zip(hp, pools):
+                h.copy_(p)
+                h2d += p.numel() * p.element_size()
+            host[n] = (hp, pools)
+        h_out = torch.empty(total_ints, dtype=torch.int32, pin_memory=True)
+        d2h = 4 * total_ints * len(idxs)
+
+        def e2e_step():
+            for n in idxs:
+                hp, pools = host[n]
+                for h, p in zip(hp, pools):
+                    p.copy_(h, non_blocking=True)
+                graphs[n].replay()
+                h_out.copy_(out, non_blocking=True)
+
+        for _ in range(max(1, a.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(cur)
+        ksteps = max(1, min(a.steps, 5))
+        for _ in range(ksteps):
+            e2e_step()
+        f1.record(cur)
+        torch.cuda.synchronize()
+        barrier()
+        ems = f0.elapsed_time(f1)
+        if world > 1:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": ints_per_step * ksteps * world / (ems / 1e3), "unit": "ints/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ksteps}
+        for n in idxs:
+            gc.check_status(status[n], f"e2e decode {n}")
+
+    # one launch per list (gc_decode on each list of a sample)
+    per_list = None
+    if not a.no_per_list:
+        per_list = per_list_rate(gc, idxs, lengths, dev)
+
+    cpu = None
+    if not a.no_cpu_baseline and rank == 0 and world == 1:
+        kinds_id = [CODECS[n][0] for n in idxs]
+        r, desc, _ = cpu_oracle_rate(lengths, kinds_id, a.k, a.zeta, a.cpu_seconds / len(kinds_id))
+        cpu = {"value": r, "unit": "ints/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": "decoded uint32/s (batched index decode + docID prefix sum)",
+        "value": value, "unit": "ints/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "nlists": a.nlists, "ints": total_ints,
+                   "codecs": [CODECS[n][1] + (f" zeta={a.zeta}" if n == "pfd" else "") for n in idxs],
+                   "k": a.k, "l2": "inputs and outputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "launch": {"warps_per_block": a.warps or 8, "blocks_per_sm": a.bps or "max"}},
+        "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list,
+        "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": int(sum(launches.values()) * a.steps),
+        "verified_full_output": verified, "setup_s": {"generate": t_gen, "encode": t_enc},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def per_list_rate(gc, idxs, lengths, dev, nsample=2000, seed=3):
+    """Decode a random sample of lists with one gc_decode call (one launch)
+    per list, from the same resident pools."""
+    import ctypes
+    import torch
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(len(lengths), min(nsample, len(lengths)), replace=False)
+    res = {}
+    lib = gc.load()
+    for n, idx in idxs.items():
+        lists = idx.lists.cpu().numpy().view(np.dtype([("ctrl_off", "<u8"), ("data_off", "<u8"),
+                                                        ("out_off", "<u8"), ("n", "<u4"), ("tile_off", "<u4")]))
+        nmax = int(lengths[ids].max())
+        scratch = torch.empty(gc.gc_decode_scratch_size(idx.codec, nmax, True), dtype=torch.uint8, device=dev)
+        out = torch.empty(nmax, dtype=torch.int32, device=dev)
+        st = gc.new_status(dev)
+        cbase, dbase, tbase = idx.ctrl.data_ptr(), idx.data.data_ptr(), idx.tiles.data_ptr()
+        cb_total, dw_total = idx.ctrl.numel(), idx.data.numel()
+        s = torch.cuda.current_stream().cuda_stream
+        calls = []
+        for i in ids.tolist():
+            d = lists[i]
+            tp = tbase + (int(d["tile_off"]) - 1) * gc.TILE_BYTES
+            calls.append((cbase + int(d["ctrl_off"]), cb_total - int(d["ctrl_off"]),
+                          dbase + 4 * int(d["data_off"]), dw_total - int(d["data_off"]), int(d["n"]), tp))
+        cp = ctypes.byref(idx.codec)
+
+        def run():
+            for c in calls:
+                rc = lib.gc_decode(cp, c[0], c[1], c[2], c[3], c[4], c[5], out.data_ptr(), 1, scratch.data_ptr(),
+                                   scratch.numel(), st.data_ptr(), s)
+                if rc:
+                    raise gc.GcError(rc, "gc_decode")
+
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        gc.check_status(st, "per-list decode")
+        ints = int(lengths[ids].sum())
+        res[n] = {"ints_per_s": ints / (ms / 1e3), "lists": len(ids), "ints": ints, "ms": ms}
+    return res
+
+
+if __name__ == "__main__":
+    main()

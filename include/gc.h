@@ -1,0 +1,228 @@
+/*
+ * gc.h -- C ABI of the GB300 Group-codec library (decode hot path of
+ * "A General SIMD-based Approach to Accelerating Compression Algorithms",
+ * arXiv 1502.01916).
+ *
+ * The library compresses and decompresses the d-gaps of posting lists
+ * (Sec 2.1.1) with the paper's four Group codecs: Group-Simple (Sec 4),
+ * Group-Scheme (Sec 5), Group-AFOR (Sec 6.1) and Group-PFD (Sec 6.2). Every
+ * codec keeps its control patterns in a control area apart from the data
+ * area (Sec 3.1), and the data area uses the k-way vertical layout
+ * (Sec 2.1.2): int i of a list goes to component i mod k of row i / k. k = 4
+ * is the paper's layout (128-bit vectors); k = 32 is the same rule with
+ * 128-byte vectors, one component per lane of a warp.
+ *
+ * Conventions for every call:
+ *   - All buffers are owned by the caller. Pointers named d_* are device
+ *     pointers (cudaMalloc / torch CUDA tensors); h_* are host pointers.
+ *   - Calls that take a `stream` (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) are asynchronous: argument errors that the host
+ *     can see are returned at once; errors found by the GPU (a corrupt
+ *     stream, a look-back wait that ran out) are written to the caller's
+ *     d_status (two uint32: error code, then the failing tile or list), which
+ *     the caller reads after synchronising. d_status is never cleared by the
+ *     library: zero it before a call whose errors you want to see.
+ *   - The library allocates no device memory: scratch is passed in, sized by
+ *     the matching *_scratch_size call.
+ *   - Bit order is LSB-first everywhere: control bit t is bit t%8 of byte
+ *     t/8; lane j's data bit t is bit t%32 of data word (t/32)*k + j.
+ */
+#ifndef GC_H
+#define GC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GC_OK = 0,
+  GC_ERR_INVALID = 1,     /* bad argument (codec, size, alignment, NULL) */
+  GC_ERR_NOSPACE = 2,     /* an output or scratch buffer is too small */
+  GC_ERR_CORRUPT = 3,     /* a control or data stream is malformed (device) */
+  GC_ERR_CUDA = 4,        /* a CUDA call failed */
+  GC_ERR_TIMEOUT = 5,     /* a bounded wait between tiles gave up (device) */
+  GC_ERR_UNSUPPORTED = 6  /* a valid request that this build does not serve */
+} gc_status;
+
+enum { GC_SIMPLE = 0, GC_SCHEME = 1, GC_AFOR = 2, GC_PFD = 3 };
+enum { GC_LD_BINARY = 0, GC_LD_CU = 1, GC_LD_IU = 2 };
+
+/* A codec.
+ *   kind: GC_SIMPLE (Table III selectors, Algorithm 1), GC_SCHEME (Eq. 1/2),
+ *         GC_AFOR (frames of 8/16/32 rows by dynamic programming), GC_PFD
+ *         (32-row frames with exceptions).
+ *   k:    4 or 32 ints per row.
+ *   cg, ld: Group-Scheme compression granularity (1, 2, 4, 8 bits) and
+ *         length descriptor (binary, complete unary, incomplete unary; IU
+ *         only with cg 4 or 8, Sec 5.2.1(a)).
+ *   pfd_exc_rows: Group-PFD, the most rows of a 32-row frame that may hold
+ *         exceptions (the ratio threshold zeta of Sec 6.2 Step 2 as an
+ *         integer; gc_pfd_rows_for_zeta converts). */
+typedef struct gc_codec {
+  uint32_t kind;
+  uint32_t k;
+  uint32_t cg;
+  uint32_t ld;
+  uint32_t pfd_exc_rows;
+  uint32_t reserved; /* must be 0 */
+} gc_codec;
+
+/* Where decoding of one 1024-int tile (1024/k rows) starts: the unit (a
+ * selector, a Group-Scheme row, an AFOR or PFD frame) that holds the tile's
+ * first row. lane_bit: first bit of the unit in every lane stream; ctrl_bit:
+ * first control bit of the unit; exc_off: Group-PFD, byte offset of the
+ * unit's exception record from the start of the exception records (0 for
+ * other codecs); row_skip: rows of the unit before the tile. Tile 0 of any
+ * list is all zeros. The paper's format carries no tile records; the library
+ * derives them from the control area (gc_build_tiles). 24 bytes. */
+typedef struct gc_tile {
+  uint64_t lane_bit;
+  uint64_t ctrl_bit;
+  uint32_t exc_off;
+  uint32_t row_skip;
+} gc_tile;
+
+/* One posting list in a batch (32 bytes). ctrl_off: byte offset of its
+ * control area in the control pool; data_off: word offset of its data area
+ * in the data pool (the data of every list starts on a vector boundary,
+ * i.e. data_off is a multiple of k); out_off: index of its first output int;
+ * n: ints in the list; tile_off: index in the tile pool of the record of its
+ * tile 1 (lists of one tile need no record). */
+typedef struct gc_list {
+  uint64_t ctrl_off;
+  uint64_t data_off;
+  uint64_t out_off;
+  uint32_t n;
+  uint32_t tile_off;
+} gc_list;
+
+/* Launch shape of the batched decoder (NULL = the library default).
+ * warps_per_block: 1..32; blocks_per_sm: resident blocks per SM to launch
+ * (0 = as many as fit); the persistent grid is blocks_per_sm * SMs. */
+typedef struct gc_launch {
+  uint32_t warps_per_block;
+  uint32_t blocks_per_sm;
+} gc_launch;
+
+/* ------------------------------------------------------------- sizes */
+
+/* The exception ratio threshold zeta of Group-PFD (Sec 6.2 Step 2: the
+ * ratio must stay below zeta) as the largest row count c with c/32 < zeta,
+ * clamped to 0..31. */
+uint32_t gc_pfd_rows_for_zeta(double zeta);
+
+/* Upper bounds on the control bytes and data words of n ints, and the number
+ * of 1024-int tiles. Returns GC_ERR_INVALID for a bad codec. */
+gc_status gc_max_encoded_size(const gc_codec* codec, uint64_t n, uint64_t* ctrl_cap,
+                              uint64_t* data_cap, uint64_t* ntiles);
+
+/* ----------------------------------------------------------- encoding */
+
+/* Scratch bytes gc_encode needs for n ints. */
+gc_status gc_encode_scratch_size(const gc_codec* codec, uint64_t n, uint64_t* bytes);
+
+/* Encode n uint32 (d-gaps, or any values) on the GPU. Output streams are
+ * byte-identical to the paper's procedures: Algorithm 1 for Group-Simple,
+ * Eq. 1 for Group-Scheme, the size-minimising partition for Group-AFOR,
+ * Steps 1-4 of Sec 6.2 for Group-PFD.
+ *   d_gaps: n uint32 on the device.
+ *   d_ctrl / ctrl_cap, d_data / data_cap: output areas on the device, at
+ *     least gc_max_encoded_size; d_ctrl must be 4-byte aligned, d_data
+ *     16-byte aligned.
+ *   d_tiles: NULL, or gc_max_encoded_size's ntiles records to receive the
+ *     tile index.
+ *   d_sizes: two uint64 on the device, receive (control bytes, data words).
+ * Asynchronous on `stream`. */
+gc_status gc_encode(const gc_codec* codec, const uint32_t* d_gaps, uint64_t n, uint8_t* d_ctrl,
+                    uint64_t ctrl_cap, uint32_t* d_data, uint64_t data_cap, gc_tile* d_tiles,
+                    uint64_t* d_sizes, void* d_scratch, uint64_t scratch_bytes, void* stream);
+
+/* Encode many lists at once (an index). h_n[i] ints of list i start at
+ * h_in_off[i] of d_gaps. The library lays the lists out back to back and
+ * writes, on the device: d_lists (one gc_list per list), d_ctrl, d_data,
+ * d_tiles (tile records of tiles >= 1), and d_totals = (control bytes, data
+ * words, tile records). Capacities are checked on the host from the
+ * gc_max_encoded_size bounds of each list. */
+gc_status gc_encode_batch_scratch_size(const gc_codec* codec, const uint32_t* h_n, uint64_t nlists,
+                                       uint64_t* bytes);
+gc_status gc_encode_batch(const gc_codec* codec, const uint32_t* d_gaps, const uint32_t* h_n,
+                          const uint64_t* h_in_off, uint64_t nlists, gc_list* d_lists,
+                          uint8_t* d_ctrl, uint64_t ctrl_cap, uint32_t* d_data, uint64_t data_cap,
+                          gc_tile* d_tiles, uint64_t tiles_cap, uint64_t* d_totals, void* d_scratch,
+                          uint64_t scratch_bytes, void* stream);
+
+/* ----------------------------------------------------------- decoding */
+
+/* Scratch bytes gc_decode needs for n ints; have_tiles = 0 when the caller
+ * passes no tile index (the paper's format) and the library must build one. */
+gc_status gc_decode_scratch_size(const gc_codec* codec, uint64_t n, int have_tiles,
+                                 uint64_t* bytes);
+
+/* Build the tile index of one encoded list from its control area alone
+ * (one pass over control bytes, no data read). d_tiles receives
+ * gc_max_encoded_size's ntiles records. */
+gc_status gc_build_tiles(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes,
+                         uint64_t n, gc_tile* d_tiles, void* d_scratch, uint64_t scratch_bytes,
+                         uint32_t* d_status, void* stream);
+
+/* Decode one list of n ints (Sec 4.3, Sec 5.2.3, Sec 6.2 decoding Steps 1-3)
+ * and, when restore_docids != 0, restore docIDs with the inclusive prefix
+ * sum of the gaps modulo 2^32 (Sec 2.1.1) in the same kernel.
+ *   d_ctrl / ctrl_bytes, d_data / data_words: the list's areas; d_data
+ *     16-byte aligned.
+ *   d_tiles: the list's tile index, or NULL to build it into scratch first.
+ *   d_out: n uint32.
+ * One launch decodes every tile; tiles chain their prefix sums with a
+ * bounded decoupled look-back. */
+gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes,
+                    const uint32_t* d_data, uint64_t data_words, uint64_t n, const gc_tile* d_tiles,
+                    uint32_t* d_out, int restore_docids, void* d_scratch, uint64_t scratch_bytes,
+                    uint32_t* d_status, void* stream);
+
+/* Paper's single buffer (Sec 4.3 step 1): u32 offset of the data area in
+ * 4-byte words | control area | zero padding to 16 bytes | data area.
+ * gc_decode_paper reads the offset from the head of the buffer (a device
+ * buffer: the offset is copied to the host, so this call synchronises
+ * `stream` once) and decodes as gc_decode with no tile index. */
+gc_status gc_decode_paper(const gc_codec* codec, const uint8_t* d_buf, uint64_t buf_bytes,
+                          uint64_t n, uint32_t* d_out, int restore_docids, void* d_scratch,
+                          uint64_t scratch_bytes, uint32_t* d_status, void* stream);
+
+/* Scratch bytes gc_decode_batch needs for a batch of up to max_tiles tiles
+ * (the sum over its lists of gc_max_encoded_size's ntiles). */
+gc_status gc_decode_batch_scratch_size(uint64_t nlists, uint64_t max_tiles, uint64_t* bytes);
+
+/* Decode many lists in one persistent launch: warps claim 1024-int tiles of
+ * all lists from a shared queue; tiles of one list chain their prefix sums
+ * by look-back.
+ *   d_lists: nlists descriptors on the device (see gc_list).
+ *   d_ctrl_pool / ctrl_pool_bytes, d_data_pool / data_pool_words,
+ *   d_tile_pool / tile_pool_len: the index areas; every read is
+ *     bounds-checked against these sizes.
+ *   d_out_pool / out_pool_len: outputs; list i goes to out_off.
+ *   max_tiles: the scratch was sized for this many tiles; a batch with more
+ *     reports GC_ERR_NOSPACE in d_status.
+ * The call is graph-capturable (no host synchronisation). */
+gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists,
+                          const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
+                          const uint32_t* d_data_pool, uint64_t data_pool_words,
+                          const gc_tile* d_tile_pool, uint64_t tile_pool_len, uint32_t* d_out_pool,
+                          uint64_t out_pool_len, int restore_docids, uint64_t max_tiles,
+                          const gc_launch* launch, void* d_scratch, uint64_t scratch_bytes,
+                          uint32_t* d_status, void* stream);
+
+/* Number of kernels the last gc_* call on this host thread launched (for
+ * launch accounting). */
+uint32_t gc_last_launch_count(void);
+
+/* Library version string. */
+const char* gc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GC_H */

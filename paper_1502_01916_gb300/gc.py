@@ -1,0 +1,453 @@
+"""ctypes binding of the C ABI in ``include/gc.h``.
+
+Each ``gc_*`` function here forwards to the C call of the same name: it
+turns torch tensors into device pointers and sizes, passes the current CUDA
+stream, and raises ``GcError`` on a non-zero status. Nothing is computed in
+Python. A few helpers (``encode``, ``decode``, ``encode_index``,
+``decode_index``) allocate the caller-owned buffers the C calls expect, with
+torch, and then make exactly those calls.
+
+Integer streams are held in torch tensors of dtype int32 (bit pattern of
+the uint32 values) and uint8; ``as_u32`` views one as numpy uint32.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+import torch
+
+__all__ = [
+    "SIMPLE", "SCHEME", "AFOR", "PFD", "LD_BINARY", "LD_CU", "LD_IU", "TILE_INTS", "GcError",
+    "gc_codec", "gc_tile", "gc_list", "gc_launch", "library_path", "load", "make_codec",
+    "gc_pfd_rows_for_zeta", "gc_max_encoded_size", "gc_encode_scratch_size", "gc_encode",
+    "gc_encode_batch_scratch_size", "gc_encode_batch", "gc_decode_scratch_size", "gc_build_tiles",
+    "gc_decode", "gc_decode_paper", "gc_decode_batch_scratch_size", "gc_decode_batch",
+    "gc_last_launch_count", "gc_version", "EncodedList", "Index", "encode", "decode",
+    "build_tiles", "decode_paper", "encode_index", "decode_index", "new_status", "check_status",
+    "as_u32", "codec_name",
+]
+
+SIMPLE, SCHEME, AFOR, PFD = 0, 1, 2, 3
+LD_BINARY, LD_CU, LD_IU = 0, 1, 2
+TILE_INTS = 1024
+_STATUS = {0: "GC_OK", 1: "GC_ERR_INVALID", 2: "GC_ERR_NOSPACE", 3: "GC_ERR_CORRUPT",
+           4: "GC_ERR_CUDA", 5: "GC_ERR_TIMEOUT", 6: "GC_ERR_UNSUPPORTED"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "_build", "libgc.so")
+
+
+class GcError(RuntimeError):
+    def __init__(self, code: int, what: str, where: int | None = None):
+        msg = f"{what}: {_STATUS.get(code, code)}"
+        if where is not None:
+            msg += f" (tile/list {where})"
+        super().__init__(msg)
+        self.code = code
+        self.where = where
+
+
+class gc_codec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("k", ctypes.c_uint32), ("cg", ctypes.c_uint32),
+                ("ld", ctypes.c_uint32), ("pfd_exc_rows", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class gc_tile(ctypes.Structure):
+    _fields_ = [("lane_bit", ctypes.c_uint64), ("ctrl_bit", ctypes.c_uint64),
+                ("exc_off", ctypes.c_uint32), ("row_skip", ctypes.c_uint32)]
+
+
+class gc_list(ctypes.Structure):
+    _fields_ = [("ctrl_off", ctypes.c_uint64), ("data_off", ctypes.c_uint64),
+                ("out_off", ctypes.c_uint64), ("n", ctypes.c_uint32), ("tile_off", ctypes.c_uint32)]
+
+
+class gc_launch(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+
+
+TILE_BYTES = ctypes.sizeof(gc_tile)
+LIST_BYTES = ctypes.sizeof(gc_list)
+
+_lib = None
+_lock = threading.Lock()
+_V, _U32, _U64, _I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_CP = ctypes.POINTER(gc_codec)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+
+
+def library_path() -> str:
+    return _LIB
+
+
+def load():
+    """Load libgc.so. Raises if it has not been built: there is no fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB):
+            raise RuntimeError(f"{_LIB} is missing: build it with paper_1502_01916_gb300.build.build() "
+                               "(nvcc, sm_103a); the decode path has no CPU fallback")
+        lib = ctypes.CDLL(_LIB)
+        sig = {
+            "gc_pfd_rows_for_zeta": (_U32, [ctypes.c_double]),
+            "gc_max_encoded_size": (_I, [_CP, _U64, _U64P, _U64P, _U64P]),
+            "gc_encode_scratch_size": (_I, [_CP, _U64, _U64P]),
+            "gc_encode": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V, _U64, _V]),
+            "gc_encode_batch_scratch_size": (_I, [_CP, _V, _U64, _U64P]),
+            "gc_encode_batch": (_I, [_CP, _V, _V, _V, _U64, _V, _V, _U64, _V, _U64, _V, _U64, _V, _V,
+                                     _U64, _V]),
+            "gc_decode_scratch_size": (_I, [_CP, _U64, _I, _U64P]),
+            "gc_build_tiles": (_I, [_CP, _V, _U64, _U64, _V, _V, _U64, _V, _V]),
+            "gc_decode": (_I, [_CP, _V, _U64, _V, _U64, _U64, _V, _V, _I, _V, _U64, _V, _V]),
+            "gc_decode_paper": (_I, [_CP, _V, _U64, _U64, _V, _I, _V, _U64, _V, _V]),
+            "gc_decode_batch_scratch_size": (_I, [_U64, _U64, _U64P]),
+            "gc_decode_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I, _U64,
+                                     ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
+            "gc_last_launch_count": (_U32, []),
+            "gc_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise GcError(st, what)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def make_codec(kind: int, k: int = 32, cg: int = 8, ld: int = LD_BINARY, zeta: float = 0.10,
+               exc_rows: int | None = None) -> gc_codec:
+    """A codec descriptor; Group-PFD's zeta becomes the row count of Step 2."""
+    rows = gc_pfd_rows_for_zeta(zeta) if exc_rows is None else exc_rows
+    return gc_codec(kind, k, cg if kind == SCHEME else 0, ld if kind == SCHEME else 0,
+                    rows if kind == PFD else 0, 0)
+
+
+def codec_name(c: gc_codec) -> str:
+    base = {SIMPLE: "GS", AFOR: "AFOR"}.get(c.kind)
+    if c.kind == SCHEME:
+        base = f"GSC-{c.cg}-{['B', 'CU', 'IU'][c.ld]}"
+    elif c.kind == PFD:
+        base = f"PFD(x{c.pfd_exc_rows})"
+    return f"{base}/k{c.k}"
+
+
+# ------------------------------------------------------------------ raw ABI
+
+def gc_pfd_rows_for_zeta(zeta: float) -> int:
+    return int(load().gc_pfd_rows_for_zeta(float(zeta)))
+
+
+def gc_max_encoded_size(codec: gc_codec, n: int):
+    cc, dc, nt = _U64(), _U64(), _U64()
+    _check(load().gc_max_encoded_size(ctypes.byref(codec), n, ctypes.byref(cc), ctypes.byref(dc),
+                                      ctypes.byref(nt)), "gc_max_encoded_size")
+    return cc.value, dc.value, nt.value
+
+
+def gc_encode_scratch_size(codec: gc_codec, n: int) -> int:
+    b = _U64()
+    _check(load().gc_encode_scratch_size(ctypes.byref(codec), n, ctypes.byref(b)), "gc_encode_scratch_size")
+    return b.value
+
+
+def gc_encode(codec, d_gaps, n, d_ctrl, d_data, d_tiles, d_sizes, d_scratch, stream=None):
+    lib = load()
+    _check(lib.gc_encode(ctypes.byref(codec), _ptr(d_gaps), n, _ptr(d_ctrl), d_ctrl.numel(), _ptr(d_data),
+                         d_data.numel(), _ptr(d_tiles), _ptr(d_sizes), _ptr(d_scratch), d_scratch.numel(),
+                         _stream(stream)), "gc_encode")
+
+
+def gc_encode_batch_scratch_size(codec: gc_codec, h_n: np.ndarray) -> int:
+    h_n = np.ascontiguousarray(h_n, dtype=np.uint32)
+    b = _U64()
+    _check(load().gc_encode_batch_scratch_size(ctypes.byref(codec), h_n.ctypes.data, len(h_n), ctypes.byref(b)),
+           "gc_encode_batch_scratch_size")
+    return b.value
+
+
+def gc_encode_batch(codec, d_gaps, h_n, h_in_off, d_lists, d_ctrl, d_data, d_tiles, d_totals, d_scratch,
+                    stream=None):
+    h_n = np.ascontiguousarray(h_n, dtype=np.uint32)
+    h_in_off = np.ascontiguousarray(h_in_off, dtype=np.uint64)
+    _check(load().gc_encode_batch(ctypes.byref(codec), _ptr(d_gaps), h_n.ctypes.data, h_in_off.ctypes.data,
+                                  len(h_n), _ptr(d_lists), _ptr(d_ctrl), d_ctrl.numel(), _ptr(d_data),
+                                  d_data.numel(), _ptr(d_tiles), d_tiles.numel() // TILE_BYTES,
+                                  _ptr(d_totals), _ptr(d_scratch), d_scratch.numel(), _stream(stream)),
+           "gc_encode_batch")
+
+
+def gc_decode_scratch_size(codec: gc_codec, n: int, have_tiles: bool) -> int:
+    b = _U64()
+    _check(load().gc_decode_scratch_size(ctypes.byref(codec), n, int(bool(have_tiles)), ctypes.byref(b)),
+           "gc_decode_scratch_size")
+    return b.value
+
+
+def gc_build_tiles(codec, d_ctrl, ctrl_bytes, n, d_tiles, d_scratch, d_status, stream=None):
+    _check(load().gc_build_tiles(ctypes.byref(codec), _ptr(d_ctrl), ctrl_bytes, n, _ptr(d_tiles),
+                                 _ptr(d_scratch), d_scratch.numel(), _ptr(d_status), _stream(stream)),
+           "gc_build_tiles")
+
+
+def gc_decode(codec, d_ctrl, ctrl_bytes, d_data, data_words, n, d_tiles, d_out, restore_docids, d_scratch,
+              d_status, stream=None):
+    _check(load().gc_decode(ctypes.byref(codec), _ptr(d_ctrl), ctrl_bytes, _ptr(d_data), data_words, n,
+                            _ptr(d_tiles), _ptr(d_out), int(bool(restore_docids)), _ptr(d_scratch),
+                            d_scratch.numel(), _ptr(d_status), _stream(stream)), "gc_decode")
+
+
+def gc_decode_paper(codec, d_buf, n, d_out, restore_docids, d_scratch, d_status, stream=None):
+    _check(load().gc_decode_paper(ctypes.byref(codec), _ptr(d_buf), d_buf.numel(), n, _ptr(d_out),
+                                  int(bool(restore_docids)), _ptr(d_scratch), d_scratch.numel(), _ptr(d_status),
+                                  _stream(stream)), "gc_decode_paper")
+
+
+def gc_decode_batch_scratch_size(nlists: int, max_tiles: int) -> int:
+    b = _U64()
+    _check(load().gc_decode_batch_scratch_size(nlists, max_tiles, ctypes.byref(b)), "gc_decode_batch_scratch_size")
+    return b.value
+
+
+def gc_decode_batch(codec, d_lists, nlists, d_ctrl_pool, d_data_pool, d_tile_pool, d_out_pool, restore_docids,
+                    max_tiles, launch, d_scratch, d_status, stream=None):
+    lp = ctypes.byref(launch) if launch is not None else None
+    tile_len = d_tile_pool.numel() // TILE_BYTES if d_tile_pool is not None else 0
+    _check(load().gc_decode_batch(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_ctrl_pool),
+                                  d_ctrl_pool.numel(), _ptr(d_data_pool), d_data_pool.numel(),
+                                  _ptr(d_tile_pool), tile_len, _ptr(d_out_pool), d_out_pool.numel(),
+                                  int(bool(restore_docids)), max_tiles, lp, _ptr(d_scratch), d_scratch.numel(),
+                                  _ptr(d_status), _stream(stream)), "gc_decode_batch")
+
+
+def gc_last_launch_count() -> int:
+    return int(load().gc_last_launch_count())
+
+
+def gc_version() -> str:
+    return load().gc_version().decode()
+
+
+# ------------------------------------------------------------------ helpers
+
+def _dev(device=None):
+    return torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+
+
+def new_status(device=None) -> torch.Tensor:
+    """The two-word device status a decode call reports into (zeroed)."""
+    return torch.zeros(2, dtype=torch.int32, device=_dev(device))
+
+
+def check_status(status: torch.Tensor, what: str = "device status"):
+    """Synchronise by reading the status words; raise if the GPU reported one."""
+    code, where = (int(x) & 0xFFFFFFFF for x in status.cpu().tolist())
+    if code:
+        raise GcError(code, what, where)
+
+
+def as_u32(t: torch.Tensor) -> np.ndarray:
+    """A device or host int32 tensor's values as numpy uint32."""
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def _i32(a, device) -> torch.Tensor:
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return torch.from_numpy(a.view(np.int32)).to(device)
+
+
+@dataclasses.dataclass
+class EncodedList:
+    """One encoded list on the device: control bytes, data words (int32
+    holding uint32), and its tile index (gc_tile records as raw bytes)."""
+    codec: gc_codec
+    n: int
+    ctrl: torch.Tensor
+    data: torch.Tensor
+    tiles: torch.Tensor | None
+
+    @property
+    def ctrl_bytes(self) -> int:
+        return self.ctrl.numel()
+
+    @property
+    def data_words(self) -> int:
+        return self.data.numel()
+
+    def compressed_bytes(self) -> int:
+        return self.ctrl.numel() + 4 * self.data.numel()
+
+
+def _data_buffer(words: int, device) -> torch.Tensor:
+    # 16-byte aligned by the torch caching allocator (512-byte blocks)
+    return torch.empty(max(4, words), dtype=torch.int32, device=device)
+
+
+def encode(codec: gc_codec, gaps, device=None, with_tiles: bool = True, stream=None) -> EncodedList:
+    """Encode one list on the GPU (gc_encode). `gaps` is a uint32 array or an
+    int32 CUDA tensor."""
+    dev = _dev(device)
+    d_gaps = gaps if isinstance(gaps, torch.Tensor) else _i32(gaps, dev)
+    n = d_gaps.numel()
+    cc, dc, nt = gc_max_encoded_size(codec, n)
+    d_ctrl = torch.empty(max(4, cc), dtype=torch.uint8, device=dev)
+    d_data = _data_buffer(dc, dev)
+    d_tiles = torch.empty(max(1, nt) * TILE_BYTES, dtype=torch.uint8, device=dev) if with_tiles else None
+    d_sizes = torch.zeros(2, dtype=torch.int64, device=dev)
+    d_scratch = torch.empty(max(256, gc_encode_scratch_size(codec, n)), dtype=torch.uint8, device=dev)
+    gc_encode(codec, d_gaps, n, d_ctrl, d_data, d_tiles, d_sizes, d_scratch, stream)
+    cb, dw = (int(x) for x in d_sizes.cpu().tolist())
+    return EncodedList(codec, n, d_ctrl[:cb], d_data[:dw], d_tiles[:nt * TILE_BYTES] if with_tiles else None)
+
+
+def decode(enc: EncodedList, restore_docids: bool = True, use_tiles: bool = True, out=None,
+           status=None, check: bool = True, stream=None) -> torch.Tensor:
+    """Decode one list (gc_decode); docIDs when restore_docids, else gaps."""
+    dev = enc.data.device
+    out = torch.empty(max(1, enc.n), dtype=torch.int32, device=dev) if out is None else out
+    tiles = enc.tiles if use_tiles else None
+    scratch = torch.empty(max(256, gc_decode_scratch_size(enc.codec, enc.n, tiles is not None)),
+                          dtype=torch.uint8, device=dev)
+    st = new_status(dev) if status is None else status
+    gc_decode(enc.codec, enc.ctrl, enc.ctrl_bytes, enc.data, enc.data_words, enc.n, tiles, out,
+              restore_docids, scratch, st, stream)
+    if check:
+        check_status(st, "gc_decode")
+    return out[:enc.n]
+
+
+def build_tiles(codec: gc_codec, ctrl: torch.Tensor, n: int, status=None, stream=None) -> torch.Tensor:
+    """The tile index of an encoded list from its control area (gc_build_tiles)."""
+    dev = ctrl.device
+    _, _, nt = gc_max_encoded_size(codec, n)
+    tiles = torch.zeros(max(1, nt) * TILE_BYTES, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(max(256, gc_decode_scratch_size(codec, n, False)), dtype=torch.uint8, device=dev)
+    st = new_status(dev) if status is None else status
+    gc_build_tiles(codec, ctrl, ctrl.numel(), n, tiles, scratch, st, stream)
+    check_status(st, "gc_build_tiles")
+    return tiles[:nt * TILE_BYTES]
+
+
+def decode_paper(codec: gc_codec, buf: torch.Tensor, n: int, restore_docids: bool = True,
+                 stream=None) -> torch.Tensor:
+    """Decode the paper's single buffer (gc_decode_paper)."""
+    dev = buf.device
+    out = torch.empty(max(1, n), dtype=torch.int32, device=dev)
+    scratch = torch.empty(max(256, gc_decode_scratch_size(codec, n, False)), dtype=torch.uint8, device=dev)
+    st = new_status(dev)
+    gc_decode_paper(codec, buf, n, out, restore_docids, scratch, st, stream)
+    check_status(st, "gc_decode_paper")
+    return out[:n]
+
+
+@dataclasses.dataclass
+class Index:
+    """Many encoded lists laid out back to back on the device (gc_encode_batch):
+    descriptors (gc_list records), control pool, data pool, tile pool."""
+    codec: gc_codec
+    lengths: np.ndarray      # uint32 per list
+    out_offsets: np.ndarray  # uint64 per list: first output int
+    lists: torch.Tensor      # nlists * 32 bytes
+    ctrl: torch.Tensor
+    data: torch.Tensor
+    tiles: torch.Tensor
+    max_tiles: int           # tiles of all lists (the decode scratch bound)
+
+    @property
+    def nlists(self) -> int:
+        return len(self.lengths)
+
+    @property
+    def total_ints(self) -> int:
+        return int(self.lengths.sum(dtype=np.uint64))
+
+    def compressed_bytes(self) -> int:
+        return self.ctrl.numel() + 4 * self.data.numel()
+
+    def index_bytes(self) -> int:
+        """Everything the batched decoder reads besides the streams."""
+        return self.lists.numel() + self.tiles.numel()
+
+
+def encode_index(codec: gc_codec, d_gaps: torch.Tensor, lengths, out_offsets=None, stream=None) -> Index:
+    """Encode every list of `d_gaps` (lists back to back, `lengths` ints each)
+    in one gc_encode_batch call."""
+    dev = d_gaps.device
+    h_n = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if out_offsets is None:
+        out_offsets = np.zeros(len(h_n), np.uint64)
+        if len(h_n) > 1:
+            np.cumsum(h_n[:-1], dtype=np.uint64, out=out_offsets[1:])
+    out_offsets = np.ascontiguousarray(out_offsets, dtype=np.uint64)
+    tr = TILE_INTS // codec.k
+    rows = (h_n.astype(np.uint64) + codec.k - 1) // codec.k
+    nt = (rows + tr - 1) // tr
+    max_tiles = int(nt.sum())
+    tile_recs = int(np.maximum(nt, 1).sum() - len(nt))
+    cc = dc = 0
+    # per-list bounds, summed on the host (the C call re-checks them)
+    for kind_n in _bounds(codec, h_n):
+        cc += kind_n[0]
+        dc += kind_n[1]
+    d_lists = torch.empty(max(1, len(h_n)) * LIST_BYTES, dtype=torch.uint8, device=dev)
+    d_ctrl = torch.empty(max(4, cc), dtype=torch.uint8, device=dev)
+    d_data = _data_buffer(dc, dev)
+    d_tiles = torch.empty(max(1, tile_recs) * TILE_BYTES, dtype=torch.uint8, device=dev)
+    d_totals = torch.zeros(3, dtype=torch.int64, device=dev)
+    scratch = torch.empty(max(256, gc_encode_batch_scratch_size(codec, h_n)), dtype=torch.uint8, device=dev)
+    gc_encode_batch(codec, d_gaps, h_n, out_offsets, d_lists, d_ctrl, d_data, d_tiles, d_totals, scratch, stream)
+    cb, dw, tl = (int(x) for x in d_totals.cpu().tolist())
+    del scratch
+    return Index(codec, h_n, out_offsets, d_lists, d_ctrl[:cb], d_data[:dw], d_tiles[:tl * TILE_BYTES],
+                 max_tiles)
+
+
+def _bounds(codec: gc_codec, h_n: np.ndarray):
+    """(ctrl, data) capacity of every distinct length, expanded per list."""
+    uniq, counts = np.unique(h_n, return_counts=True)
+    for n, c in zip(uniq.tolist(), counts.tolist()):
+        cc, dc, _ = gc_max_encoded_size(codec, n)
+        yield cc * c, dc * c
+
+
+def decode_index(index: Index, out: torch.Tensor | None = None, restore_docids: bool = True,
+                 launch: gc_launch | None = None, scratch: torch.Tensor | None = None, status=None,
+                 check: bool = True, stream=None) -> torch.Tensor:
+    """Decode every list of an index in one gc_decode_batch call."""
+    dev = index.data.device
+    total = index.total_ints
+    out = torch.empty(max(1, total), dtype=torch.int32, device=dev) if out is None else out
+    if scratch is None:
+        scratch = torch.empty(gc_decode_batch_scratch_size(index.nlists, index.max_tiles), dtype=torch.uint8,
+                              device=dev)
+    st = new_status(dev) if status is None else status
+    gc_decode_batch(index.codec, index.lists, index.nlists, index.ctrl, index.data, index.tiles, out,
+                    restore_docids, index.max_tiles, launch, scratch, st, stream)
+    if check:
+        check_status(st, "gc_decode_batch")
+    return out

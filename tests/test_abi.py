@@ -1,0 +1,112 @@
+"""The C ABI without a GPU: the library builds, loads, exports every call that
+include/gc.h declares, and validates arguments on the host (no kernel is
+launched by any call made here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_1502_01916_gb300 import build
+    build.build()
+    import paper_1502_01916_gb300 as gc
+    return gc
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(gc_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("gc_encode", "gc_decode", "gc_decode_batch", "gc_build_tiles", "gc_decode_paper",
+                 "gc_max_encoded_size"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(gc):
+    lib = ctypes.CDLL(gc.library_path())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_sizes_match_header(gc):
+    assert ctypes.sizeof(gc.gc_codec) == 24
+    assert ctypes.sizeof(gc.gc_tile) == 24
+    assert ctypes.sizeof(gc.gc_list) == 32
+    assert O.TILE_DTYPE.itemsize == 24
+
+
+@pytest.mark.parametrize("zeta", [0.0, 0.01, 0.05, 0.1, 0.125, 0.3, 0.5, 0.99, 1.0, 2.0])
+def test_zeta_rule_agrees_with_oracle(gc, zeta):
+    assert gc.gc_pfd_rows_for_zeta(zeta) == O.pfd_rows_for_zeta(zeta)
+
+
+@pytest.mark.parametrize("kind,cg,ld", [(0, 8, 0), (1, 1, 0), (1, 2, 1), (1, 4, 2), (1, 8, 2), (2, 8, 0),
+                                        (3, 8, 0)])
+@pytest.mark.parametrize("k", [4, 32])
+def test_size_bounds_cover_oracle(gc, kind, cg, ld, k):
+    """The library's worst-case sizes are at least the oracle's."""
+    c = gc.make_codec(kind, k, cg, ld, 0.3)
+    oc = O.Codec(kind, k, cg, ld, 0.3)
+    for n in [0, 1, 7, 1000, 1024, 1025, 123457]:
+        cc, dc, nt = gc.gc_max_encoded_size(c, n)
+        occ, odc = O.max_sizes(oc, n)
+        assert cc >= occ and dc >= odc and cc % 4 == 0
+        assert nt == -(-(-(-n // k)) // (1024 // k))
+
+
+@pytest.mark.parametrize("bad", [dict(k=8), dict(kind=5), dict(kind=1, cg=3), dict(kind=1, cg=2, ld=2),
+                                 dict(kind=1, cg=8, ld=3), dict(kind=3, pfd_exc_rows=32),
+                                 dict(reserved=1)])
+def test_bad_codec_rejected_on_host(gc, bad):
+    c = gc.gc_codec(0, 32, 0, 0, 0, 0)
+    for key, val in bad.items():
+        setattr(c, key, val)
+    with pytest.raises(gc.GcError) as ei:
+        gc.gc_max_encoded_size(c, 100)
+    assert ei.value.code == 1
+    lib = gc.load()
+    st = lib.gc_decode(ctypes.byref(c), None, 0, None, 0, 10, None, None, 1, None, 0, None, None)
+    assert st == 1
+
+
+def test_decode_rejects_missing_buffers_and_misaligned_data(gc):
+    lib = gc.load()
+    c = gc.make_codec(gc.SIMPLE, 32)
+    buf = (ctypes.c_uint8 * 64)()
+    base = ctypes.addressof(buf)
+    # NULL output
+    assert lib.gc_decode(ctypes.byref(c), base, 4, base, 4, 10, None, None, 1, base, 1 << 20, None, None) == 1
+    # data not 16-byte aligned
+    mis = (base + 15) // 16 * 16 + 4
+    assert lib.gc_decode(ctypes.byref(c), base, 4, mis, 4, 10, None, base, 1, base, 1 << 20, None, None) == 1
+    # scratch too small
+    assert lib.gc_decode(ctypes.byref(c), base, 4, (base + 15) // 16 * 16, 4, 10, None, base, 1, base, 0,
+                         None, None) == 2
+    # n = 0 is a no-op
+    assert lib.gc_decode(ctypes.byref(c), None, 0, None, 0, 0, None, None, 1, None, 0, None, None) == 0
+
+
+def test_scratch_sizes(gc):
+    c = gc.make_codec(gc.PFD, 32)
+    assert gc.gc_decode_scratch_size(c, 1 << 20, True) < gc.gc_decode_scratch_size(c, 1 << 20, False)
+    assert gc.gc_decode_batch_scratch_size(10, 1000) >= 2 * 8 * 1000
+    lens = np.array([0, 1, 5000, 70000], np.uint32)
+    assert gc.gc_encode_batch_scratch_size(c, lens) > 0
+    assert gc.gc_version().startswith("gc ")

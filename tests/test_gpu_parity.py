@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA library against the CPU oracle, bit for bit.
+
+Every test goes through the C ABI (via the ctypes binding). Decoding is
+checked on streams the oracle encoded; encoding is checked byte for byte
+against the oracle's streams; the batched decoder is checked on indexes the
+GPU encoder built, list by list against the oracle. Integer work: no
+tolerance anywhere.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+K_GSC = [(1, 0), (2, 0), (4, 0), (8, 0), (1, 1), (2, 1), (4, 1), (8, 1), (4, 2), (8, 2)]
+CODECS = ([(O.SIMPLE, k, 0, 0, 0.1) for k in (4, 32)]
+          + [(O.SCHEME, k, cg, ld, 0.1) for k in (4, 32) for cg, ld in K_GSC]
+          + [(O.AFOR, k, 0, 0, 0.1) for k in (4, 32)]
+          + [(O.PFD, k, 0, 0, z) for k in (4, 32) for z in (0.01, 0.1, 0.3)])
+
+
+def cid(c):
+    kind, k, cg, ld, z = c
+    return repr(O.Codec(kind, k, cg or 8, ld, z))
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_1502_01916_gb300 import build
+    build.build()
+    import paper_1502_01916_gb300 as gc
+    return gc
+
+
+def pair(gc, c):
+    kind, k, cg, ld, z = c
+    return O.Codec(kind, k, cg or 8, ld, z), gc.make_codec(kind, k, cg or 8, ld, z)
+
+
+def upload_u8(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint8).copy()).cuda()
+
+
+def upload_u32(a):
+    a = np.ascontiguousarray(a, np.uint32)
+    if a.size == 0:
+        a = np.zeros(4, np.uint32)
+    return torch.from_numpy(a.view(np.int32).copy()).cuda()
+
+
+def inputs(seed, n):
+    """Values of every width (one case in four) or d-gap-like mixes."""
+    if seed % 4 == 0:
+        return synth.width_mix(seed, n, 0, 32)
+    if seed % 4 == 1:
+        return synth.width_mix(seed, n, 0, 9)
+    if seed % 4 == 2:
+        return synth.mixed_runs(seed, n, 256, 8.0, 0.1, 1 << 20)
+    return synth.geometric_gaps(seed, n, 20.0)
+
+
+SIZES = [1, 3, 31, 129, 1000, 1024, 1025, 4100, 33007]
+
+
+# ------------------------------------------------------------------- decode
+
+@pytest.mark.parametrize("c", CODECS, ids=cid)
+def test_decode_matches_oracle(gc, c):
+    """Oracle-encoded streams, decoded on the GPU with the oracle's tile index,
+    with the GPU-built tile index and with none (built inside gc_decode)."""
+    oc, gcc = pair(gc, c)
+    for i, n in enumerate(SIZES):
+        g = inputs(17 * i + c[1], n)
+        ctrl, data = O.encode(oc, g)
+        want_gaps = O.decode(oc, ctrl, data, n)
+        assert (want_gaps == g).all()
+        want_ids = O.prefix_sum(want_gaps)
+        tiles_ref = O.tile_index(oc, ctrl, n)
+        d_ctrl, d_data = upload_u8(ctrl), upload_u32(data)
+        enc = gc.EncodedList(gcc, n, d_ctrl, d_data[:len(data)], upload_u8(tiles_ref.view(np.uint8)))
+        got = gc.as_u32(gc.decode(enc, restore_docids=False))
+        assert (got == want_gaps).all(), f"gaps n={n}"
+        got = gc.as_u32(gc.decode(enc, restore_docids=True))
+        assert (got == want_ids).all(), f"docids n={n}"
+        built = gc.build_tiles(gcc, d_ctrl, n).cpu().numpy()
+        assert built.tobytes() == tiles_ref.tobytes(), f"tile index n={n}"
+        got = gc.as_u32(gc.decode(enc, restore_docids=True, use_tiles=False))
+        assert (got == want_ids).all(), f"docids without tiles n={n}"
+
+
+@pytest.mark.parametrize("k", [4, 32])
+def test_decode_paper_buffer(gc, k):
+    """Section 4.3: the data-area offset is read from the buffer head."""
+    oc, gcc = pair(gc, (O.SIMPLE, k, 0, 0, 0.1))
+    g = synth.single_list_geometric(65536, 20.0, 0)
+    ctrl, data = O.encode(oc, g)
+    buf = O.paper_pack(ctrl, data)
+    got = gc.as_u32(gc.decode_paper(gcc, upload_u8(buf), len(g)))
+    assert (got == O.prefix_sum(g)).all()
+
+
+def test_prefix_sum_wraps_mod_2_32(gc):
+    """Gaps near 2^32: docIDs wrap modulo 2^32 on both sides."""
+    oc, gcc = pair(gc, (O.PFD, 32, 0, 0, 0.1))
+    g = synth.uniform_u32(5, 5000, 1 << 30, 0xFFFFFFFF)
+    ctrl, data = O.encode(oc, g)
+    enc = gc.EncodedList(gcc, len(g), upload_u8(ctrl), upload_u32(data), None)
+    got = gc.as_u32(gc.decode(enc, restore_docids=True, use_tiles=False))
+    assert (got == O.prefix_sum(g)).all()
+
+
+@pytest.mark.parametrize("c", [(O.SIMPLE, 32, 0, 0, 0.1), (O.AFOR, 4, 0, 0, 0.1), (O.SCHEME, 4, 8, 2, 0.1),
+                               (O.PFD, 32, 0, 0, 0.1)], ids=cid)
+def test_corrupt_control_is_reported(gc, c):
+    """A malformed control area ends in GC_ERR_CORRUPT, never in a fault."""
+    oc, gcc = pair(gc, c)
+    g = inputs(3, 5000)
+    ctrl, data = O.encode(oc, g)
+    bad = ctrl.copy()
+    if c[0] == O.SIMPLE:
+        bad[1] = 0xFF                      # selectors 2 and 3 become 15
+    elif c[0] == O.AFOR:
+        bad[0] = 0xFF                      # size code 3, b = 63
+    elif c[0] == O.SCHEME:
+        bad[:] = 0xFF                      # no closing zero anywhere
+    else:
+        bad[0] = (bad[0] & 0xC0) | 40      # b = 40
+    enc = gc.EncodedList(gcc, len(g), upload_u8(bad), upload_u32(data), None)
+    with pytest.raises(gc.GcError) as ei:
+        gc.decode(enc, restore_docids=True, use_tiles=False)
+    assert ei.value.code == 3
+
+
+def test_truncated_data_is_reported(gc):
+    oc, gcc = pair(gc, (O.SIMPLE, 32, 0, 0, 0.1))
+    g = inputs(4, 5000)
+    ctrl, data = O.encode(oc, g)
+    enc = gc.EncodedList(gcc, len(g), upload_u8(ctrl), upload_u32(data)[:len(data) // 2], None)
+    with pytest.raises(gc.GcError) as ei:
+        gc.decode(enc, restore_docids=False, use_tiles=False)
+    assert ei.value.code == 3
+
+
+# ------------------------------------------------------------------- encode
+
+@pytest.mark.parametrize("c", CODECS, ids=cid)
+def test_encode_byte_identical(gc, c):
+    """GPU streams and tile index equal the oracle's, byte for byte."""
+    oc, gcc = pair(gc, c)
+    for i, n in enumerate([1, 5, 1000, 1025, 4100, 33007]):
+        g = inputs(31 * i + c[1] + 1, n)
+        ctrl, data = O.encode(oc, g)
+        enc = gc.encode(gcc, g)
+        assert enc.ctrl.cpu().numpy().tobytes() == ctrl.tobytes(), f"control n={n}"
+        assert (gc.as_u32(enc.data) == data).all(), f"data n={n}"
+        assert enc.tiles.cpu().numpy().tobytes() == O.tile_index(oc, ctrl, n).tobytes(), f"tiles n={n}"
+
+
+# ------------------------------------------------------------------- batch
+
+def small_index(seed, nlists=300, universe=2_000_000):
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(1, 3000, size=nlists).astype(np.uint32)
+    lens[:12] = [0, 1, 2, 31, 32, 33, 1023, 1024, 1025, 2048, 70000, 0]
+    rng.shuffle(lens)
+    gaps, off = synth.uniform_index(seed, lens, universe)
+    return lens, gaps, off
+
+
+@pytest.mark.parametrize("c", CODECS, ids=cid)
+def test_batch_encode_decode(gc, c):
+    """gc_encode_batch lays out the oracle's per-list streams; gc_decode_batch
+    restores every list's docIDs (and raw gaps) in one launch."""
+    oc, gcc = pair(gc, c)
+    lens, gaps, off = small_index(11 + c[1])
+    idx = gc.encode_index(gcc, upload_u32(gaps), lens)
+    lists = idx.lists.cpu().numpy().view(np.dtype([("ctrl_off", "<u8"), ("data_off", "<u8"), ("out_off", "<u8"),
+                                                    ("n", "<u4"), ("tile_off", "<u4")]))
+    ctrl_pool = idx.ctrl.cpu().numpy()
+    data_pool = gc.as_u32(idx.data)
+    tiles_pool = idx.tiles.cpu().numpy().view(O.TILE_DTYPE)
+    want_ids = np.zeros(len(gaps), np.uint32)
+    for i, n in enumerate(lens.tolist()):
+        g = gaps[off[i]:off[i + 1]]
+        ctrl, data = O.encode(oc, g)
+        d = lists[i]
+        assert int(d["n"]) == n and int(d["out_off"]) == int(off[i])
+        assert ctrl_pool[d["ctrl_off"]:d["ctrl_off"] + len(ctrl)].tobytes() == ctrl.tobytes(), f"list {i}"
+        assert (data_pool[d["data_off"]:d["data_off"] + len(data)] == data).all(), f"list {i}"
+        tref = O.tile_index(oc, ctrl, n)
+        if len(tref) > 1:
+            got_t = tiles_pool[d["tile_off"]:d["tile_off"] + len(tref) - 1]
+            assert got_t.tobytes() == tref[1:].tobytes(), f"tiles list {i}"
+        want_ids[off[i]:off[i + 1]] = O.prefix_sum(g)
+    out = gc.decode_index(idx, restore_docids=True)
+    assert (gc.as_u32(out)[:len(gaps)] == want_ids).all()
+    out = gc.decode_index(idx, restore_docids=False)
+    assert (gc.as_u32(out)[:len(gaps)] == gaps).all()
+
+
+@pytest.mark.parametrize("warps,bps", [(1, 1), (4, 2), (8, 0), (16, 0), (32, 1)])
+def test_batch_launch_shapes(gc, warps, bps):
+    """The result does not depend on the launch shape."""
+    oc, gcc = pair(gc, (O.PFD, 32, 0, 0, 0.1))
+    lens, gaps, off = small_index(5)
+    idx = gc.encode_index(gcc, upload_u32(gaps), lens)
+    want = np.concatenate([O.prefix_sum(gaps[off[i]:off[i + 1]]) for i in range(len(lens))])
+    out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps))
+    assert (gc.as_u32(out)[:len(gaps)] == want).all()
+
+
+def test_batch_overflow_reports_nospace(gc):
+    """A scratch sized for fewer tiles than the batch has: GC_ERR_NOSPACE."""
+    _, gcc = pair(gc, (O.SIMPLE, 32, 0, 0, 0.1))
+    lens, gaps, off = small_index(6, nlists=50)
+    idx = gc.encode_index(gcc, upload_u32(gaps), lens)
+    idx.max_tiles = max(1, idx.max_tiles // 2)
+    with pytest.raises(gc.GcError) as ei:
+        gc.decode_index(idx)
+    assert ei.value.code == 2
+
+
+# ------------------------------------------------------------ full sizes
+
+@pytest.mark.parametrize("c", [(O.SIMPLE, 4, 0, 0, 0.1), (O.PFD, 32, 0, 0, 0.1), (O.SCHEME, 32, 8, 2, 0.1)],
+                         ids=cid)
+def test_mixed_2_26_single_list(gc, c):
+    """2^26 d-gaps (90% geometric mean 8, 10% uniform to 2^20, runs of 256):
+    GPU encoding equals the oracle's; one-launch decode restores the gaps
+    and the docIDs."""
+    oc, gcc = pair(gc, c)
+    g = synth.single_list_mixed(1 << 26, 0)
+    enc = gc.encode(gcc, g)
+    ctrl, data = O.encode(oc, g)
+    assert enc.ctrl.cpu().numpy().tobytes() == ctrl.tobytes()
+    assert (gc.as_u32(enc.data) == data).all()
+    got = gc.as_u32(gc.decode(enc, restore_docids=False))
+    assert (got == g).all()
+    got = gc.as_u32(gc.decode(enc, restore_docids=True))
+    assert (got == O.prefix_sum(g)).all()
