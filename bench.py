@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--zeta", type=float, default=0.10)
     p.add_argument("--warps", type=int, default=0, help="warps per block (0 = library default)")
     p.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = as many as fit)")
+    p.add_argument("--claim", type=int, default=0, help="tiles per claim (0 = library default)")
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-list", action="store_true")
@@ -220,15 +221,16 @@ def main():
     for name in kinds:
         codec = gc.make_codec(CODECS[name][0], a.k, zeta=a.zeta)
         idxs[name] = gc.encode_index(codec, d_gaps, lengths)
+    plans = {n: gc.plan_index(idx) for n, idx in idxs.items()}
     torch.cuda.synchronize()
     t_enc = time.time() - t0
     del d_gaps
     torch.cuda.empty_cache()
 
     out = torch.empty(total_ints, dtype=torch.int32, device=dev)
-    launch = gc.gc_launch(a.warps, a.bps) if a.warps else None
-    scratch = {n: torch.empty(gc.gc_decode_batch_scratch_size(i.nlists, i.max_tiles), dtype=torch.uint8,
-                              device=dev) for n, i in idxs.items()}
+    launch = gc.gc_launch(a.warps, a.bps, a.claim) if (a.warps or a.bps or a.claim) else None
+    scratch = {n: torch.empty(gc.gc_decode_plan_scratch_size(i.max_tiles), dtype=torch.uint8, device=dev)
+               for n, i in idxs.items()}
     status = {n: gc.new_status(dev) for n in idxs}
 
     # correctness at full size: every docID against the host's prefix sums
@@ -240,7 +242,7 @@ def main():
         del cs
         verified = True
         for n, idx in idxs.items():
-            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch)
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, plan=plans[n])
             if not np.array_equal(gc.as_u32(out), want):
                 verified = False
                 print(f"VERIFY FAILED for {n}", file=sys.stderr)
@@ -248,16 +250,18 @@ def main():
         if not verified:
             raise SystemExit("decoded docIDs differ from the input's prefix sums")
 
-    # one CUDA graph per codec: zero the queue, expand work items, decode
+    # one CUDA graph per codec: zero the queue and the look-back words, decode
     stream = torch.cuda.Stream(device=dev)
     graphs, launches = {}, {}
     for n, idx in idxs.items():
         with torch.cuda.stream(stream):
-            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, check=False)
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, check=False,
+                            plan=plans[n])
         stream.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
-            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, check=False)
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, check=False,
+                            plan=plans[n])
         launches[n] = gc.gc_last_launch_count()
         graphs[n] = g
     torch.cuda.synchronize()
@@ -310,19 +314,21 @@ def main():
     for n, idx in idxs.items():
         ms = float(np.mean([s.elapsed_time(e) for s, e in ev[n]]))
         comp = idx.compressed_bytes()
-        alg = comp + idx.index_bytes() + 4 * total_ints
+        alg = comp + plans[n].nbytes() + 4 * total_ints
         per_codec[n] = {"ms_per_launch": ms, "ints_per_s": total_ints / (ms / 1e3),
                         "algorithmic_bytes": alg, "compressed_bytes": comp,
-                        "bits_per_int": 8.0 * comp / total_ints, "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                        "bits_per_int": 8.0 * comp / total_ints, "plan_bytes": plans[n].nbytes(),
+                        "tiles": idx.max_tiles, "achieved_gbs": alg / (ms / 1e3) / 1e9,
                         "frac": alg / (ms / 1e3) / 1e9 / peak, "launches_per_graph": launches[n]}
     dom = max(per_codec, key=lambda n: per_codec[n]["ms_per_launch"])
     kh = kernel_hash()
     traffic = NCU_TRAFFIC.get(dom)
     traffic = traffic["bytes"] if traffic and traffic.get("hash") == kh else None
     roofline = {"bound": "hbm", "kernel": f"k_decode<{CODECS[dom][1]}, k={a.k}, batched>",
+                "bytes_per_launch": per_codec[dom]["algorithmic_bytes"],
                 "achieved": per_codec[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
                 "frac": per_codec[dom]["frac"], "traffic": traffic, "peak_source": peak_src,
-                "timed_as": "graph launch (queue memset + work expansion + decode kernel)"}
+                "timed_as": "graph launch (memset of the queue counter and look-back words + decode kernel)"}
 
     # end to end through the C ABI with host buffers: pinned index pools in,
     # docIDs out, every step
@@ -331,7 +337,7 @@ def main():
         host = {}
         h2d = 0
         for n, idx in idxs.items():
-            pools = [idx.lists, idx.ctrl, idx.data, idx.tiles]
+            pools = [plans[n].work, idx.ctrl, idx.data]
             hp = [torch.empty(p.shape, dtype=p.dtype, pin_memory=True) for p in pools]
             for h, p in zip(hp, pools):
                 h.copy_(p)
@@ -390,7 +396,9 @@ def main():
                    "codecs": [CODECS[n][1] + (f" zeta={a.zeta}" if n == "pfd" else "") for n in idxs],
                    "k": a.k, "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "launch": {"warps_per_block": a.warps or 8, "blocks_per_sm": a.bps or "max"}},
+                   "launch": {"warps_per_block": a.warps or 8, "blocks_per_sm": a.bps or "max",
+                              "items_per_claim": a.claim or 4},
+                   "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},
         "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list,
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(sum(launches.values()) * a.steps),

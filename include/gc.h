@@ -99,12 +99,34 @@ typedef struct gc_list {
   uint32_t tile_off;
 } gc_list;
 
-/* Launch shape of the batched decoder (NULL = the library default).
- * warps_per_block: 1..32; blocks_per_sm: resident blocks per SM to launch
- * (0 = as many as fit); the persistent grid is blocks_per_sm * SMs. */
+/* One unit of work of the batched decoder: tile `tile` of list `list`,
+ * with the list's descriptor and the tile's record copied in, so that a
+ * warp starts a tile with one 64-byte load (64 bytes, 16-byte aligned).
+ * gc_plan_batch writes them; list = 0xffffffff marks an empty slot. */
+typedef struct gc_work {
+  uint64_t ctrl_off;
+  uint64_t data_off;
+  uint64_t out_off;
+  uint32_t n;
+  uint32_t tile;
+  uint64_t lane_bit;
+  uint64_t ctrl_bit;
+  uint32_t exc_off;
+  uint32_t row_skip;
+  uint32_t list;
+  uint32_t reserved;
+} gc_work;
+
+/* Launch shape of the persistent decoders (NULL = the library default).
+ * warps_per_block: 1..16 (default 8); blocks_per_sm: resident blocks per
+ * SM to launch (0 = as many as fit); the persistent grid is blocks_per_sm *
+ * SMs. items_per_claim: 1..64 tiles a warp takes from the shared queue per
+ * atomic (0 = default 4); consecutive tiles of one list in a claim pass
+ * their prefix sum in registers. */
 typedef struct gc_launch {
   uint32_t warps_per_block;
   uint32_t blocks_per_sm;
+  uint32_t items_per_claim;
 } gc_launch;
 
 /* ------------------------------------------------------------- sizes */
@@ -191,13 +213,42 @@ gc_status gc_decode_paper(const gc_codec* codec, const uint8_t* d_buf, uint64_t 
                           uint64_t n, uint32_t* d_out, int restore_docids, void* d_scratch,
                           uint64_t scratch_bytes, uint32_t* d_status, void* stream);
 
+/* The work plan of a batch (one gc_work per tile of every list, list by
+ * list, a list's tiles in order), built on the device from the descriptors
+ * and the tile pool. A plan depends only on the index, so a caller that
+ * decodes the same resident index many times builds it once.
+ *   d_lists / nlists, d_tile_pool / tile_pool_len: as for gc_decode_batch.
+ *   d_work / work_cap: output records (16-byte aligned). A batch with more
+ *     tiles reports GC_ERR_NOSPACE in d_status.
+ *   d_count: one uint64 on the device, receives the number of tiles.
+ * Asynchronous on `stream`; graph-capturable. */
+gc_status gc_plan_batch(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists,
+                        const gc_tile* d_tile_pool, uint64_t tile_pool_len, gc_work* d_work,
+                        uint64_t work_cap, uint64_t* d_count, uint32_t* d_status, void* stream);
+
+/* Scratch bytes gc_decode_plan needs for a plan of up to work_cap tiles. */
+gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes);
+
+/* Decode every tile of a plan in one persistent launch (Sec 4.3, 5.2.3,
+ * 6.2 decoding per tile; docIDs by Sec 2.1.1 when restore_docids != 0,
+ * chained across the tiles of a list by look-back). Warps claim tiles from
+ * a shared counter in plan order. The pools are those the plan's records
+ * point into; every read is bounds-checked against these sizes, and a
+ * record whose list does not fit out_pool_len reports GC_ERR_INVALID.
+ * Asynchronous on `stream`; graph-capturable (two memsets and one kernel). */
+gc_status gc_decode_plan(const gc_codec* codec, const gc_work* d_work, const uint64_t* d_count,
+                         uint64_t work_cap, const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
+                         const uint32_t* d_data_pool, uint64_t data_pool_words, uint32_t* d_out_pool,
+                         uint64_t out_pool_len, int restore_docids, const gc_launch* launch,
+                         void* d_scratch, uint64_t scratch_bytes, uint32_t* d_status, void* stream);
+
 /* Scratch bytes gc_decode_batch needs for a batch of up to max_tiles tiles
  * (the sum over its lists of gc_max_encoded_size's ntiles). */
 gc_status gc_decode_batch_scratch_size(uint64_t nlists, uint64_t max_tiles, uint64_t* bytes);
 
-/* Decode many lists in one persistent launch: warps claim 1024-int tiles of
- * all lists from a shared queue; tiles of one list chain their prefix sums
- * by look-back.
+/* Decode many lists in one persistent launch: gc_plan_batch into scratch,
+ * then gc_decode_plan. Warps claim 1024-int tiles of all lists from a
+ * shared queue; tiles of one list chain their prefix sums by look-back.
  *   d_lists: nlists descriptors on the device (see gc_list).
  *   d_ctrl_pool / ctrl_pool_bytes, d_data_pool / data_pool_words,
  *   d_tile_pool / tile_pool_len: the index areas; every read is

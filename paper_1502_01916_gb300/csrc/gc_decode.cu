@@ -29,14 +29,18 @@ constexpr unsigned long long kFlagPrefix = 2ull << 32;
 constexpr uint32_t kSpinLimit = 1u << 22;  // ~0.5 s of polling
 
 template <int K>
-struct WarpSmem {
+struct __align__(16) WarpSmem {
   static constexpr int TR = kTileInts / K;  // rows per tile
   static constexpr int FPT = TR / 32;       // PFD frames per tile
-  uint64_t fx[FPT];                         // PFD: byte offset of each frame's exception record
+  // the tile's data words, staged (TR rows of at most 32 bits per lane and
+  // a start offset below 32 span at most TR + 1 words per lane)
+  static constexpr int DW = (TR + 1) * K;
+  uint32_t d[DW];
   uint32_t outs[kTileInts + kTileInts / 32];  // padded: int i at i + i/32
-  uint32_t rb[TR];                          // lane-bit offset of each row (from the tile's unit)
-  uint32_t fe[FPT], fw[FPT], fr[FPT];       // PFD: exceptions, width code, rows of each frame
-  uint8_t rw[TR];                           // bit width of each row
+  uint64_t fx[FPT];                           // PFD: byte offset of each frame's exception record
+  uint32_t rb[TR];                            // lane-bit offset of each row (from the tile's unit)
+  uint32_t fe[FPT], fw[FPT], fr[FPT];         // PFD: exceptions, width code, rows of each frame
+  uint8_t rw[TR];                             // bit width of each row
 };
 
 struct ListRef {
@@ -52,20 +56,19 @@ struct DecodeArgs {
   ListRef one;  // single-list launch
   const gc_tile* one_tiles;
   uint64_t one_ntiles;
-  const gc_list* lists;  // batched launch
-  uint64_t nlists;
+  const gc_work* work;  // batched launch: one record per tile
+  const unsigned long long* work_count;
+  uint64_t work_cap;
   const uint8_t* ctrl_pool;
   uint64_t ctrl_pool_bytes;
   const uint32_t* data_pool;
   uint64_t data_pool_words;
-  const gc_tile* tile_pool;
-  uint64_t tile_pool_len;
   uint32_t* out_pool;
   uint64_t out_pool_len;
-  const uint2* items;       // batched: (list, tile) per work item
-  uint32_t* counters;       // [0] claim counter, [1] items (batched)
+  uint32_t* counters;       // [0] claim counter
   unsigned long long* lb;   // look-back word per work item
   uint32_t cg, ld;
+  uint32_t claim;           // work items per claim
   int restore;
   uint32_t* status;
 };
@@ -323,49 +326,79 @@ __device__ bool patch_pfd(const ListRef& L, uint32_t rows, uint32_t nints, WarpS
 
 // ------------------------------------------------------------ look-back
 
-// Lane 0: publish this tile's aggregate, sum the predecessors' values back
-// to the first inclusive prefix, publish the inclusive prefix. Returns the
-// exclusive prefix. Every wait is bounded.
-__device__ uint32_t look_back(unsigned long long* lb, uint64_t item, bool first, uint32_t agg,
-                              uint32_t* status, uint32_t where) {
-  if (first) {
-    st_release(lb + item, kFlagPrefix | agg);
+// Decoupled look-back over the tiles of one list, a warp at a time: publish
+// this tile's aggregate, then read the 32 nearest predecessors at once; the
+// nearest one that carries an inclusive prefix ends the walk, otherwise the
+// window moves 32 tiles back. Tile 0 of a list always carries a prefix, so
+// the walk ends inside the list. Returns the exclusive prefix (all lanes).
+// Every wait is bounded; a wait that runs out reports GC_ERR_TIMEOUT.
+__device__ uint32_t look_back(unsigned long long* lb, uint64_t item, uint64_t t, uint32_t agg, uint32_t* status,
+                              uint32_t where) {
+  const uint32_t lane = lane_id();
+  if (t == 0) {
+    if (lane == 0) st_release(lb + item, kFlagPrefix | agg);
     return 0;
   }
-  st_release(lb + item, kFlagAgg | agg);
+  if (lane == 0) st_release(lb + item, kFlagAgg | agg);
   uint32_t excl = 0;
-  uint64_t j = item - 1;
   bool timed_out = false;
-  for (;;) {
-    unsigned long long s = ld_acquire(lb + j);
-    uint32_t spins = 0;
-    while ((s >> 32) == 0) {
-      if (++spins > kSpinLimit) { timed_out = true; break; }
-      __nanosleep(64);
-      s = ld_acquire(lb + j);
+  for (uint64_t d = 1;; d += 32) {
+    const uint64_t dist = d + lane;  // predecessor tile t - dist
+    unsigned long long s = kFlagPrefix;
+    if (dist <= t) {
+      s = ld_acquire(lb + item - dist);
+      uint32_t spins = 0;
+      while ((s >> 32) == 0) {
+        if (++spins > kSpinLimit) {
+          timed_out = true;
+          break;
+        }
+        __nanosleep(32);
+        s = ld_acquire(lb + item - dist);
+      }
     }
-    if (timed_out) break;
-    excl += (uint32_t)s;
-    if ((s & ~0xffffffffull) == kFlagPrefix) break;
-    --j;
+    if (__any_sync(kFull, timed_out)) {
+      if (lane == 0) report(status, GC_ERR_TIMEOUT, where);
+      break;
+    }
+    const uint32_t pm = __ballot_sync(kFull, (s & ~0xffffffffull) == kFlagPrefix);
+    uint32_t v = (uint32_t)s;
+    if (pm) {
+      if (lane > (uint32_t)(__ffs(pm) - 1)) v = 0;
+      excl += warp_sum(v);
+      break;
+    }
+    excl += warp_sum(v);
   }
-  if (timed_out) report(status, GC_ERR_TIMEOUT, where);
-  st_release(lb + item, kFlagPrefix | (uint32_t)(excl + agg));
+  if (lane == 0) st_release(lb + item, kFlagPrefix | (uint32_t)(excl + agg));
   return excl;
+}
+
+__device__ __forceinline__ uint4 ldg_v4(const uint32_t* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
 }
 
 // ---------------------------------------------------------------- tile
 
+// Decode tile t of list L (work item `item`). `chained`: the previous tile
+// of the list was decoded by this warp, and `carry` is its inclusive prefix.
+// Returns the tile's inclusive prefix (docIDs modulo 2^32).
 template <int KIND, int K>
-__device__ void decode_tile(const DecodeArgs& a, const ListRef& L, const gc_tile& rec, uint64_t t,
-                            uint64_t item, uint32_t where, WarpSmem<K>& ws) {
+__device__ uint32_t decode_tile(const DecodeArgs& a, const ListRef& L, const gc_tile& rec, uint64_t t,
+                                uint64_t item, uint32_t where, bool chained, uint32_t carry, WarpSmem<K>& ws) {
   constexpr uint32_t TR = kTileInts / K;
+  constexpr uint32_t DW = WarpSmem<K>::DW;
   const uint32_t lane = lane_id();
   const uint64_t R = (L.n + K - 1) / K;
   const uint64_t row0 = t * TR;
   const uint32_t rows = (uint32_t)((R - row0) < TR ? (R - row0) : TR);
   const uint32_t nints = (uint32_t)((L.n - row0 * K) < (uint64_t)kTileInts ? (L.n - row0 * K) : kTileInts);
 
+  // 1. control patterns -> per-row (lane-bit offset, width)
   bool ok;
   if (KIND == GC_SIMPLE) ok = parse_simple<K>(L, rec, row0, rows, ws);
   else if (KIND == GC_SCHEME) {
@@ -375,8 +408,30 @@ __device__ void decode_tile(const DecodeArgs& a, const ListRef& L, const gc_tile
   else ok = parse_pfd<K>(L, rec, row0, rows, R, ws);
   __syncwarp();
 
-  // extract: int i of the tile is lane i % K of row i / K
+  // 2. stage the tile's data words in shared memory: whole k-word vectors
+  // from the first row's word to the last row's, with 16-byte loads that
+  // are all in flight at once
+  const uint32_t rb0 = ws.rb[0];
+  const uint64_t base = rec.lane_bit + rb0;
+  const uint32_t off0 = (uint32_t)base & 31u;
+  const uint32_t tbits = ws.rb[rows - 1] - rb0 + ws.rw[rows - 1];
+  uint32_t nwr = (off0 + tbits + 31) >> 5;
+  if (nwr * K > DW) {
+    nwr = DW / K;
+    ok = false;
+  }
+  const uint64_t g0 = (base >> 5) * K;
   bool dok = true;
+  for (uint32_t c = lane; c < nwr * K / 4; c += 32) {
+    const uint64_t gw = g0 + 4ull * c;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (gw + 4 <= L.data_words) v = ldg_v4(L.data + gw);
+    else dok = false;
+    *reinterpret_cast<uint4*>(ws.d + 4 * c) = v;
+  }
+  __syncwarp();
+
+  // 3. extract: int i of the tile is lane i % K of row i / K
 #pragma unroll 4
   for (uint32_t m = 0; m < 32; ++m) {
     const uint32_t i = lane + 32 * m;
@@ -384,20 +439,15 @@ __device__ void decode_tile(const DecodeArgs& a, const ListRef& L, const gc_tile
     if (i < nints) {
       const uint32_t r = i / K, j = i % K;
       const uint32_t w = ws.rw[r];
-      if (w) {
-        const uint64_t bit = rec.lane_bit + ws.rb[r];
-        const uint32_t off = (uint32_t)bit & 31u;
-        uint64_t idx = (bit >> 5) * K + j;
-        uint32_t lo = 0, hi = 0;
-        if (idx < L.data_words) lo = __ldg(L.data + idx);
-        else dok = false;
-        if (off + w > 32) {
-          idx += K;
-          if (idx < L.data_words) hi = __ldg(L.data + idx);
-          else dok = false;
-        }
-        v = __funnelshift_r(lo, hi, off) & low_mask(w);
-      }
+      const uint32_t bit = off0 + ws.rb[r] - rb0;
+      const uint32_t o = bit & 31u;
+      uint32_t wi = (bit >> 5) * K + j;
+      wi = wi < DW ? wi : DW - 1;
+      const uint32_t lo = ws.d[wi];
+      uint32_t hi = 0;
+      if (o + w > 32) hi = ws.d[wi + K < DW ? wi + K : DW - 1];
+      v = __funnelshift_r(lo, hi, o) & low_mask(w);
+      if (w == 0) v = 0;
     }
     ws.outs[pad_idx(i)] = v;
   }
@@ -409,6 +459,9 @@ __device__ void decode_tile(const DecodeArgs& a, const ListRef& L, const gc_tile
   if (!__all_sync(kFull, dok)) ok = false;
   if (!ok && lane == 0) report(a.status, GC_ERR_CORRUPT, where);
 
+  // 4. docIDs: lane l sums ints 32l..32l+31, a warp scan joins the lanes, the
+  // previous tile's prefix comes from this warp (chained) or by look-back
+  uint32_t incl_tile = 0;
   if (a.restore) {
     uint32_t v[32];
     uint32_t s = 0;
@@ -419,14 +472,21 @@ __device__ void decode_tile(const DecodeArgs& a, const ListRef& L, const gc_tile
     }
     const uint32_t incl = warp_incl_sum(s);
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    uint32_t pre = 0;
-    if (lane == 0) pre = look_back(a.lb, item, t == 0, total, a.status, where);
-    pre = __shfl_sync(kFull, pre, 0) + (incl - s);
+    uint32_t pre;
+    if (chained) {
+      pre = carry;
+      if (lane == 0) st_release(a.lb + item, kFlagPrefix | (uint32_t)(carry + total));
+    } else {
+      pre = look_back(a.lb, item, t, total, a.status, where);
+    }
+    incl_tile = pre + total;
+    pre += incl - s;
 #pragma unroll
     for (int c = 0; c < 32; ++c) ws.outs[lane * 33 + c] = v[c] + pre;
     __syncwarp();
   }
 
+  // 5. coalesced stores
   uint32_t* out = L.out + row0 * K;
 #pragma unroll 8
   for (uint32_t m = 0; m < 32; ++m) {
@@ -434,109 +494,188 @@ __device__ void decode_tile(const DecodeArgs& a, const ListRef& L, const gc_tile
     if (i < nints) out[i] = ws.outs[pad_idx(i)];
   }
   __syncwarp();
+  return incl_tile;
 }
 
-template <int KIND, int K, bool BATCH>
-__global__ void __launch_bounds__(1024) k_decode(DecodeArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSmem<K>& ws = reinterpret_cast<WarpSmem<K>*>(smem_raw)[threadIdx.x >> 5];
-  const uint32_t lane = lane_id();
-  const uint64_t total = BATCH ? (uint64_t)*(volatile uint32_t*)(a.counters + 1) : a.one_ntiles;
+// Persistent decoder. A block claims chunks of C = warps * G consecutive
+// work items from the global counter (one atomic per chunk); its warps take
+// the chunk's items one at a time, in order, through a shared-memory word
+// (base << 32 | items taken). Items are thus handed out in increasing
+// order: every item below a handed-out item has been handed out too, and a
+// warp holds only items below those still in its block's chunk. A look-back
+// waits on lower items only, so the lowest unfinished item always belongs
+// to a running warp and decoding always progresses. When one warp happens
+// to take consecutive tiles of a list, it passes the prefix in registers.
+__device__ uint64_t take_item(unsigned long long* sq, uint32_t* counter, uint64_t total, uint32_t C,
+                              uint32_t* status) {
+  // The word starts as (no chunk, C taken), so the first taker refills. A
+  // returned item at or past `total` ends the caller's loop.
   for (;;) {
-    uint32_t item = 0;
-    if (lane == 0) item = atomicAdd(a.counters, 1u);
-    item = __shfl_sync(kFull, item, 0);
-    if (item >= total) break;
-    ListRef L;
-    uint64_t t;
-    gc_tile rec = {0, 0, 0, 0};
-    uint32_t where;
-    if (!BATCH) {
-      L = a.one;
-      t = item;
-      where = item;
-      if (t > 0) {
-        uint64_t x0 = 0, x1 = 0, x2 = 0;
-        if (lane == 0) {
-          const gc_tile* p = a.one_tiles + t;
-          x0 = p->lane_bit;
-          x1 = p->ctrl_bit;
-          x2 = ((uint64_t)p->row_skip << 32) | p->exc_off;
-        }
-        rec.lane_bit = __shfl_sync(kFull, x0, 0);
-        rec.ctrl_bit = __shfl_sync(kFull, x1, 0);
-        x2 = __shfl_sync(kFull, x2, 0);
-        rec.exc_off = (uint32_t)x2;
-        rec.row_skip = (uint32_t)(x2 >> 32);
-      }
-    } else {
-      const uint2 it = a.items[item];
-      if (it.x >= a.nlists) {
-        // an empty slot (the batch overflowed its item table)
-        if (a.restore && lane == 0) look_back(a.lb, item, true, 0, a.status, 0xffffffffu);
-        continue;
-      }
-      const gc_list d = a.lists[it.x];
-      t = it.y;
-      where = it.x;
-      L.ctrl = a.ctrl_pool + d.ctrl_off;
-      L.ctrl_bytes = d.ctrl_off < a.ctrl_pool_bytes ? a.ctrl_pool_bytes - d.ctrl_off : 0;
-      L.data = a.data_pool + d.data_off;
-      L.data_words = d.data_off < a.data_pool_words ? a.data_pool_words - d.data_off : 0;
-      L.out = a.out_pool + d.out_off;
-      L.n = d.n;
-      if (d.out_off + d.n > a.out_pool_len) {
-        if (lane == 0) report(a.status, GC_ERR_INVALID, where);
-        L.n = 0;
-      }
-      if (t > 0) {
-        const uint64_t ti = (uint64_t)d.tile_off + t - 1;
-        if (ti < a.tile_pool_len) rec = a.tile_pool[ti];
-        else if (lane == 0) report(a.status, GC_ERR_CORRUPT, where);
-      }
+    const unsigned long long old = atomicAdd(sq, 1ull);
+    const uint64_t base = old >> 32;
+    const uint32_t taken = (uint32_t)old;
+    if (taken < C) return base + taken < total ? base + taken : total;
+    if (taken == C) {
+      uint64_t nb = atomicAdd(counter, C);
+      if (nb > total) nb = total;
+      atomicExch(sq, ((unsigned long long)nb << 32) | 1ull);
+      return nb;
     }
-    if ((uint64_t)t * kTileInts >= L.n) {
-      // nothing to decode (an empty list or a bad record); keep the chain alive
-      if (a.restore && lane == 0) look_back(a.lb, item, true, 0, a.status, where);
-      continue;
+    // another warp is refilling the chunk
+    uint32_t spins = 0;
+    while ((*(volatile unsigned long long*)sq >> 32) == base) {
+      if (++spins > kSpinLimit) {
+        report(status, GC_ERR_TIMEOUT, 0xffffffffu);
+        return total;
+      }
+      __nanosleep(20);
     }
-    decode_tile<KIND, K>(a, L, rec, t, item, where, ws);
   }
 }
 
-// Batched: one work item per tile of every list. Lists reserve contiguous
-// item ranges with one atomic per warp, so a list's tiles are consecutive
-// items and a tile's predecessor was claimed before it.
-__global__ void k_expand(const gc_list* lists, uint64_t nlists, uint32_t k, uint2* items,
-                         uint64_t max_items, uint32_t* counters, uint32_t* status) {
+template <int KIND, int K, bool BATCH>
+__global__ void __launch_bounds__(512) k_decode(DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long s_queue;
+  WarpSmem<K>& ws = reinterpret_cast<WarpSmem<K>*>(smem_raw)[threadIdx.x >> 5];
+  const uint32_t lane = lane_id();
+  uint64_t total = a.one_ntiles;
+  if (BATCH) {
+    total = *(volatile const unsigned long long*)a.work_count;
+    if (total > a.work_cap) total = a.work_cap;
+  }
+  const uint32_t C = a.claim * (blockDim.x >> 5);
+  if (threadIdx.x == 0) s_queue = (0xffffffffull << 32) | C;  // empty: the first taker refills
+  __syncthreads();
+  uint64_t prev_list = ~0ull, prev_t = ~0ull;
+  uint32_t prev_incl = 0;
+  for (;;) {
+    uint64_t item = 0;
+    if (lane == 0) item = take_item(&s_queue, a.counters, total, C, a.status);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= total) break;
+    ListRef L;
+    uint64_t t, list;
+    gc_tile rec = {0, 0, 0, 0};
+    uint32_t where;
+    bool skip = false;
+    if (!BATCH) {
+      L = a.one;
+      t = item;
+      list = 0;
+      where = (uint32_t)item;
+      if (t > 0) {
+        const gc_tile* p = a.one_tiles + t;
+        rec.lane_bit = p->lane_bit;
+        rec.ctrl_bit = p->ctrl_bit;
+        rec.exc_off = p->exc_off;
+        rec.row_skip = p->row_skip;
+      }
+    } else {
+      const uint4* wp = reinterpret_cast<const uint4*>(a.work + item);
+      const uint4 q0 = __ldg(wp), q1 = __ldg(wp + 1), q2 = __ldg(wp + 2), q3 = __ldg(wp + 3);
+      const uint64_t ctrl_off = q0.x | ((uint64_t)q0.y << 32);
+      const uint64_t data_off = q0.z | ((uint64_t)q0.w << 32);
+      const uint64_t out_off = q1.x | ((uint64_t)q1.y << 32);
+      const uint32_t n = q1.z;
+      t = q1.w;
+      rec.lane_bit = q2.x | ((uint64_t)q2.y << 32);
+      rec.ctrl_bit = q2.z | ((uint64_t)q2.w << 32);
+      rec.exc_off = q3.x;
+      rec.row_skip = q3.y;
+      list = q3.z;
+      where = q3.z;
+      L.ctrl = a.ctrl_pool + ctrl_off;
+      L.ctrl_bytes = ctrl_off < a.ctrl_pool_bytes ? a.ctrl_pool_bytes - ctrl_off : 0;
+      L.data = a.data_pool + data_off;
+      L.data_words = data_off < a.data_pool_words ? a.data_pool_words - data_off : 0;
+      L.out = a.out_pool + out_off;
+      L.n = n;
+      if (q3.z == 0xffffffffu) {
+        skip = true;  // an empty slot (the plan overflowed its table)
+      } else if (out_off + n > a.out_pool_len || (data_off % K) != 0) {
+        if (lane == 0) report(a.status, GC_ERR_INVALID, where);
+        skip = true;
+      }
+    }
+    if (skip || t * kTileInts >= L.n) {
+      // nothing to decode; keep the chain of prefixes alive
+      if (a.restore && lane == 0) st_release(a.lb + item, kFlagPrefix);
+      prev_list = ~0ull;
+      continue;
+    }
+    const bool chained = (list == prev_list) && (t == prev_t + 1);
+    prev_incl = decode_tile<KIND, K>(a, L, rec, t, item, where, chained, prev_incl, ws);
+    prev_list = list;
+    prev_t = t;
+  }
+}
+
+// Batched plan, pass 1: one thread per list reserves a contiguous range of
+// work items for the list's tiles (one atomic per warp) and writes (list,
+// tile) into each record. A list's tiles are consecutive items, so a tile's
+// predecessor is always claimed before it.
+__global__ void k_plan_reserve(const gc_list* lists, uint64_t nlists, uint32_t k, gc_work* work, uint64_t cap,
+                               unsigned long long* count, uint32_t* status) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = lane_id();
-  uint32_t nt = 0;
+  uint64_t nt = 0;
   if (i < nlists) {
     const uint64_t n = lists[i].n;
     const uint64_t R = (n + k - 1) / k;
     const uint64_t tr = kTileInts / k;
-    nt = (uint32_t)((R + tr - 1) / tr);
+    nt = (R + tr - 1) / tr;
   }
-  const uint32_t incl = warp_incl_sum(nt);
-  uint32_t base = 0;
-  if (lane == 31) base = atomicAdd(counters + 1, incl);
-  base = __shfl_sync(kFull, base, 31) + incl - nt;
-  if (i < nlists) {
-    if ((uint64_t)base + nt > max_items) {
-      report(status, GC_ERR_NOSPACE, (uint32_t)i);
-      // the slots of this list that fall inside the table are marked empty:
-      // the count is clamped to max_items afterwards, so they are read
-      for (uint64_t t = base; t < max_items && t < (uint64_t)base + nt; ++t)
-        items[t] = make_uint2(0xffffffffu, 0u);
-    } else {
-      for (uint32_t t = 0; t < nt; ++t) items[base + t] = make_uint2((uint32_t)i, t);
-    }
+  const uint64_t incl = warp_incl_sum(nt);
+  unsigned long long b = 0;
+  if (lane == 31) b = atomicAdd(count, (unsigned long long)incl);
+  const uint64_t base = __shfl_sync(kFull, b, 31) + incl - nt;
+  if (i >= nlists) return;
+  const bool fits = base + nt <= cap;
+  if (!fits) report(status, GC_ERR_NOSPACE, (uint32_t)i);
+  for (uint64_t t = 0; t < nt && base + t < cap; ++t) {
+    gc_work* w = work + base + t;
+    w->tile = (uint32_t)t;
+    w->list = fits ? (uint32_t)i : 0xffffffffu;
   }
 }
 
-__global__ void k_clamp_items(uint32_t* counters, uint64_t max_items) {
-  if (counters[1] > max_items) counters[1] = (uint32_t)max_items;
+// Pass 2: one thread per work item fills in the list's descriptor and the
+// tile's record (tile 0 starts at the list's first unit).
+__global__ void k_plan_fill(const gc_list* lists, uint64_t nlists, const gc_tile* tiles, uint64_t ntiles,
+                            gc_work* work, uint64_t cap, const unsigned long long* count, uint32_t* status) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t total = *count;
+  if (total > cap) total = cap;
+  if (i >= total) return;
+  gc_work w = work[i];
+  if (w.list >= nlists) {
+    w = gc_work{0, 0, 0, 0, 0, 0, 0, 0, 0, 0xffffffffu, 0};
+    work[i] = w;
+    return;
+  }
+  const gc_list d = lists[w.list];
+  w.ctrl_off = d.ctrl_off;
+  w.data_off = d.data_off;
+  w.out_off = d.out_off;
+  w.n = d.n;
+  w.lane_bit = w.ctrl_bit = 0;
+  w.exc_off = w.row_skip = 0;
+  w.reserved = 0;
+  if (w.tile > 0) {
+    const uint64_t ti = (uint64_t)d.tile_off + w.tile - 1;
+    if (ti < ntiles) {
+      const gc_tile r = tiles[ti];
+      w.lane_bit = r.lane_bit;
+      w.ctrl_bit = r.ctrl_bit;
+      w.exc_off = r.exc_off;
+      w.row_skip = r.row_skip;
+    } else {
+      report(status, GC_ERR_CORRUPT, w.list);
+      w.n = 0;  // decodes nothing
+    }
+  }
+  work[i] = w;
 }
 
 // ------------------------------------------------------- tile index build
@@ -738,30 +877,41 @@ namespace {
 template <int K>
 size_t warp_smem() { return sizeof(WarpSmem<K>); }
 
+constexpr uint32_t kMaxWarps = 16;     // warps per block (launch bounds: 512 threads)
+constexpr uint32_t kDefaultWarps = 8;
+constexpr uint32_t kMaxClaim = 64;     // work items per claim
+constexpr uint32_t kDefaultClaim = 4;
+
 template <int KIND, int K, bool BATCH>
 cudaError_t launch_decode_t(const DecodeArgs& a, uint32_t warps, uint32_t blocks_per_sm, uint64_t work,
                             cudaStream_t s) {
   auto fn = k_decode<KIND, K, BATCH>;
   const size_t smem = warps * warp_smem<K>();
-  // the attribute and the occupancy are fixed per (device, warps): cache them
-  static int cached_occ[64][33] = {};
+  // the shared-memory limit only grows, and the occupancy is fixed per
+  // (device, warps): both are cached so a launch costs one API call
+  static size_t smem_limit[64] = {};
+  static int cached_occ[64][kMaxWarps + 1] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int occ = (dev >= 0 && dev < 64) ? cached_occ[dev][warps] : 0;
-  if (occ == 0) {
+  const bool cache = dev >= 0 && dev < 64;
+  if (!cache || smem > smem_limit[dev]) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (cache) smem_limit[dev] = smem;
+  }
+  int occ = cache ? cached_occ[dev][warps] : 0;
+  if (occ == 0) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, (int)(warps * 32), smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    if (dev >= 0 && dev < 64) cached_occ[dev][warps] = occ;
+    if (cache) cached_occ[dev][warps] = occ;
   }
   const int sms = gc_host::sm_count();
   uint32_t bps = blocks_per_sm ? blocks_per_sm : (uint32_t)occ;
   if (bps > (uint32_t)occ) bps = (uint32_t)occ;
   uint64_t grid = (uint64_t)bps * sms;
-  const uint64_t need = (work + warps - 1) / warps;  // one tile per warp at most
+  const uint64_t need = (work + (uint64_t)warps * a.claim - 1) / ((uint64_t)warps * a.claim);
   if (!BATCH && grid > need) grid = need ? need : 1;
   fn<<<(unsigned)grid, warps * 32, smem, s>>>(a);
   gc_host::count_launch();
@@ -782,6 +932,21 @@ cudaError_t launch_decode(uint32_t kind, uint32_t k, const DecodeArgs& a, uint32
   GC_DISPATCH(GC_PFD)
 #undef GC_DISPATCH
   return cudaErrorInvalidValue;
+}
+
+// Launch shape from the caller's request (NULL = defaults); GC_ERR_INVALID
+// for a shape out of range.
+gc_status launch_shape(const gc_launch* l, uint32_t* warps, uint32_t* bps, uint32_t* claim) {
+  *warps = kDefaultWarps;
+  *bps = 0;
+  *claim = kDefaultClaim;
+  if (!l) return GC_OK;
+  if (l->warps_per_block < 1 || l->warps_per_block > kMaxWarps) return GC_ERR_INVALID;
+  if (l->items_per_claim > kMaxClaim) return GC_ERR_INVALID;
+  *warps = l->warps_per_block;
+  *bps = l->blocks_per_sm;
+  if (l->items_per_claim) *claim = l->items_per_claim;
+  return GC_OK;
 }
 
 uint64_t index_nunits(const gc_codec& c, uint64_t R, uint64_t ctrl_bytes) {
@@ -866,7 +1031,7 @@ gc_status gc_build_tiles(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t 
   gc_status st = gc_host::check_codec(codec);
   if (st != GC_OK) return st;
   if (n == 0) return GC_OK;
-  if (!d_ctrl || !d_tiles || !d_scratch) return GC_ERR_INVALID;
+  if ((!d_ctrl && ctrl_bytes) || !d_tiles || !d_scratch) return GC_ERR_INVALID;
   if (scratch_bytes < index_scratch(*codec, n)) return GC_ERR_NOSPACE;
   return build_tiles_impl(*codec, d_ctrl, ctrl_bytes, n, d_tiles, (UnitAgg*)d_scratch, d_status,
                           (cudaStream_t)stream);
@@ -880,7 +1045,9 @@ gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_
   gc_status st = gc_host::check_codec(codec);
   if (st != GC_OK) return st;
   if (n == 0) return GC_OK;
-  if (!d_ctrl || !d_data || !d_out || !d_scratch) return GC_ERR_INVALID;
+  // an area may be empty (a Group-PFD or AFOR list of zeros has no data
+  // words); a non-empty one needs a pointer
+  if ((!d_ctrl && ctrl_bytes) || (!d_data && data_words) || !d_out || !d_scratch) return GC_ERR_INVALID;
   if (((uintptr_t)d_data & 15) != 0) return GC_ERR_INVALID;
   uint64_t need = 0;
   gc_decode_scratch_size(codec, n, d_tiles != nullptr, &need);
@@ -889,7 +1056,7 @@ gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_
   const uint64_t R = (n + codec->k - 1) / codec->k;
   const uint64_t tr = kTileInts / codec->k;
   const uint64_t nt = (R + tr - 1) / tr;
-  if (nt > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  if (nt > 0xffffffffull - kMaxClaim * kMaxWarps) return GC_ERR_UNSUPPORTED;
   unsigned char* base = (unsigned char*)d_scratch;
   uint32_t* counters = (uint32_t*)base;
   unsigned long long* lb = (unsigned long long*)(base + gc_host::align_up(64, 256));
@@ -916,8 +1083,9 @@ gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_
   a.ld = codec->ld;
   a.restore = restore_docids;
   a.status = d_status;
+  a.claim = kDefaultClaim;
   gc_host::reset_launches();
-  cudaError_t e = launch_decode<false>(codec->kind, codec->k, a, 8, 0, nt, s);
+  cudaError_t e = launch_decode<false>(codec->kind, codec->k, a, kDefaultWarps, 0, nt, s);
   gc_host::count_launch(launches);
   return e == cudaSuccess ? GC_OK : GC_ERR_CUDA;
 }
@@ -938,11 +1106,87 @@ gc_status gc_decode_paper(const gc_codec* codec, const uint8_t* d_buf, uint64_t 
                    nullptr, d_out, restore_docids, d_scratch, scratch_bytes, d_status, stream);
 }
 
+gc_status gc_plan_batch(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists, const gc_tile* d_tile_pool,
+                        uint64_t tile_pool_len, gc_work* d_work, uint64_t work_cap, uint64_t* d_count,
+                        uint32_t* d_status, void* stream) {
+  gc_host::reset_launches();
+  gc_status st = gc_host::check_codec(codec);
+  if (st != GC_OK) return st;
+  if (!d_count || (nlists && (!d_lists || !d_work))) return GC_ERR_INVALID;
+  if (nlists > 0xffffffffull || work_cap > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_count, 0, 8, s) != cudaSuccess) return GC_ERR_CUDA;
+  if (nlists == 0) return GC_OK;
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d_count);
+  k_plan_reserve<<<(unsigned)((nlists + 255) / 256), 256, 0, s>>>(d_lists, nlists, codec->k, d_work, work_cap, cnt,
+                                                                  d_status);
+  if (work_cap)
+    k_plan_fill<<<(unsigned)((work_cap + 255) / 256), 256, 0, s>>>(d_lists, nlists, d_tile_pool,
+                                                                   d_tile_pool ? tile_pool_len : 0, d_work,
+                                                                   work_cap, cnt, d_status);
+  gc_host::count_launch(work_cap ? 2 : 1);
+  return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+}
+
+gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes) {
+  if (!bytes) return GC_ERR_INVALID;
+  *bytes = gc_host::align_up(64, 256) + gc_host::align_up(work_cap * 8, 256);
+  return GC_OK;
+}
+
+gc_status gc_decode_plan(const gc_codec* codec, const gc_work* d_work, const uint64_t* d_count, uint64_t work_cap,
+                         const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes, const uint32_t* d_data_pool,
+                         uint64_t data_pool_words, uint32_t* d_out_pool, uint64_t out_pool_len, int restore_docids,
+                         const gc_launch* launch, void* d_scratch, uint64_t scratch_bytes, uint32_t* d_status,
+                         void* stream) {
+  gc_host::reset_launches();
+  gc_status st = gc_host::check_codec(codec);
+  if (st != GC_OK) return st;
+  if (work_cap == 0) return GC_OK;
+  if (!d_work || !d_count || (!d_ctrl_pool && ctrl_pool_bytes) || (!d_data_pool && data_pool_words) ||
+      !d_out_pool || !d_scratch)
+    return GC_ERR_INVALID;
+  if (((uintptr_t)d_data_pool & 15) != 0 || ((uintptr_t)d_work & 15) != 0) return GC_ERR_INVALID;
+  if (work_cap > 0xffffffffull - kMaxClaim * kMaxWarps) return GC_ERR_UNSUPPORTED;
+  uint64_t need = 0;
+  gc_decode_plan_scratch_size(work_cap, &need);
+  if (scratch_bytes < need) return GC_ERR_NOSPACE;
+  uint32_t warps, bps, claim;
+  st = launch_shape(launch, &warps, &bps, &claim);
+  if (st != GC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base = (unsigned char*)d_scratch;
+  uint32_t* counters = (uint32_t*)base;
+  unsigned long long* lb = (unsigned long long*)(base + gc_host::align_up(64, 256));
+  if (cudaMemsetAsync(base, 0, 64, s) != cudaSuccess) return GC_ERR_CUDA;
+  if (restore_docids && cudaMemsetAsync(lb, 0, work_cap * 8, s) != cudaSuccess) return GC_ERR_CUDA;
+  DecodeArgs a = {};
+  a.work = d_work;
+  a.work_count = reinterpret_cast<const unsigned long long*>(d_count);
+  a.work_cap = work_cap;
+  a.ctrl_pool = d_ctrl_pool;
+  a.ctrl_pool_bytes = ctrl_pool_bytes;
+  a.data_pool = d_data_pool;
+  a.data_pool_words = data_pool_words;
+  a.out_pool = d_out_pool;
+  a.out_pool_len = out_pool_len;
+  a.counters = counters;
+  a.lb = lb;
+  a.cg = codec->cg;
+  a.ld = codec->ld;
+  a.claim = claim;
+  a.restore = restore_docids;
+  a.status = d_status;
+  cudaError_t e = launch_decode<true>(codec->kind, codec->k, a, warps, bps, work_cap, s);
+  return e == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+}
+
 gc_status gc_decode_batch_scratch_size(uint64_t nlists, uint64_t max_tiles, uint64_t* bytes) {
   (void)nlists;
   if (!bytes) return GC_ERR_INVALID;
-  *bytes = gc_host::align_up(64, 256) + gc_host::align_up(max_tiles * 8, 256) +
-           gc_host::align_up(max_tiles * 8, 256);
+  uint64_t dec = 0;
+  gc_decode_plan_scratch_size(max_tiles, &dec);
+  *bytes = gc_host::align_up(64, 256) + gc_host::align_up(max_tiles * sizeof(gc_work), 256) + dec;
   return GC_OK;
 }
 
@@ -955,51 +1199,31 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
   gc_host::reset_launches();
   gc_status st = gc_host::check_codec(codec);
   if (st != GC_OK) return st;
-  if (nlists == 0) return GC_OK;
-  if (!d_lists || !d_ctrl_pool || !d_data_pool || !d_out_pool || !d_scratch) return GC_ERR_INVALID;
+  if (nlists == 0 || max_tiles == 0) return GC_OK;
+  if (!d_lists || (!d_ctrl_pool && ctrl_pool_bytes) || (!d_data_pool && data_pool_words) || !d_out_pool ||
+      !d_scratch)
+    return GC_ERR_INVALID;
   if (((uintptr_t)d_data_pool & 15) != 0) return GC_ERR_INVALID;
-  if (max_tiles > 0xffffffffull || nlists > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  if (max_tiles > 0xffffffffull - kMaxClaim * kMaxWarps || nlists > 0xffffffffull) return GC_ERR_UNSUPPORTED;
   uint64_t need = 0;
   gc_decode_batch_scratch_size(nlists, max_tiles, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
-  uint32_t warps = 8, bps = 0;
-  if (launch) {
-    if (launch->warps_per_block < 1 || launch->warps_per_block > 32) return GC_ERR_INVALID;
-    warps = launch->warps_per_block;
-    bps = launch->blocks_per_sm;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t warps, bps, claim;
+  st = launch_shape(launch, &warps, &bps, &claim);
+  if (st != GC_OK) return st;
   unsigned char* base = (unsigned char*)d_scratch;
-  uint32_t* counters = (uint32_t*)base;
-  uint2* items = (uint2*)(base + gc_host::align_up(64, 256));
-  unsigned long long* lb = (unsigned long long*)(base + gc_host::align_up(64, 256) +
-                                                 gc_host::align_up(max_tiles * 8, 256));
-  if (cudaMemsetAsync(base, 0, 64, s) != cudaSuccess) return GC_ERR_CUDA;
-  if (restore_docids && cudaMemsetAsync(lb, 0, max_tiles * 8, s) != cudaSuccess) return GC_ERR_CUDA;
-  const unsigned eb = (unsigned)((nlists + 255) / 256);
-  k_expand<<<eb, 256, 0, s>>>(d_lists, nlists, codec->k, items, max_tiles, counters, d_status);
-  k_clamp_items<<<1, 1, 0, s>>>(counters, max_tiles);
-  DecodeArgs a = {};
-  a.lists = d_lists;
-  a.nlists = nlists;
-  a.ctrl_pool = d_ctrl_pool;
-  a.ctrl_pool_bytes = ctrl_pool_bytes;
-  a.data_pool = d_data_pool;
-  a.data_pool_words = data_pool_words;
-  a.tile_pool = d_tile_pool;
-  a.tile_pool_len = d_tile_pool ? tile_pool_len : 0;
-  a.out_pool = d_out_pool;
-  a.out_pool_len = out_pool_len;
-  a.items = items;
-  a.counters = counters;
-  a.lb = lb;
-  a.cg = codec->cg;
-  a.ld = codec->ld;
-  a.restore = restore_docids;
-  a.status = d_status;
-  cudaError_t e = launch_decode<true>(codec->kind, codec->k, a, warps, bps, max_tiles, s);
-  gc_host::count_launch(2);
-  return e == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+  uint64_t* count = (uint64_t*)base;
+  gc_work* work = (gc_work*)(base + gc_host::align_up(64, 256));
+  unsigned char* rest = base + gc_host::align_up(64, 256) + gc_host::align_up(max_tiles * sizeof(gc_work), 256);
+  st = gc_plan_batch(codec, d_lists, nlists, d_tile_pool, tile_pool_len, work, max_tiles, count, d_status, stream);
+  if (st != GC_OK) return st;
+  const uint32_t planned = gc_host::launches();
+  uint64_t dec = 0;
+  gc_decode_plan_scratch_size(max_tiles, &dec);
+  st = gc_decode_plan(codec, work, count, max_tiles, d_ctrl_pool, ctrl_pool_bytes, d_data_pool, data_pool_words,
+                      d_out_pool, out_pool_len, restore_docids, launch, rest, dec, d_status, stream);
+  gc_host::count_launch(planned);
+  return st;
 }
 
 }  // extern "C"

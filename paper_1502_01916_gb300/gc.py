@@ -21,7 +21,9 @@ import numpy as np
 import torch
 
 __all__ = [
-    "SIMPLE", "SCHEME", "AFOR", "PFD", "LD_BINARY", "LD_CU", "LD_IU", "TILE_INTS", "GcError",
+    "SIMPLE", "SCHEME", "AFOR", "PFD", "LD_BINARY", "LD_CU", "LD_IU", "TILE_INTS", "TILE_BYTES", "LIST_BYTES",
+    "WORK_BYTES", "GcError", "gc_work", "gc_plan_batch", "gc_decode_plan_scratch_size", "gc_decode_plan", "Plan",
+    "plan_index",
     "gc_codec", "gc_tile", "gc_list", "gc_launch", "library_path", "load", "make_codec",
     "gc_pfd_rows_for_zeta", "gc_max_encoded_size", "gc_encode_scratch_size", "gc_encode",
     "gc_encode_batch_scratch_size", "gc_encode_batch", "gc_decode_scratch_size", "gc_build_tiles",
@@ -68,11 +70,20 @@ class gc_list(ctypes.Structure):
 
 
 class gc_launch(ctypes.Structure):
-    _fields_ = [("warps_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+    _fields_ = [("warps_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("items_per_claim", ctypes.c_uint32)]
+
+
+class gc_work(ctypes.Structure):
+    _fields_ = [("ctrl_off", ctypes.c_uint64), ("data_off", ctypes.c_uint64), ("out_off", ctypes.c_uint64),
+                ("n", ctypes.c_uint32), ("tile", ctypes.c_uint32), ("lane_bit", ctypes.c_uint64),
+                ("ctrl_bit", ctypes.c_uint64), ("exc_off", ctypes.c_uint32), ("row_skip", ctypes.c_uint32),
+                ("list", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 TILE_BYTES = ctypes.sizeof(gc_tile)
 LIST_BYTES = ctypes.sizeof(gc_list)
+WORK_BYTES = ctypes.sizeof(gc_work)
 
 _lib = None
 _lock = threading.Lock()
@@ -110,6 +121,10 @@ def load():
             "gc_decode_batch_scratch_size": (_I, [_U64, _U64, _U64P]),
             "gc_decode_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I, _U64,
                                      ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
+            "gc_plan_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V]),
+            "gc_decode_plan_scratch_size": (_I, [_U64, _U64P]),
+            "gc_decode_plan": (_I, [_CP, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I,
+                                    ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
             "gc_last_launch_count": (_U32, []),
             "gc_version": (ctypes.c_char_p, []),
         }
@@ -243,6 +258,29 @@ def gc_decode_batch(codec, d_lists, nlists, d_ctrl_pool, d_data_pool, d_tile_poo
                                   _ptr(d_tile_pool), tile_len, _ptr(d_out_pool), d_out_pool.numel(),
                                   int(bool(restore_docids)), max_tiles, lp, _ptr(d_scratch), d_scratch.numel(),
                                   _ptr(d_status), _stream(stream)), "gc_decode_batch")
+
+
+def gc_plan_batch(codec, d_lists, nlists, d_tile_pool, d_work, d_count, d_status, stream=None):
+    tile_len = d_tile_pool.numel() // TILE_BYTES if d_tile_pool is not None else 0
+    _check(load().gc_plan_batch(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_tile_pool), tile_len,
+                                _ptr(d_work), d_work.numel() // WORK_BYTES, _ptr(d_count), _ptr(d_status),
+                                _stream(stream)), "gc_plan_batch")
+
+
+def gc_decode_plan_scratch_size(work_cap: int) -> int:
+    b = _U64()
+    _check(load().gc_decode_plan_scratch_size(work_cap, ctypes.byref(b)), "gc_decode_plan_scratch_size")
+    return b.value
+
+
+def gc_decode_plan(codec, d_work, d_count, d_ctrl_pool, d_data_pool, d_out_pool, restore_docids, launch, d_scratch,
+                   d_status, stream=None):
+    lp = ctypes.byref(launch) if launch is not None else None
+    _check(load().gc_decode_plan(ctypes.byref(codec), _ptr(d_work), _ptr(d_count), d_work.numel() // WORK_BYTES,
+                                 _ptr(d_ctrl_pool), d_ctrl_pool.numel(), _ptr(d_data_pool), d_data_pool.numel(),
+                                 _ptr(d_out_pool), d_out_pool.numel(), int(bool(restore_docids)), lp,
+                                 _ptr(d_scratch), d_scratch.numel(), _ptr(d_status), _stream(stream)),
+           "gc_decode_plan")
 
 
 def gc_last_launch_count() -> int:
@@ -435,19 +473,46 @@ def _bounds(codec: gc_codec, h_n: np.ndarray):
         yield cc * c, dc * c
 
 
+@dataclasses.dataclass
+class Plan:
+    """The work plan of an index (gc_plan_batch): one gc_work per tile."""
+    work: torch.Tensor   # max_tiles * 64 bytes
+    count: torch.Tensor  # one int64: the number of tiles
+
+    def nbytes(self) -> int:
+        return self.work.numel()
+
+
+def plan_index(index: Index, status=None, stream=None) -> Plan:
+    """Build the index's work plan on the device (gc_plan_batch)."""
+    dev = index.data.device
+    work = torch.empty(max(1, index.max_tiles) * WORK_BYTES, dtype=torch.uint8, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = new_status(dev) if status is None else status
+    gc_plan_batch(index.codec, index.lists, index.nlists, index.tiles, work, count, st, stream)
+    check_status(st, "gc_plan_batch")
+    return Plan(work, count)
+
+
 def decode_index(index: Index, out: torch.Tensor | None = None, restore_docids: bool = True,
                  launch: gc_launch | None = None, scratch: torch.Tensor | None = None, status=None,
-                 check: bool = True, stream=None) -> torch.Tensor:
-    """Decode every list of an index in one gc_decode_batch call."""
+                 check: bool = True, stream=None, plan: Plan | None = None) -> torch.Tensor:
+    """Decode every list of an index in one call: gc_decode_plan when a plan
+    is given, else gc_decode_batch (which plans into its scratch)."""
     dev = index.data.device
     total = index.total_ints
     out = torch.empty(max(1, total), dtype=torch.int32, device=dev) if out is None else out
     if scratch is None:
-        scratch = torch.empty(gc_decode_batch_scratch_size(index.nlists, index.max_tiles), dtype=torch.uint8,
-                              device=dev)
+        size = (gc_decode_plan_scratch_size(index.max_tiles) if plan is not None
+                else gc_decode_batch_scratch_size(index.nlists, index.max_tiles))
+        scratch = torch.empty(size, dtype=torch.uint8, device=dev)
     st = new_status(dev) if status is None else status
-    gc_decode_batch(index.codec, index.lists, index.nlists, index.ctrl, index.data, index.tiles, out,
-                    restore_docids, index.max_tiles, launch, scratch, st, stream)
+    if plan is not None:
+        gc_decode_plan(index.codec, plan.work, plan.count, index.ctrl, index.data, out, restore_docids, launch,
+                       scratch, st, stream)
+    else:
+        gc_decode_batch(index.codec, index.lists, index.nlists, index.ctrl, index.data, index.tiles, out,
+                        restore_docids, index.max_tiles, launch, scratch, st, stream)
     if check:
-        check_status(st, "gc_decode_batch")
+        check_status(st, "gc_decode_plan" if plan is not None else "gc_decode_batch")
     return out

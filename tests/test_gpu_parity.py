@@ -201,15 +201,49 @@ def test_batch_encode_decode(gc, c):
     assert (gc.as_u32(out)[:len(gaps)] == gaps).all()
 
 
-@pytest.mark.parametrize("warps,bps", [(1, 1), (4, 2), (8, 0), (16, 0), (32, 1)])
-def test_batch_launch_shapes(gc, warps, bps):
-    """The result does not depend on the launch shape."""
-    oc, gcc = pair(gc, (O.PFD, 32, 0, 0, 0.1))
+@pytest.mark.parametrize("warps,bps,claim", [(1, 1, 1), (4, 2, 2), (8, 0, 0), (16, 0, 7), (2, 1, 64)])
+@pytest.mark.parametrize("k", [4, 32])
+def test_batch_launch_shapes(gc, warps, bps, claim, k):
+    """The result does not depend on the launch shape or the claim size, with
+    a plan built once and reused."""
+    oc, gcc = pair(gc, (O.PFD, k, 0, 0, 0.1))
     lens, gaps, off = small_index(5)
     idx = gc.encode_index(gcc, upload_u32(gaps), lens)
     want = np.concatenate([O.prefix_sum(gaps[off[i]:off[i + 1]]) for i in range(len(lens))])
-    out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps))
+    out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps, claim))
     assert (gc.as_u32(out)[:len(gaps)] == want).all()
+    plan = gc.plan_index(idx)
+    assert int(plan.count.item()) == idx.max_tiles
+    for _ in range(2):
+        out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps, claim), plan=plan)
+        assert (gc.as_u32(out)[:len(gaps)] == want).all()
+
+
+def test_plan_records(gc):
+    """Each plan record carries its list's descriptor and its tile's record,
+    lists in order and tiles in order inside a list."""
+    oc, gcc = pair(gc, (O.SIMPLE, 4, 0, 0, 0.1))
+    lens, gaps, off = small_index(8, nlists=40)
+    idx = gc.encode_index(gcc, upload_u32(gaps), lens)
+    plan = gc.plan_index(idx)
+    w = plan.work.cpu().numpy().view(np.dtype([("ctrl_off", "<u8"), ("data_off", "<u8"), ("out_off", "<u8"),
+                                                ("n", "<u4"), ("tile", "<u4"), ("lane_bit", "<u8"),
+                                                ("ctrl_bit", "<u8"), ("exc_off", "<u4"), ("row_skip", "<u4"),
+                                                ("list", "<u4"), ("reserved", "<u4")]))
+    ntiles = [-(-(-(-int(n) // 4)) // 256) for n in lens]
+    seen = {}
+    for r in w[:int(plan.count.item())]:
+        seen.setdefault(int(r["list"]), []).append(r)
+    assert sorted(seen) == [i for i in range(len(lens)) if ntiles[i] > 0]
+    for i, recs in seen.items():
+        assert [int(r["tile"]) for r in recs] == list(range(ntiles[i]))
+        ctrl, _ = O.encode(oc, gaps[off[i]:off[i + 1]])
+        tref = O.tile_index(oc, ctrl, int(lens[i]))
+        for r in recs:
+            assert int(r["n"]) == int(lens[i]) and int(r["out_off"]) == int(off[i])
+            t = tref[int(r["tile"])]
+            assert (int(r["lane_bit"]), int(r["ctrl_bit"]), int(r["exc_off"]), int(r["row_skip"])) == \
+                (int(t["lane_bit"]), int(t["ctrl_bit"]), int(t["exc_off"]), int(t["row_skip"]))
 
 
 def test_batch_overflow_reports_nospace(gc):
