@@ -396,8 +396,8 @@ def main():
                    "codecs": [CODECS[n][1] + (f" zeta={a.zeta}" if n == "pfd" else "") for n in idxs],
                    "k": a.k, "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "launch": {"warps_per_block": a.warps or 8, "blocks_per_sm": a.bps or "max",
-                              "items_per_claim": a.claim or 4},
+                   "launch": {"warps_per_block": a.warps or 4, "blocks_per_sm": a.bps or "max",
+                              "items_per_claim": a.claim or 8},
                    "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},
         "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list,
         "cpu_baseline": cpu, "clocks": clk,
@@ -420,21 +420,21 @@ def per_list_rate(gc, idxs, lengths, dev, nsample=2000, seed=3):
     res = {}
     lib = gc.load()
     for n, idx in idxs.items():
-        lists = idx.lists.cpu().numpy().view(np.dtype([("ctrl_off", "<u8"), ("data_off", "<u8"),
-                                                        ("out_off", "<u8"), ("n", "<u4"), ("tile_off", "<u4")]))
+        lists = idx.lists.cpu().numpy().view(gc.LIST_DTYPE)
         nmax = int(lengths[ids].max())
         scratch = torch.empty(gc.gc_decode_scratch_size(idx.codec, nmax, True), dtype=torch.uint8, device=dev)
         out = torch.empty(nmax, dtype=torch.int32, device=dev)
         st = gc.new_status(dev)
         cbase, dbase, tbase = idx.ctrl.data_ptr(), idx.data.data_ptr(), idx.tiles.data_ptr()
-        cb_total, dw_total = idx.ctrl.numel(), idx.data.numel()
         s = torch.cuda.current_stream().cuda_stream
         calls = []
         for i in ids.tolist():
             d = lists[i]
+            # gc_decode indexes a single list's records from tile 0; the pool
+            # holds them from tile 1 (tile 0's record is never read)
             tp = tbase + (int(d["tile_off"]) - 1) * gc.TILE_BYTES
-            calls.append((cbase + int(d["ctrl_off"]), cb_total - int(d["ctrl_off"]),
-                          dbase + 4 * int(d["data_off"]), dw_total - int(d["data_off"]), int(d["n"]), tp))
+            calls.append((cbase + int(d["ctrl_off"]), int(d["ctrl_bytes"]), dbase + 4 * int(d["data_off"]),
+                          int(d["data_words"]), int(d["n"]), tp))
         cp = ctypes.byref(idx.codec)
 
         def run():

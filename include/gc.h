@@ -75,54 +75,101 @@ typedef struct gc_codec {
  * first row. lane_bit: first bit of the unit in every lane stream; ctrl_bit:
  * first control bit of the unit; exc_off: Group-PFD, byte offset of the
  * unit's exception record from the start of the exception records (0 for
- * other codecs); row_skip: rows of the unit before the tile. Tile 0 of any
- * list is all zeros. The paper's format carries no tile records; the library
- * derives them from the control area (gc_build_tiles). 24 bytes. */
+ * other codecs); row_skip: rows of the unit before the tile.
+ *
+ * A record may also carry a skip entry in the sense of Sec 7.5 (the index
+ * keeps a docID every so many postings): base is the docID just before the
+ * tile, i.e. the sum of the list's gaps before the tile modulo 2^32, valid
+ * when flags has GC_TILE_BASE. A tile with a base decodes without waiting
+ * for the tiles before it; one without a base takes its prefix from them
+ * by look-back. The GPU encoders write bases; a tile index built from the
+ * control area alone (gc_build_tiles, the paper's format) has none. Tile 0
+ * of any list is (0, 0, 0, 0, base 0, GC_TILE_BASE). 32 bytes. */
 typedef struct gc_tile {
   uint64_t lane_bit;
   uint64_t ctrl_bit;
   uint32_t exc_off;
   uint32_t row_skip;
+  uint32_t base;
+  uint32_t flags;
 } gc_tile;
 
-/* One posting list in a batch (32 bytes). ctrl_off: byte offset of its
+enum { GC_TILE_BASE = 1u };
+
+/* One posting list in a batch (40 bytes). ctrl_off: byte offset of its
  * control area in the control pool; data_off: word offset of its data area
  * in the data pool (the data of every list starts on a vector boundary,
  * i.e. data_off is a multiple of k); out_off: index of its first output int;
  * n: ints in the list; tile_off: index in the tile pool of the record of its
- * tile 1 (lists of one tile need no record). */
+ * tile 1 (lists of one tile need no record); ctrl_bytes, data_words: the
+ * sizes of its two areas. */
 typedef struct gc_list {
   uint64_t ctrl_off;
   uint64_t data_off;
   uint64_t out_off;
   uint32_t n;
   uint32_t tile_off;
+  uint32_t ctrl_bytes;
+  uint32_t data_words;
 } gc_list;
 
-/* One unit of work of the batched decoder: tile `tile` of list `list`,
- * with the list's descriptor and the tile's record copied in, so that a
- * warp starts a tile with one 64-byte load (64 bytes, 16-byte aligned).
- * gc_plan_batch writes them; list = 0xffffffff marks an empty slot. */
+/* One unit of work of the decoder: one tile of one list, with what a warp
+ * needs to stage the tile's streams in shared memory and decode it (64
+ * bytes, 16-byte aligned). gc_plan_batch writes them.
+ *   ctrl_at:  byte offset of the list's control area in the control pool.
+ *   data_at:  word offset in the data pool of the vector that holds the
+ *             tile's first row (a Group-AFOR frame may start rows earlier).
+ *   out_at:   index of the tile's first output int in the output pool.
+ *   ctrl_bit: first control bit of the tile's first unit, from ctrl_at.
+ *   ctrl_bytes: control bytes of the list.
+ *   tile:     tile index within the list.
+ *   list:     list index; 0xffffffff marks an empty record.
+ *   base:     docID just before the tile (GC_WORK_HAS_BASE).
+ *   exc_at:   Group-PFD: first byte of the tile's exception records, from
+ *             ctrl_at.
+ *   win_at, win_len: the control bytes to stage, from ctrl_at (win_at may
+ *             be negative: the window starts on a 16-byte boundary of the
+ *             pool); win_len is a multiple of 16.
+ *   shape:    GC_WORK_* fields below.
+ *   exc_len:  Group-PFD exception bytes to stage, from exc_at rounded down
+ *             to a 16-byte boundary of the pool; a multiple of 16. */
 typedef struct gc_work {
-  uint64_t ctrl_off;
-  uint64_t data_off;
-  uint64_t out_off;
-  uint32_t n;
-  uint32_t tile;
-  uint64_t lane_bit;
+  uint64_t ctrl_at;
+  uint64_t data_at;
+  uint64_t out_at;
   uint64_t ctrl_bit;
-  uint32_t exc_off;
-  uint32_t row_skip;
+  uint32_t ctrl_bytes;
+  uint32_t tile;
   uint32_t list;
-  uint32_t reserved;
+  uint32_t base;
+  uint32_t exc_at;
+  int32_t win_at;
+  uint32_t shape;
+  uint16_t win_len;
+  uint16_t exc_len;
 } gc_work;
 
-/* Launch shape of the persistent decoders (NULL = the library default).
- * warps_per_block: 1..16 (default 8); blocks_per_sm: resident blocks per
- * SM to launch (0 = as many as fit); the persistent grid is blocks_per_sm *
- * SMs. items_per_claim: 1..64 tiles a warp takes from the shared queue per
- * atomic (0 = default 4); consecutive tiles of one list in a claim pass
- * their prefix sum in registers. */
+/* gc_work.shape: bits 0-9 the tile's ints minus one; 10-18 data vectors
+ * (k words each) to stage from data_at; 19-23 the lane bit of the tile's
+ * first row within the first staged word; 24-28 rows of the tile's first
+ * unit before the tile; bit 29 base is valid; bit 30 a later tile without
+ * a base takes its prefix from this tile. */
+enum {
+  GC_WORK_VEC_SHIFT = 10,
+  GC_WORK_BIT_SHIFT = 19,
+  GC_WORK_SKIP_SHIFT = 24,
+  GC_WORK_HAS_BASE = 1u << 29,
+  GC_WORK_PUBLISH = 1u << 30
+};
+
+/* Launch shape of the persistent decoder (NULL = the library default).
+ * warps_per_block: 1..16 (default 4; lowered to what one block's shared
+ * memory holds, about 15 KB a warp); blocks_per_sm: resident blocks per SM
+ * to launch (0 = as many as fit); the persistent grid is blocks_per_sm *
+ * SMs. items_per_claim: 1..32 tiles a warp takes from the shared counter
+ * per atomic (0 = default 8). A plan with tiles that take their prefix by
+ * look-back is claimed one tile at a time whatever this says, so that the
+ * tiles a warp holds never delay the tiles after them for long. */
 typedef struct gc_launch {
   uint32_t warps_per_block;
   uint32_t blocks_per_sm;
@@ -155,7 +202,7 @@ gc_status gc_encode_scratch_size(const gc_codec* codec, uint64_t n, uint64_t* by
  *     least gc_max_encoded_size; d_ctrl must be 4-byte aligned, d_data
  *     16-byte aligned.
  *   d_tiles: NULL, or gc_max_encoded_size's ntiles records to receive the
- *     tile index.
+ *     tile index, every record with its base (GC_TILE_BASE).
  *   d_sizes: two uint64 on the device, receive (control bytes, data words).
  * Asynchronous on `stream`. */
 gc_status gc_encode(const gc_codec* codec, const uint32_t* d_gaps, uint64_t n, uint8_t* d_ctrl,
@@ -165,8 +212,8 @@ gc_status gc_encode(const gc_codec* codec, const uint32_t* d_gaps, uint64_t n, u
 /* Encode many lists at once (an index). h_n[i] ints of list i start at
  * h_in_off[i] of d_gaps. The library lays the lists out back to back and
  * writes, on the device: d_lists (one gc_list per list), d_ctrl, d_data,
- * d_tiles (tile records of tiles >= 1), and d_totals = (control bytes, data
- * words, tile records). Capacities are checked on the host from the
+ * d_tiles (tile records of tiles >= 1, with bases), and d_totals = (control
+ * bytes, data words, tile records). Capacities are checked on the host from the
  * gc_max_encoded_size bounds of each list. */
 gc_status gc_encode_batch_scratch_size(const gc_codec* codec, const uint32_t* h_n, uint64_t nlists,
                                        uint64_t* bytes);
@@ -185,7 +232,7 @@ gc_status gc_decode_scratch_size(const gc_codec* codec, uint64_t n, int have_til
 
 /* Build the tile index of one encoded list from its control area alone
  * (one pass over control bytes, no data read). d_tiles receives
- * gc_max_encoded_size's ntiles records. */
+ * gc_max_encoded_size's ntiles records; none but tile 0 carries a base. */
 gc_status gc_build_tiles(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes,
                          uint64_t n, gc_tile* d_tiles, void* d_scratch, uint64_t scratch_bytes,
                          uint32_t* d_status, void* stream);
@@ -194,11 +241,15 @@ gc_status gc_build_tiles(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t 
  * and, when restore_docids != 0, restore docIDs with the inclusive prefix
  * sum of the gaps modulo 2^32 (Sec 2.1.1) in the same kernel.
  *   d_ctrl / ctrl_bytes, d_data / data_words: the list's areas; d_data
- *     16-byte aligned.
- *   d_tiles: the list's tile index, or NULL to build it into scratch first.
+ *     16-byte aligned. Control bytes are staged from the 16-byte boundary
+ *     at or below d_ctrl, inside the allocation that holds d_ctrl.
+ *   d_tiles: the list's tile index (as written by gc_encode or
+ *     gc_build_tiles), or NULL to build it into scratch first.
  *   d_out: n uint32.
- * One launch decodes every tile; tiles chain their prefix sums with a
- * bounded decoupled look-back. */
+ * One launch decodes every tile: a plan of the list's tiles is built in
+ * scratch, then the decoder of gc_decode_plan runs it. Tiles whose records
+ * carry a base (GC_TILE_BASE) start from it; the others chain their prefix
+ * sums to the tiles before them with a bounded decoupled look-back. */
 gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes,
                     const uint32_t* d_data, uint64_t data_words, uint64_t n, const gc_tile* d_tiles,
                     uint32_t* d_out, int restore_docids, void* d_scratch, uint64_t scratch_bytes,
@@ -208,34 +259,46 @@ gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_
  * 4-byte words | control area | zero padding to 16 bytes | data area.
  * gc_decode_paper reads the offset from the head of the buffer (a device
  * buffer: the offset is copied to the host, so this call synchronises
- * `stream` once) and decodes as gc_decode with no tile index. */
+ * `stream` once) and decodes as gc_decode with no tile index. d_buf must be
+ * 16-byte aligned. */
 gc_status gc_decode_paper(const gc_codec* codec, const uint8_t* d_buf, uint64_t buf_bytes,
                           uint64_t n, uint32_t* d_out, int restore_docids, void* d_scratch,
                           uint64_t scratch_bytes, uint32_t* d_status, void* stream);
 
-/* The work plan of a batch (one gc_work per tile of every list, list by
- * list, a list's tiles in order), built on the device from the descriptors
- * and the tile pool. A plan depends only on the index, so a caller that
- * decodes the same resident index many times builds it once.
- *   d_lists / nlists, d_tile_pool / tile_pool_len: as for gc_decode_batch.
+/* The work plan of a batch: one gc_work per tile of every list, a list's
+ * tiles in order at consecutive records, built on the device from the
+ * descriptors, the tile pool and the control pool (read only where a
+ * Group-AFOR frame straddles two tiles). A plan depends only on the index,
+ * so a caller that decodes the same resident index many times builds it
+ * once.
+ *   d_lists / nlists, d_tile_pool / tile_pool_len, d_ctrl_pool /
+ *     ctrl_pool_bytes: as for gc_decode_batch.
  *   d_work / work_cap: output records (16-byte aligned). A batch with more
  *     tiles reports GC_ERR_NOSPACE in d_status.
- *   d_count: one uint64 on the device, receives the number of tiles.
- * Asynchronous on `stream`; graph-capturable. */
+ *   d_count: two uint64 on the device, receive the number of tiles and the
+ *     number of tiles that have no base and take their prefix by look-back.
+ * A descriptor or tile record that points outside its list reports
+ * GC_ERR_CORRUPT (the record is emptied). Asynchronous on `stream`;
+ * graph-capturable. */
 gc_status gc_plan_batch(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists,
-                        const gc_tile* d_tile_pool, uint64_t tile_pool_len, gc_work* d_work,
-                        uint64_t work_cap, uint64_t* d_count, uint32_t* d_status, void* stream);
+                        const gc_tile* d_tile_pool, uint64_t tile_pool_len, const uint8_t* d_ctrl_pool,
+                        uint64_t ctrl_pool_bytes, gc_work* d_work, uint64_t work_cap, uint64_t* d_count,
+                        uint32_t* d_status, void* stream);
 
 /* Scratch bytes gc_decode_plan needs for a plan of up to work_cap tiles. */
 gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes);
 
 /* Decode every tile of a plan in one persistent launch (Sec 4.3, 5.2.3,
- * 6.2 decoding per tile; docIDs by Sec 2.1.1 when restore_docids != 0,
- * chained across the tiles of a list by look-back). Warps claim tiles from
- * a shared counter in plan order. The pools are those the plan's records
- * point into; every read is bounds-checked against these sizes, and a
- * record whose list does not fit out_pool_len reports GC_ERR_INVALID.
- * Asynchronous on `stream`; graph-capturable (two memsets and one kernel). */
+ * 6.2 decoding per tile; docIDs by Sec 2.1.1 when restore_docids != 0).
+ * Each warp claims tiles from a shared counter in plan order, copies their
+ * control and data bytes into a shared-memory ring with bulk asynchronous
+ * copies several tiles ahead, and decodes up to 32 rows of 32 ints at a
+ * time (several small tiles together). A tile with a base starts from it;
+ * one without takes its prefix from the tiles before it by a bounded
+ * decoupled look-back. The pools are those the plan's records point into
+ * (16-byte aligned); every read is bounds-checked against these sizes, and
+ * a record whose tile does not fit out_pool_len reports GC_ERR_INVALID.
+ * Asynchronous on `stream`; graph-capturable (memsets and one kernel). */
 gc_status gc_decode_plan(const gc_codec* codec, const gc_work* d_work, const uint64_t* d_count,
                          uint64_t work_cap, const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
                          const uint32_t* d_data_pool, uint64_t data_pool_words, uint32_t* d_out_pool,
@@ -246,13 +309,12 @@ gc_status gc_decode_plan(const gc_codec* codec, const gc_work* d_work, const uin
  * (the sum over its lists of gc_max_encoded_size's ntiles). */
 gc_status gc_decode_batch_scratch_size(uint64_t nlists, uint64_t max_tiles, uint64_t* bytes);
 
-/* Decode many lists in one persistent launch: gc_plan_batch into scratch,
- * then gc_decode_plan. Warps claim 1024-int tiles of all lists from a
- * shared queue; tiles of one list chain their prefix sums by look-back.
+/* Decode many lists in one call: gc_plan_batch into scratch, then
+ * gc_decode_plan.
  *   d_lists: nlists descriptors on the device (see gc_list).
  *   d_ctrl_pool / ctrl_pool_bytes, d_data_pool / data_pool_words,
- *   d_tile_pool / tile_pool_len: the index areas; every read is
- *     bounds-checked against these sizes.
+ *   d_tile_pool / tile_pool_len: the index areas (control and data pools
+ *     16-byte aligned); every read is bounds-checked against these sizes.
  *   d_out_pool / out_pool_len: outputs; list i goes to out_off.
  *   max_tiles: the scratch was sized for this many tiles; a batch with more
  *     reports GC_ERR_NOSPACE in d_status.

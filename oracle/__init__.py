@@ -31,7 +31,7 @@ LD_BINARY, LD_CU, LD_IU = 0, 1, 2
 OK, ERR_INVALID, ERR_NOSPACE, ERR_CORRUPT = 0, 1, 2, 3
 
 TILE_DTYPE = np.dtype([("lane_bit", "<u8"), ("ctrl_bit", "<u8"), ("exc_off", "<u4"),
-                       ("row_skip", "<u4")])
+                       ("row_skip", "<u4"), ("base", "<u4"), ("flags", "<u4")])
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -83,6 +83,8 @@ def _load():
             lib.orc_tile_count.argtypes = [_U64, _U32]
             lib.orc_tile_count.restype = _U64
             lib.orc_tile_index.argtypes = [_U32, _U32, _U32, _U32, _u8p, _U64, _U64, ctypes.c_void_p]
+            lib.orc_tile_bases.argtypes = [_u32p, _U64, _U32, ctypes.c_void_p]
+            lib.orc_tile_bases.restype = None
             _lib = lib
     return _lib
 
@@ -272,8 +274,10 @@ def paper_pack(ctrl, data) -> np.ndarray:
     return buf
 
 
-def tile_index(codec: Codec, ctrl, n: int) -> np.ndarray:
-    """Per 1024-int tile: where its first unit starts (see gc_oracle.c)."""
+def tile_index(codec: Codec, ctrl, n: int, gaps=None) -> np.ndarray:
+    """Per 1024-int tile: where its first unit starts (see gc_oracle.c). With
+    the list's gaps, every record also gets its skip entry (the docID before
+    the tile, Sections 2.1.1 and 7.5); without them only tile 0 has one."""
     lib = _load()
     nt = lib.orc_tile_count(n, codec.k)
     out = np.zeros(nt, TILE_DTYPE)
@@ -284,6 +288,11 @@ def tile_index(codec: Codec, ctrl, n: int) -> np.ndarray:
                                 out.ctypes.data_as(ctypes.c_void_p))
         if st:
             raise OracleError(st, "tile_index")
+        if gaps is not None:
+            g = _u32(gaps)
+            if len(g) != n:
+                raise ValueError("gaps must hold the list's n ints")
+            lib.orc_tile_bases(_p(g, _u32p), n, codec.k, out.ctypes.data_as(ctypes.c_void_p))
     return out
 
 

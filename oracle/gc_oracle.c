@@ -712,13 +712,20 @@ uint64_t orc_paper_pack(const uint8_t* ctrl, uint64_t cb, const uint32_t* data, 
  * Group-Simple selector, a Group-Scheme row, an AFOR or PFD frame) that holds
  * that row, given by its first lane bit, its first control bit, the PFD
  * exception byte offset of its frame (from the start of the exception
- * records), and how many of its rows precede the tile. One record of 24
- * bytes per tile: u64 lane_bit, u64 ctrl_bit, u32 exc_off, u32 row_skip. */
+ * records), and how many of its rows precede the tile. A record may also
+ * hold a skip entry in the sense of Sec 7.5: base, the docID just before
+ * the tile, valid when flags is 1. One record of 32 bytes per tile: u64
+ * lane_bit, u64 ctrl_bit, u32 exc_off, u32 row_skip, u32 base, u32 flags.
+ * orc_tile_index fills the positions from the control area alone, which
+ * gives no base but the first (the docID before the list is 0);
+ * orc_tile_bases adds every base from the gaps. */
 typedef struct {
   uint64_t lane_bit;
   uint64_t ctrl_bit;
   uint32_t exc_off;
   uint32_t row_skip;
+  uint32_t base;
+  uint32_t flags;
 } orc_tile;
 
 uint64_t orc_tile_count(uint64_t n, uint32_t k) {
@@ -791,6 +798,8 @@ int orc_tile_index(uint32_t kind, uint32_t k, uint32_t cg, uint32_t ld, const ui
       tiles[t].ctrl_bit = cstart;
       tiles[t].exc_off = (uint32_t)xoff;
       tiles[t].row_skip = (uint32_t)(t * tr - row);
+      tiles[t].base = 0;
+      tiles[t].flags = t == 0 ? 1u : 0u;
       ++t;
     }
     row += rows;
@@ -802,4 +811,18 @@ int orc_tile_index(uint32_t kind, uint32_t k, uint32_t cg, uint32_t ld, const ui
   }
   free(units);
   return ORC_OK;
+}
+
+/* Skip entries: the docID before tile t is the prefix sum of Sec 2.1.1 up
+ * to int t*1024 - 1, i.e. the sum of the gaps before the tile modulo 2^32
+ * (0 for tile 0). Sets base and flags = 1 in each of the nt records. */
+void orc_tile_bases(const uint32_t* gaps, uint64_t n, uint32_t k, orc_tile* tiles) {
+  const uint64_t nt = orc_tile_count(n, k);
+  uint32_t sum = 0;
+  uint64_t i = 0;
+  for (uint64_t t = 0; t < nt; ++t) {
+    for (; i < t * TILE_INTS; ++i) sum += gaps[i];
+    tiles[t].base = sum;
+    tiles[t].flags = 1u;
+  }
 }

@@ -1,21 +1,27 @@
-// gc_decode.cu -- decoding kernels of the Group-codec library.
+// gc_decode.cu -- the decoder of the Group-codec library.
 //
-// One warp decodes one tile of 1024 ints (1024/k rows) of one list:
-//   1. parse the tile's control patterns into a per-row table (lane-bit
-//      offset, bit width): Group-Simple selectors (Table III, Sec 4.3),
-//      Group-Scheme length descriptors (Eq. 2; binary, complete unary and
-//      incomplete unary, Sec 5.2.1 and 5.3.1), Group-AFOR frame bytes
-//      (Sec 6.1), Group-PFD frame headers (Sec 6.2 decoding Step 1);
-//   2. extract every int with a funnel shift from its lane's stream (the
-//      k-way vertical layout: at k = 32 a warp reads one 128-byte vector per
-//      row, fully coalesced);
-//   3. Group-PFD: write the frame's exceptions over their slots (Step 3);
-//   4. optionally restore docIDs (Sec 2.1.1): per-lane sequential sums, a
-//      warp scan, and a decoupled look-back across the tiles of the list
-//      (bounded waits: a wait that runs out reports GC_ERR_TIMEOUT);
-//   5. store the 1024 ints with coalesced 128-byte stores.
-// Warps claim tiles in increasing order from a global counter, so the tile
-// a warp waits on has always been claimed by a running warp.
+// Decoding runs a plan: one 64-byte record (gc_work) per 1024-int tile of
+// every list, giving the unit that holds the tile's first row and the exact
+// byte ranges of the tile's control and data streams. The persistent
+// kernel's warps work independently. Each warp
+//   1. claims records from a shared counter and keeps them in shared memory;
+//   2. stages every claimed tile's data vectors, control window and
+//      (Group-PFD) exception records in its own shared-memory ring with bulk
+//      asynchronous copies (cp.async.bulk, one mbarrier per tile), up to 16
+//      tiles ahead of the one it decodes;
+//   3. decodes a pack of up to 32 lines of 32 consecutive ints (one full
+//      tile, or several small tiles together): the control patterns become
+//      one (word, shift, width) entry per row -- Table III selectors
+//      (Sec 4.3), Eq. 2 length descriptors (Sec 5.2.3, 5.3.1), AFOR frame
+//      bytes (Sec 6.1), PFD frame headers (Sec 6.2 decoding Step 1) -- then
+//      lane l extracts the 32 ints of line l with funnel shifts, in a
+//      rotated column order that keeps shared-memory banks apart, patches
+//      Group-PFD exceptions over their slots (Step 3) and sums them;
+//   4. restores docIDs (Sec 2.1.1): a segmented warp scan joins the line
+//      sums of each tile, and a tile starts from its base (a skip entry of
+//      the index) or, without one, from the tiles before it by a bounded
+//      decoupled look-back;
+//   5. transposes the ints through shared memory and stores 128-byte rows.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -28,36 +34,42 @@ constexpr unsigned long long kFlagAgg = 1ull << 32;
 constexpr unsigned long long kFlagPrefix = 2ull << 32;
 constexpr uint32_t kSpinLimit = 1u << 22;  // ~0.5 s of polling
 
+constexpr int kRing = 8192;     // staging ring bytes per warp
+constexpr int kSeq = 32;        // claimed records kept per warp
+constexpr int kFly = 16;        // tiles staged at once per warp (one mbarrier each)
+constexpr int kCtrlCap = 512;   // control bytes staged per tile at most
+constexpr int kExcCap = 1024;   // exception bytes staged per tile (all or none)
+
 template <int K>
-struct __align__(16) WarpSmem {
-  static constexpr int TR = kTileInts / K;  // rows per tile
-  static constexpr int FPT = TR / 32;       // PFD frames per tile
-  // the tile's data words, staged (TR rows of at most 32 bits per lane and
-  // a start offset below 32 span at most TR + 1 words per lane)
-  static constexpr int DW = (TR + 1) * K;
-  uint32_t d[DW];
-  uint32_t outs[kTileInts + kTileInts / 32];  // padded: int i at i + i/32
-  uint64_t fx[FPT];                           // PFD: byte offset of each frame's exception record
-  uint32_t rb[TR];                            // lane-bit offset of each row (from the tile's unit)
-  uint32_t fe[FPT], fw[FPT], fr[FPT];         // PFD: exceptions, width code, rows of each frame
-  uint8_t rw[TR];                             // bit width of each row
+struct Geo {
+  static constexpr int TR = kTileInts / K;   // rows per tile
+  static constexpr int RPL = 32 / K;         // rows per 32-int line (K = 4: 8, K = 32: 1)
+  static constexpr int PROWS = 32 * RPL;     // row entries of a pack
+  static constexpr int MAXVEC = TR + 1;      // data vectors a tile spans at most
 };
 
-struct ListRef {
-  const uint8_t* ctrl;
-  uint64_t ctrl_bytes;
-  const uint32_t* data;
-  uint64_t data_words;
-  uint32_t* out;
-  uint64_t n;
+template <int K>
+struct __align__(128) WarpSmem {
+  uint8_t ring[kRing];                   // staged tiles (data 128-byte aligned)
+  uint32_t tb[32 * 32];                  // line-major transpose buffer
+  uint4 rec[kSeq][4];                    // claimed records
+  unsigned long long mbar[kFly];
+  uint32_t item[kSeq];                   // plan index of each claimed record
+  uint32_t at[kFly];                     // ring offset of each staged tile
+  uint32_t end[kFly];                    // ring position after its allocation
+  uint16_t cst[kFly], xst[kFly];         // control / exception bytes staged
+  uint32_t rw[Geo<K>::PROWS];            // row: ring word of its first word (lane 0)
+  uint32_t rs[Geo<K>::PROWS];            // row: shift | width << 8
+  uint32_t xm[32];                       // line: Group-PFD exception slots
+  uint32_t xw[32];                       // line: exception value bytes
+  unsigned long long xv[32];             // line: generic address of its frame's values
+  unsigned long long lout[32];           // line: output index of its first int
+  uint32_t lnv[32];                      // line: ints it holds
 };
 
 struct DecodeArgs {
-  ListRef one;  // single-list launch
-  const gc_tile* one_tiles;
-  uint64_t one_ntiles;
-  const gc_work* work;  // batched launch: one record per tile
-  const unsigned long long* work_count;
+  const gc_work* work;
+  const unsigned long long* count;  // [0] records, [1] records that need look-back
   uint64_t work_cap;
   const uint8_t* ctrl_pool;
   uint64_t ctrl_pool_bytes;
@@ -65,54 +77,148 @@ struct DecodeArgs {
   uint64_t data_pool_words;
   uint32_t* out_pool;
   uint64_t out_pool_len;
-  uint32_t* counters;       // [0] claim counter
-  unsigned long long* lb;   // look-back word per work item
+  uint32_t* counter;        // claim counter (zeroed before the launch)
+  unsigned long long* lb;   // look-back word per record (zeroed when restoring)
   uint32_t cg, ld;
-  uint32_t claim;           // work items per claim
-  int restore;
+  uint32_t claim;           // records per claim when no record needs look-back
   uint32_t* status;
 };
 
-__device__ __forceinline__ uint32_t pad_idx(uint32_t i) { return i + (i >> 5); }
+// ------------------------------------------------------------- async copy
 
-// ---------------------------------------------------------------- parse
-// Each parser fills rb[0..rows) and rw[0..rows) for rows row0.. of the list,
-// starting from the tile record `rec`. Returns false on a malformed stream.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// ------------------------------------------------------------ control view
+
+// The control bytes of one list, as the parsers see them: byte `off` (from
+// the list's control area) comes from the staged control window, the staged
+// exception window or global memory, and past the list's end reads `fill`.
+struct CtrlView {
+  const uint8_t* g;
+  uint64_t size;
+  const uint8_t* s1;  // staged control window
+  int64_t lo1;
+  uint32_t len1;
+  const uint8_t* s2;  // staged exception window
+  int64_t lo2;
+  uint32_t len2;
+
+  __device__ __forceinline__ uint32_t byte(uint64_t off, uint32_t fill) const {
+    if (off >= size) return fill;
+    uint64_t r = off - (uint64_t)lo1;
+    if (r < len1) return s1[r];
+    r = off - (uint64_t)lo2;
+    if (r < len2) return s2[r];
+    return __ldg(g + off);
+  }
+  // little-endian read of nb (1..4) bytes
+  __device__ __forceinline__ uint32_t le(uint64_t off, uint32_t nb, uint32_t fill = 0) const {
+    uint32_t v = 0;
+    for (uint32_t t = 0; t < nb; ++t) v |= byte(off + t, fill) << (8 * t);
+    return v;
+  }
+  __device__ __forceinline__ uint32_t bits(uint64_t pos, uint32_t width) const {
+    return (le(pos >> 3, 4) >> (pos & 7)) & low_mask(width);
+  }
+  // generic address of bytes [off, off + n) (in a staged window when all
+  // of them are there, else in global memory; the caller keeps them inside
+  // the list)
+  __device__ __forceinline__ const uint8_t* addr(uint64_t off, uint64_t n) const {
+    uint64_t r = off - (uint64_t)lo2;
+    if (r < len2 && r + n <= len2) return s2 + r;
+    r = off - (uint64_t)lo1;
+    if (r < len1 && r + n <= len1) return s1 + r;
+    return g + off;
+  }
+};
+
+// Where a parser puts row q of the tile: the ring word of the row's first
+// word in lane 0's stream, and (shift, width). A row that would run past the
+// staged data vectors is an error (its width becomes 0).
 template <int K>
-__device__ bool parse_simple(const ListRef& L, const gc_tile& rec, uint64_t row0, uint32_t rows,
-                             WarpSmem<K>& ws) {
+struct RowSink {
+  uint32_t* rw;
+  uint32_t* rs;
+  uint32_t word0;     // ring word of the tile's first staged word
+  uint32_t bit0;      // lane bit of the tile's first unit in that word
+  uint32_t vec_bits;  // 32 * staged vectors
+
+  __device__ __forceinline__ void put(uint32_t q, uint32_t rb, uint32_t w, bool& ok) const {
+    const uint32_t b = bit0 + rb;
+    if (b + w > vec_bits) {
+      ok = false;
+      rw[q] = word0;
+      rs[q] = 0;
+      return;
+    }
+    rw[q] = word0 + (b >> 5) * K;
+    rs[q] = (b & 31u) | (w << 8);
+  }
+};
+
+// ---------------------------------------------------------------- parsers
+// Each fills rows 0..rows-1 of the tile (tile-relative) and returns false
+// (in every lane) for a malformed stream.
+
+// Table III selectors, 4 bits each, low nibble first; selector u holds NUM
+// rows of BW bits in one 32-bit word of every lane (Sec 4.1.1, 4.3).
+template <int K>
+__device__ bool parse_simple(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip, uint32_t rows,
+                             const RowSink<K>& out) {
   const uint32_t lane = lane_id();
-  const uint64_t u0 = rec.ctrl_bit >> 2;
-  const uint64_t tile_end = row0 + rows;
-  uint64_t cov = row0 - rec.row_skip;  // first row of the next unit to read
+  const uint64_t u0 = ctrl_bit >> 2;
+  int32_t cov = -(int32_t)skip;  // first row (tile-relative) of the next selector
   bool ok = true;
-  for (uint32_t c = 0; cov < tile_end; c += 32) {
+  for (uint32_t c = 0; cov < (int32_t)rows; c += 32) {
     const uint64_t u = u0 + c + lane;
-    uint32_t sel = 15;
-    if ((u >> 1) < L.ctrl_bytes) sel = (__ldg(L.ctrl + (u >> 1)) >> ((u & 1) * 4)) & 15u;
+    const uint32_t sel = (C.byte(u >> 1, 0xffu) >> ((u & 1) * 4)) & 15u;
     const bool bad = sel > 9;
     const uint32_t num = bad ? 32u : sel_num(sel);
     const uint32_t bw = bad ? 0u : sel_bw(sel);
     const uint32_t incl = warp_incl_sum(num);
-    const uint64_t start = cov + incl - num;
-    if (start < tile_end) {
+    const int32_t start = cov + (int32_t)(incl - num);
+    if (start < (int32_t)rows) {
       if (bad) ok = false;
-      const uint64_t a = start > row0 ? start : row0;
-      const uint64_t b = (start + num) < tile_end ? (start + num) : tile_end;
-      for (uint64_t q = a; q < b; ++q) {
-        ws.rb[q - row0] = 32u * (c + lane) + (uint32_t)(q - start) * bw;
-        ws.rw[q - row0] = (uint8_t)bw;
-      }
+      const int32_t a = start > 0 ? start : 0;
+      const int32_t b = (start + (int32_t)num) < (int32_t)rows ? start + (int32_t)num : (int32_t)rows;
+      for (int32_t q = a; q < b; ++q) out.put((uint32_t)q, 32u * (c + lane) + (uint32_t)(q - start) * bw, bw, ok);
     }
-    cov += __shfl_sync(kFull, incl, 31);
+    cov += (int32_t)__shfl_sync(kFull, incl, 31);
   }
   return __all_sync(kFull, ok);
 }
 
+// Binary length descriptors at fixed positions (Sec 5.2.1(b)); the width of
+// row r is CG * (descriptor + 1) (Eq. 2).
 template <int K>
-__device__ bool parse_scheme_binary(const ListRef& L, uint64_t row0, uint32_t rows, uint32_t cg,
-                                    WarpSmem<K>& ws) {
+__device__ bool parse_scheme_binary(const CtrlView& C, uint64_t row0, uint32_t rows, uint32_t cg,
+                                    const RowSink<K>& out) {
   const uint32_t lane = lane_id();
   const uint32_t width = 5 - log2_cg(cg);
   const uint32_t maxu = 32 / cg;
@@ -123,16 +229,13 @@ __device__ bool parse_scheme_binary(const ListRef& L, uint64_t row0, uint32_t ro
     uint32_t bw = 0;
     if (q < rows) {
       const uint64_t pos = bin_ld_pos(row0 + q, cg);
-      if (((pos + width + 7) >> 3) > L.ctrl_bytes) ok = false;
-      const uint32_t u = read_ctrl_bits(L.ctrl, L.ctrl_bytes, pos, width) + 1;
+      if (((pos + width + 7) >> 3) > C.size) ok = false;
+      const uint32_t u = C.bits(pos, width) + 1;
       if (u > maxu) ok = false;
       bw = cg * u;
     }
     const uint32_t incl = warp_incl_sum(bw);
-    if (q < rows) {
-      ws.rb[q] = carry + incl - bw;
-      ws.rw[q] = (uint8_t)bw;
-    }
+    if (q < rows) out.put(q, carry + incl - bw, bw, ok);
     carry += __shfl_sync(kFull, incl, 31);
   }
   return __all_sync(kFull, ok);
@@ -143,22 +246,34 @@ __device__ bool parse_scheme_binary(const ListRef& L, uint64_t row0, uint32_t ro
 // closes one descriptor. CU: a descriptor starts right after the previous
 // zero (possibly in an earlier window). IU: descriptors never straddle a
 // byte, so one starts after the previous zero of its byte or at the byte's
-// first bit; trailing ones of a byte are padding.
+// first bit; trailing ones of a byte are padding. While the windows lie in
+// the staged control bytes only those are read; past them, 32 at a time.
 template <int K>
-__device__ bool parse_scheme_unary(const ListRef& L, const gc_tile& rec, uint32_t rows, uint32_t cg,
-                                   bool iu, WarpSmem<K>& ws) {
+__device__ bool parse_scheme_unary(const CtrlView& C, uint64_t P0, uint32_t rows, uint32_t cg, bool iu,
+                                   const RowSink<K>& out) {
   const uint32_t lane = lane_id();
-  const uint64_t P0 = rec.ctrl_bit;
   const uint64_t A = P0 & ~7ull;
   const uint32_t maxu = 32 / cg;
+  // staged windows from A on (the staged range ends at lo1 + len1)
+  const int64_t sh_end = C.lo1 + (int64_t)C.len1;
   uint32_t found = 0, ubase = 0;
   int64_t prev_last = (int64_t)P0 - 1;  // last zero before the current window group
   bool ok = true;
-  for (uint64_t w = 0; found < rows; w += 32) {
+  for (uint64_t w = 0; found < rows;) {
+    const uint64_t gbyte = (A >> 3) + 4 * w;  // first byte of this window group
+    if (gbyte >= C.size) {
+      ok = false;  // ran off the control area
+      break;
+    }
+    uint32_t lim = 32;
+    if ((int64_t)gbyte < sh_end && (int64_t)gbyte >= C.lo1) {
+      const uint64_t nst = ((uint64_t)(sh_end - (int64_t)gbyte) + 3) / 4;
+      lim = nst < 32 ? (uint32_t)nst : 32u;
+    }
+    const bool act = lane < lim;
     const uint64_t wbit = A + 32 * (w + lane);
-    if ((A >> 3) + 4 * w >= L.ctrl_bytes) { ok = false; break; }  // ran off the control area
-    uint32_t win = read_le(L.ctrl, L.ctrl_bytes, wbit >> 3, 4, 0xffu);
-    if (wbit < P0) win |= (1u << (uint32_t)(P0 - wbit)) - 1u;
+    uint32_t win = act ? C.le(wbit >> 3, 4, 0xffu) : 0xffffffffu;
+    if (act && wbit < P0) win |= (1u << (uint32_t)(P0 - wbit)) - 1u;
     const uint32_t zeros = ~win;
     const uint32_t nz = __popc(zeros);
     const int64_t lastz = nz ? (int64_t)(wbit + 31 - __clz(zeros)) : INT64_MIN;
@@ -201,8 +316,7 @@ __device__ bool parse_scheme_unary(const ListRef& L, const gc_tile& rec, uint32_
         }
         const uint32_t u = (uint32_t)(p - start + 1);
         if (u > maxu) ok = false;
-        ws.rb[q] = cg * ub;
-        ws.rw[q] = (uint8_t)(cg * u);
+        out.put(q, cg * ub, cg * u, ok);
         ub += u;
         ++q;
         pv = p;
@@ -212,113 +326,113 @@ __device__ bool parse_scheme_unary(const ListRef& L, const gc_tile& rec, uint32_
     ubase += __shfl_sync(kFull, incl_us, 31);
     const int64_t gl = __shfl_sync(kFull, incl_last, 31);
     if (gl > prev_last) prev_last = gl;
+    w += lim;
   }
   return __all_sync(kFull, ok);
 }
 
+// Group-AFOR frame bytes: (size code << 6) | b; a frame is 8 << code rows of
+// b bits in every lane (Sec 6.1). A frame may start before the tile; the
+// staged data starts at the tile's first row, so offsets are taken from
+// there (the frame's first `skip` rows, skip * b bits, are not staged).
 template <int K>
-__device__ bool parse_afor(const ListRef& L, const gc_tile& rec, uint64_t row0, uint32_t rows,
-                           WarpSmem<K>& ws) {
+__device__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip, uint32_t rows,
+                           const RowSink<K>& out) {
   const uint32_t lane = lane_id();
-  const uint64_t f0 = rec.ctrl_bit >> 3;
-  const uint64_t tile_end = row0 + rows;
-  uint64_t cov = row0 - rec.row_skip;
-  uint32_t lcarry = 0;
+  const uint64_t f0 = ctrl_bit >> 3;
+  int32_t cov = -(int32_t)skip;
+  const uint32_t b_first = C.byte(f0, 0xffu) & 63u;
+  uint32_t lcarry = 0u - skip * (b_first <= 32 ? b_first : 0u);
   bool ok = true;
-  for (uint32_t c = 0; cov < tile_end; c += 32) {
-    const uint64_t f = f0 + c + lane;
-    const uint32_t byte = f < L.ctrl_bytes ? (uint32_t)__ldg(L.ctrl + f) : 0xffu;
+  for (uint32_t c = 0; cov < (int32_t)rows; c += 32) {
+    const uint32_t byte = C.byte(f0 + c + lane, 0xffu);
     const uint32_t code = byte >> 6, b = byte & 63u;
     const bool bad = code > 2 || b > 32;
     const uint32_t F = bad ? 32u : (8u << code);
     const uint32_t lbits = bad ? 0u : F * b;
     const uint32_t inclF = warp_incl_sum(F);
     const uint32_t inclL = warp_incl_sum(lbits);
-    const uint64_t start = cov + inclF - F;
+    const int32_t start = cov + (int32_t)(inclF - F);
     const uint32_t lstart = lcarry + inclL - lbits;
-    if (start < tile_end) {
+    if (start < (int32_t)rows) {
       if (bad) ok = false;
-      const uint64_t a = start > row0 ? start : row0;
-      const uint64_t e = (start + F) < tile_end ? (start + F) : tile_end;
-      for (uint64_t q = a; q < e; ++q) {
-        ws.rb[q - row0] = lstart + (uint32_t)(q - start) * b;
-        ws.rw[q - row0] = (uint8_t)(bad ? 0 : b);
-      }
+      const int32_t a = start > 0 ? start : 0;
+      const int32_t e = (start + (int32_t)F) < (int32_t)rows ? start + (int32_t)F : (int32_t)rows;
+      for (int32_t q = a; q < e; ++q)
+        out.put((uint32_t)q, lstart + (uint32_t)(q - start) * (bad ? 0u : b), bad ? 0u : b, ok);
     }
-    cov += __shfl_sync(kFull, inclF, 31);
+    cov += (int32_t)__shfl_sync(kFull, inclF, 31);
     lcarry += __shfl_sync(kFull, inclL, 31);
   }
   return __all_sync(kFull, ok);
 }
 
-// Group-PFD decoding Step 1: per frame, the header (b, exception width, e).
-// The exception records follow the headers, frame after frame; the tile
-// record gives the offset of the tile's first frame's record.
+// Group-PFD decoding Step 1: per 32-row frame the header (b, exception
+// width code, exception count e); the frames' exception records follow the
+// headers of the whole list, frame after frame, and the tile's first one is
+// at exc_at. Rows go to the sink; every exception sets its slot's bit in the
+// mask of its line, and each line gets the address of its frame's values.
 template <int K>
-__device__ bool parse_pfd(const ListRef& L, const gc_tile& rec, uint64_t row0, uint32_t rows,
-                          uint64_t R, WarpSmem<K>& ws) {
-  constexpr int FPT = WarpSmem<K>::FPT;
+__device__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows, const RowSink<K>& out,
+                          WarpSmem<K>& ws, uint32_t line0, uint32_t nlines) {
   constexpr uint32_t pb = (kPfdFrameRows * K) <= 256 ? 1u : 2u;
+  constexpr uint32_t LPF = K;  // lines per frame (32 rows of K ints)
   const uint32_t lane = lane_id();
-  const uint64_t nf = (R + kPfdFrameRows - 1) / kPfdFrameRows;
-  const uint64_t f0 = row0 / kPfdFrameRows;
   const uint32_t nfr = (rows + kPfdFrameRows - 1) / kPfdFrameRows;
   bool ok = true;
   uint32_t b = 0, wcode = 0, e = 0, xb = 0, frows = 0;
-  if (lane < (uint32_t)FPT && lane < nfr) {
+  if (lane < nfr) {
     const uint64_t f = f0 + lane;
-    if (4 * f + 4 > L.ctrl_bytes) ok = false;
-    const uint32_t hdr = read_le(L.ctrl, L.ctrl_bytes, 4 * f, 4);
+    if (4 * f + 4 > C.size) ok = false;
+    const uint32_t hdr = C.le(4 * f, 4);
     b = hdr & 63u;
     wcode = (hdr >> 6) & 3u;
     e = hdr >> 8;
-    if (b > 32 || wcode > 2) { ok = false; b = 0; e = 0; }
-    frows = (uint32_t)((R - f * kPfdFrameRows) < kPfdFrameRows ? (R - f * kPfdFrameRows) : kPfdFrameRows);
-    if (e > frows * K) { ok = false; e = 0; }
+    if (b > 32 || wcode > 2) {
+      ok = false;
+      b = 0;
+      e = 0;
+      wcode = 0;
+    }
+    frows = rows - 32 * lane < 32 ? rows - 32 * lane : 32;
+    if (e > frows * K) {
+      ok = false;
+      e = 0;
+    }
     xb = e * (pb + (1u << wcode));
   }
   const uint32_t inclL = warp_incl_sum(32u * b);
   const uint32_t inclX = warp_incl_sum(xb);
-  if (lane < (uint32_t)FPT) {
-    ws.fx[lane] = 4 * nf + rec.exc_off + (inclX - xb);
-    ws.fe[lane] = e;
-    ws.fw[lane] = wcode;
-    ws.fr[lane] = frows;
-    if (e && ws.fx[lane] + xb > L.ctrl_bytes) ok = false;
-  }
   const uint32_t lstart = inclL - 32u * b;
-  // rows: frame fl = q / 32
+  const uint64_t xrec = exc_at + (inclX - xb);
+  if (lane < nfr && e && xrec + xb > C.size) {
+    ok = false;
+    e = 0;
+  }
   for (uint32_t fl = 0; fl < nfr; ++fl) {
     const uint32_t bf = __shfl_sync(kFull, b, fl);
     const uint32_t ls = __shfl_sync(kFull, lstart, fl);
     const uint32_t q = fl * 32 + lane;
-    if (q < rows) {
-      ws.rb[q] = ls + lane * bf;
-      ws.rw[q] = (uint8_t)bf;
-    }
+    if (q < rows) out.put(q, ls + lane * bf, bf, ok);
   }
-  return __all_sync(kFull, ok);
-}
-
-// Step 3: write each exception over its slot.
-template <int K>
-__device__ bool patch_pfd(const ListRef& L, uint32_t rows, uint32_t nints, WarpSmem<K>& ws) {
-  constexpr uint32_t pb = (kPfdFrameRows * K) <= 256 ? 1u : 2u;
-  const uint32_t lane = lane_id();
-  const uint32_t nfr = (rows + kPfdFrameRows - 1) / kPfdFrameRows;
-  bool ok = true;
   for (uint32_t fl = 0; fl < nfr; ++fl) {
-    const uint32_t e = ws.fe[fl];
-    if (e == 0) continue;
-    const uint32_t wb = 1u << ws.fw[fl];
-    const uint64_t base = ws.fx[fl];
-    const uint32_t lim = ws.fr[fl] * K;
-    for (uint32_t x = lane; x < e; x += 32) {
-      const uint32_t pos = read_le(L.ctrl, L.ctrl_bytes, base + (uint64_t)x * pb, pb);
-      const uint32_t val = read_le(L.ctrl, L.ctrl_bytes, base + (uint64_t)e * pb + (uint64_t)x * wb, wb);
-      const uint32_t i = fl * kPfdFrameRows * K + pos;
-      if (pos < lim && i < nints) ws.outs[pad_idx(i)] = val;
-      else if (pos >= lim) ok = false;
+    const uint32_t ef = __shfl_sync(kFull, e, fl);
+    const uint32_t lim = __shfl_sync(kFull, frows, fl) * K;
+    const uint64_t rec = __shfl_sync(kFull, xrec, fl);
+    const uint32_t wb = 1u << __shfl_sync(kFull, wcode, fl);
+    for (uint32_t x = lane; x < ef; x += 32) {
+      const uint32_t pos = C.le(rec + (uint64_t)x * pb, pb);
+      if (pos >= lim) {
+        ok = false;
+        continue;
+      }
+      const uint32_t i = fl * kPfdFrameRows * K + pos;  // tile-relative int
+      atomicOr(&ws.xm[line0 + (i >> 5)], 1u << (i & 31u));
+    }
+    const uint32_t ql = fl * LPF + lane;
+    if (lane < LPF && ql < nlines) {
+      ws.xv[line0 + ql] = (unsigned long long)C.addr(rec + (uint64_t)ef * pb, (uint64_t)ef * wb);
+      ws.xw[line0 + ql] = wb;
     }
   }
   return __all_sync(kFull, ok);
@@ -326,26 +440,22 @@ __device__ bool patch_pfd(const ListRef& L, uint32_t rows, uint32_t nints, WarpS
 
 // ------------------------------------------------------------ look-back
 
-// Decoupled look-back over the tiles of one list, a warp at a time: publish
-// this tile's aggregate, then read the 32 nearest predecessors at once; the
-// nearest one that carries an inclusive prefix ends the walk, otherwise the
-// window moves 32 tiles back. Tile 0 of a list always carries a prefix, so
-// the walk ends inside the list. Returns the exclusive prefix (all lanes).
-// Every wait is bounded; a wait that runs out reports GC_ERR_TIMEOUT.
-__device__ uint32_t look_back(unsigned long long* lb, uint64_t item, uint64_t t, uint32_t agg, uint32_t* status,
+// Decoupled look-back over the tiles of one list, a warp at a time: the
+// tile's aggregate is already published; read the 32 nearest predecessors
+// at once; the nearest one that carries an inclusive prefix ends the walk,
+// otherwise the window moves 32 tiles back. Tile 0 of a list always carries
+// a prefix, so the walk ends inside the list. Returns the exclusive prefix
+// (all lanes). Every wait is bounded; one that runs out reports
+// GC_ERR_TIMEOUT and the walk stops.
+__device__ uint32_t look_back(const unsigned long long* lb, uint64_t item, uint64_t t, uint32_t* status,
                               uint32_t where) {
   const uint32_t lane = lane_id();
-  if (t == 0) {
-    if (lane == 0) st_release(lb + item, kFlagPrefix | agg);
-    return 0;
-  }
-  if (lane == 0) st_release(lb + item, kFlagAgg | agg);
   uint32_t excl = 0;
-  bool timed_out = false;
-  for (uint64_t d = 1;; d += 32) {
+  for (uint64_t d = 1; d <= t; d += 32) {
     const uint64_t dist = d + lane;  // predecessor tile t - dist
     unsigned long long s = kFlagPrefix;
-    if (dist <= t) {
+    bool timed_out = false;
+    if (dist <= t && dist <= item) {
       s = ld_acquire(lb + item - dist);
       uint32_t spins = 0;
       while ((s >> 32) == 0) {
@@ -370,500 +480,598 @@ __device__ uint32_t look_back(unsigned long long* lb, uint64_t item, uint64_t t,
     }
     excl += warp_sum(v);
   }
-  if (lane == 0) st_release(lb + item, kFlagPrefix | (uint32_t)(excl + agg));
   return excl;
 }
 
-__device__ __forceinline__ uint4 ldg_v4(const uint32_t* p) {
-  uint4 v;
-  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
-  return v;
+// ------------------------------------------------------------------ pack
+
+__device__ __forceinline__ const gc_work& rec_at(const uint4 (*rec)[4], uint32_t s) {
+  return *reinterpret_cast<const gc_work*>(rec[s % kSeq]);
 }
 
-// ---------------------------------------------------------------- tile
+__device__ __forceinline__ uint32_t w_nint(uint32_t shape) { return (shape & 1023u) + 1; }
+__device__ __forceinline__ uint32_t w_vecs(uint32_t shape) { return (shape >> GC_WORK_VEC_SHIFT) & 511u; }
+__device__ __forceinline__ uint32_t w_bit0(uint32_t shape) { return (shape >> GC_WORK_BIT_SHIFT) & 31u; }
+__device__ __forceinline__ uint32_t w_skip(uint32_t shape) { return (shape >> GC_WORK_SKIP_SHIFT) & 31u; }
 
-// Decode tile t of list L (work item `item`). `chained`: the previous tile
-// of the list was decoded by this warp, and `carry` is its inclusive prefix.
-// Returns the tile's inclusive prefix (docIDs modulo 2^32).
-template <int KIND, int K>
-__device__ uint32_t decode_tile(const DecodeArgs& a, const ListRef& L, const gc_tile& rec, uint64_t t,
-                                uint64_t item, uint32_t where, bool chained, uint32_t carry, WarpSmem<K>& ws) {
-  constexpr uint32_t TR = kTileInts / K;
-  constexpr uint32_t DW = WarpSmem<K>::DW;
+// A record the pack decodes: not empty, its tile fits the output pool, and
+// its control area and staged data vectors lie inside their pools.
+template <int K>
+__device__ __forceinline__ bool w_live(const gc_work& w, const DecodeArgs& a) {
+  const uint32_t vecs = w_vecs(w.shape);
+  return w.list != 0xffffffffu && w.out_at + w_nint(w.shape) <= a.out_pool_len &&
+         (uint64_t)w.ctrl_at + w.ctrl_bytes <= a.ctrl_pool_bytes && vecs <= (uint32_t)Geo<K>::MAXVEC &&
+         w.data_at % K == 0 && w.data_at + (uint64_t)vecs * K <= a.data_pool_words;
+}
+
+// Decode the pack of records s0 .. s0 + np - 1 of this warp's sequence
+// (staged, their mbarriers complete), `nl` lines in all.
+template <int KIND, int K, bool RESTORE>
+__device__ void decode_pack(const DecodeArgs& a, WarpSmem<K>& ws, uint32_t s0, uint32_t np, uint32_t nl) {
+  constexpr uint32_t RPL = Geo<K>::RPL;
   const uint32_t lane = lane_id();
-  const uint64_t R = (L.n + K - 1) / K;
-  const uint64_t row0 = t * TR;
-  const uint32_t rows = (uint32_t)((R - row0) < TR ? (R - row0) : TR);
-  const uint32_t nints = (uint32_t)((L.n - row0 * K) < (uint64_t)kTileInts ? (L.n - row0 * K) : kTileInts);
 
-  // 1. control patterns -> per-row (lane-bit offset, width)
-  bool ok;
-  if (KIND == GC_SIMPLE) ok = parse_simple<K>(L, rec, row0, rows, ws);
-  else if (KIND == GC_SCHEME) {
-    if (a.ld == GC_LD_BINARY) ok = parse_scheme_binary<K>(L, row0, rows, a.cg, ws);
-    else ok = parse_scheme_unary<K>(L, rec, rows, a.cg, a.ld == GC_LD_IU, ws);
-  } else if (KIND == GC_AFOR) ok = parse_afor<K>(L, rec, row0, rows, ws);
-  else ok = parse_pfd<K>(L, rec, row0, rows, R, ws);
-  __syncwarp();
-
-  // 2. stage the tile's data words in shared memory: whole k-word vectors
-  // from the first row's word to the last row's, with 16-byte loads that
-  // are all in flight at once
-  const uint32_t rb0 = ws.rb[0];
-  const uint64_t base = rec.lane_bit + rb0;
-  const uint32_t off0 = (uint32_t)base & 31u;
-  const uint32_t tbits = ws.rb[rows - 1] - rb0 + ws.rw[rows - 1];
-  uint32_t nwr = (off0 + tbits + 31) >> 5;
-  if (nwr * K > DW) {
-    nwr = DW / K;
-    ok = false;
-  }
-  const uint64_t g0 = (base >> 5) * K;
-  bool dok = true;
-  for (uint32_t c = lane; c < nwr * K / 4; c += 32) {
-    const uint64_t gw = g0 + 4ull * c;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (gw + 4 <= L.data_words) v = ldg_v4(L.data + gw);
-    else dok = false;
-    *reinterpret_cast<uint4*>(ws.d + 4 * c) = v;
-  }
-  __syncwarp();
-
-  // 3. extract: int i of the tile is lane i % K of row i / K
-#pragma unroll 4
-  for (uint32_t m = 0; m < 32; ++m) {
-    const uint32_t i = lane + 32 * m;
-    uint32_t v = 0;
-    if (i < nints) {
-      const uint32_t r = i / K, j = i % K;
-      const uint32_t w = ws.rw[r];
-      const uint32_t bit = off0 + ws.rb[r] - rb0;
-      const uint32_t o = bit & 31u;
-      uint32_t wi = (bit >> 5) * K + j;
-      wi = wi < DW ? wi : DW - 1;
-      const uint32_t lo = ws.d[wi];
-      uint32_t hi = 0;
-      if (o + w > 32) hi = ws.d[wi + K < DW ? wi + K : DW - 1];
-      v = __funnelshift_r(lo, hi, o) & low_mask(w);
-      if (w == 0) v = 0;
+  // per-item facts, item p in lane p
+  uint32_t my_line0 = 0, my_lines = 0, my_nint = 0, my_item = 0, my_tile = 0, my_base = 0, my_shape = 0;
+  uint32_t my_list = 0xffffffffu;
+  bool my_dead = false;  // a non-empty record that cannot be decoded
+  {
+    uint32_t l0 = 0;
+    for (uint32_t p = 0; p < np; ++p) {
+      const gc_work& w = rec_at(ws.rec, s0 + p);
+      const bool live = w_live<K>(w, a);
+      const uint32_t lines = live ? (w_nint(w.shape) + 31) / 32 : 0;
+      if (lane == p) {
+        my_line0 = l0;
+        my_lines = lines;
+        my_nint = live ? w_nint(w.shape) : 0;
+        my_item = ws.item[(s0 + p) % kSeq];
+        my_tile = w.tile;
+        my_base = w.base;
+        my_shape = w.shape;
+        my_list = live ? w.list : 0xffffffffu;
+        my_dead = !live && w.list != 0xffffffffu;
+      }
+      l0 += lines;
     }
-    ws.outs[pad_idx(i)] = v;
   }
+  if (KIND == GC_PFD) ws.xm[lane] = 0;
   __syncwarp();
-  if (KIND == GC_PFD) {
-    ok = patch_pfd<K>(L, rows, nints, ws) && ok;
-    __syncwarp();
-  }
-  if (!__all_sync(kFull, dok)) ok = false;
-  if (!ok && lane == 0) report(a.status, GC_ERR_CORRUPT, where);
 
-  // 4. docIDs: lane l sums ints 32l..32l+31, a warp scan joins the lanes, the
-  // previous tile's prefix comes from this warp (chained) or by look-back
-  uint32_t incl_tile = 0;
-  if (a.restore) {
-    uint32_t v[32];
-    uint32_t s = 0;
+  // 1. control patterns -> row entries
+  bool all_ok = true;
+  for (uint32_t p = 0; p < np; ++p) {
+    const uint32_t lines = __shfl_sync(kFull, my_lines, p);
+    if (lines == 0) continue;
+    const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
+    const uint32_t nint = __shfl_sync(kFull, my_nint, p);
+    const gc_work& w = rec_at(ws.rec, s0 + p);
+    const uint32_t f = (s0 + p) % kFly;
+    const uint32_t at = ws.at[f];
+    const uint32_t vecs = w_vecs(w.shape);
+    const uint32_t dbytes = vecs * K * 4;
+    CtrlView C;
+    C.g = a.ctrl_pool + w.ctrl_at;
+    C.size = w.ctrl_bytes;
+    C.s1 = ws.ring + at + dbytes;
+    C.lo1 = w.win_at;
+    C.len1 = ws.cst[f];
+    C.s2 = ws.ring + at + dbytes + ws.cst[f];
+    C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
+    C.len2 = ws.xst[f];
+    RowSink<K> out;
+    out.rw = ws.rw + line0 * RPL;
+    out.rs = ws.rs + line0 * RPL;
+    out.word0 = at / 4;
+    out.bit0 = w_bit0(w.shape);
+    out.vec_bits = 32 * vecs;
+    const uint32_t rows = (nint + K - 1) / K;
+    const uint64_t row0 = (uint64_t)w.tile * Geo<K>::TR;
+    bool ok;
+    if (KIND == GC_SIMPLE) {
+      ok = parse_simple<K>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
+    } else if (KIND == GC_SCHEME) {
+      if (a.ld == GC_LD_BINARY) ok = parse_scheme_binary<K>(C, row0, rows, a.cg, out);
+      else ok = parse_scheme_unary<K>(C, w.ctrl_bit, rows, a.cg, a.ld == GC_LD_IU, out);
+    } else if (KIND == GC_AFOR) {
+      ok = parse_afor<K>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
+    } else {
+      ok = parse_pfd<K>(C, row0 / kPfdFrameRows, w.exc_at, rows, out, ws, line0, lines);
+    }
+    // rows of the last line past the tile's end read nothing
+    if (lane < lines * RPL - rows && RPL > 1) {
+      ws.rw[line0 * RPL + rows + lane] = at / 4;
+      ws.rs[line0 * RPL + rows + lane] = 0;
+    }
+    if (!ok) {
+      if (lane == 0) report(a.status, GC_ERR_CORRUPT, w.list);
+      all_ok = false;
+    }
+  }
+  (void)all_ok;
+  __syncwarp();
+
+  // 2. lane l decodes line l: its item p_l (the last live item whose first
+  // line is at or before l) and q, the line within that item
+  const bool act = lane < nl;
+  uint32_t p_l = 0, lhead = 0;
+  for (uint32_t p = 0; p < np; ++p) {
+    const uint32_t lines = __shfl_sync(kFull, my_lines, p);
+    const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
+    if (lines && line0 <= lane) {
+      p_l = p;
+      lhead = line0;
+    }
+  }
+  const uint32_t q = lane - lhead;  // line of the item
+  const uint32_t nint_l = __shfl_sync(kFull, my_nint, p_l);
+  uint32_t nv = 0;
+  if (act) nv = nint_l - 32 * q < 32 ? nint_l - 32 * q : 32;
+
+  uint32_t xmask = 0, xfirst = 0, xwb = 1;
+  const uint8_t* xvals = nullptr;
+  if (KIND == GC_PFD) {
+    xmask = act ? ws.xm[lane] : 0;
+    // exceptions before this line in its frame (K lines per frame)
+    const bool fhead = (q % K) == 0;
+    uint32_t cnt = __popc(xmask);
+    uint32_t v = cnt;
+    bool f = fhead || !act;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, v, o);
+      const bool g = __shfl_up_sync(kFull, f, o);
+      if (lane >= (uint32_t)o && !f) {
+        v += y;
+        f = g;
+      }
+    }
+    xfirst = v - cnt;
+    if (xmask) {
+      xvals = reinterpret_cast<const uint8_t*>(ws.xv[lane]);
+      xwb = ws.xw[lane];
+    }
+  }
+
+  // 3. extract in rotated column order: step c reads column (c + l) % 32
+  uint32_t r[32];
+  uint32_t R = 0, Rw = 0;
+  const uint32_t* ringw = reinterpret_cast<const uint32_t*>(ws.ring);
+  uint32_t rw0 = 0, sh0 = 0, wd0 = 0;
+  if (K == 32 && act) {
+    rw0 = ws.rw[lane];
+    sh0 = ws.rs[lane] & 31u;
+    wd0 = ws.rs[lane] >> 8;
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const uint32_t m = (uint32_t)(c + lane) & 31u;  // int of the line
+    uint32_t wi, sh, wd, comp;
+    if (K == 32) {
+      wi = rw0;
+      sh = sh0;
+      wd = wd0;
+      comp = m;
+    } else {
+      const uint32_t row = lane * RPL + (m / K);
+      wi = act ? ws.rw[row] : 0;
+      const uint32_t s = act ? ws.rs[row] : 0;
+      sh = s & 31u;
+      wd = s >> 8;
+      comp = m % K;
+    }
+    const uint32_t lo = ringw[wi + comp];
+    const uint32_t hi = (sh + wd > 32) ? ringw[wi + K + comp] : 0u;
+    uint32_t v = __funnelshift_r(lo, hi, sh) & low_mask(wd);
+    if (KIND == GC_PFD) {
+      if ((xmask >> m) & 1u) {
+        const uint32_t idx = xfirst + __popc(xmask & ((1u << m) - 1u));
+        const uint8_t* p = xvals + (size_t)idx * xwb;
+        uint32_t x = p[0];
+        if (xwb > 1) x |= (uint32_t)p[1] << 8;
+        if (xwb > 2) x |= ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+        v = x;
+      }
+    }
+    if (m >= nv) v = 0;
+    if (RESTORE) {
+      R += v;
+      r[c] = R;
+      if ((uint32_t)c == 31u - lane) Rw = R;
+    } else {
+      r[c] = v;
+    }
+  }
+
+  // 4. docIDs: segmented scan of line totals, then each item's base
+  uint32_t base_l = 0, E = 0;
+  const uint32_t T = R;
+  if (RESTORE) {
+    const bool head = act && q == 0;
+    uint32_t v = act ? T : 0;
+    bool f = head || !act;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, v, o);
+      const bool g = __shfl_up_sync(kFull, f, o);
+      if (lane >= (uint32_t)o && !f) {
+        v += y;
+        f = g;
+      }
+    }
+    E = v - (act ? T : 0);
+    // item totals: inclusive value at each item's last line
+    const uint32_t lastl = my_lines ? my_line0 + my_lines - 1 : 0;
+    const uint32_t tot = __shfl_sync(kFull, v, lastl);
+    const bool live = lane < np && my_lines > 0;
+    const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
+    const bool needs_lb = live && my_tile > 0 && !has_base;
+    uint32_t base = has_base ? my_base : 0;
+    if (a.lb) {
+      if (live && !needs_lb && (my_shape & GC_WORK_PUBLISH)) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(base + tot));
+      if (lane < np && my_dead) st_release(a.lb + my_item, kFlagPrefix);  // its error is reported
+      if (needs_lb) st_release(a.lb + my_item, kFlagAgg | tot);
+    }
+    uint32_t pend = __ballot_sync(kFull, needs_lb);
+    while (pend) {
+      const uint32_t p = __ffs(pend) - 1;
+      pend &= pend - 1;
+      const uint32_t it = __shfl_sync(kFull, my_item, p);
+      const uint32_t tl = __shfl_sync(kFull, my_tile, p);
+      const uint32_t lst = __shfl_sync(kFull, my_list, p);
+      const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
+      if (lane == p) {
+        base = ex;
+        if (a.lb) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(ex + tot));
+      }
+    }
+    base_l = __shfl_sync(kFull, base, p_l);
+  }
+
+  // 5. final values, transposed to line-major order
+  if (act) {
+    const uint32_t k0 = E + base_l - Rw;
+    const uint32_t k1 = k0 + T;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
-      s += ws.outs[lane * 33 + c];
-      v[c] = s;
+      const uint32_t m = (uint32_t)(c + lane) & 31u;
+      uint32_t v = r[c];
+      if (RESTORE) v += ((uint32_t)c + lane < 32u) ? k1 : k0;
+      ws.tb[lane * 32 + m] = v;
     }
-    const uint32_t incl = warp_incl_sum(s);
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    uint32_t pre;
-    if (chained) {
-      pre = carry;
-      if (lane == 0) st_release(a.lb + item, kFlagPrefix | (uint32_t)(carry + total));
-    } else {
-      pre = look_back(a.lb, item, t, total, a.status, where);
-    }
-    incl_tile = pre + total;
-    pre += incl - s;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) ws.outs[lane * 33 + c] = v[c] + pre;
-    __syncwarp();
-  }
-
-  // 5. coalesced stores
-  uint32_t* out = L.out + row0 * K;
-#pragma unroll 8
-  for (uint32_t m = 0; m < 32; ++m) {
-    const uint32_t i = lane + 32 * m;
-    if (i < nints) out[i] = ws.outs[pad_idx(i)];
   }
   __syncwarp();
-  return incl_tile;
-}
-
-// Persistent decoder. A block claims chunks of C = warps * G consecutive
-// work items from the global counter (one atomic per chunk); its warps take
-// the chunk's items one at a time, in order, through a shared-memory word
-// (base << 32 | items taken). Items are thus handed out in increasing
-// order: every item below a handed-out item has been handed out too, and a
-// warp holds only items below those still in its block's chunk. A look-back
-// waits on lower items only, so the lowest unfinished item always belongs
-// to a running warp and decoding always progresses. When one warp happens
-// to take consecutive tiles of a list, it passes the prefix in registers.
-__device__ uint64_t take_item(unsigned long long* sq, uint32_t* counter, uint64_t total, uint32_t C,
-                              uint32_t* status) {
-  // The word starts as (no chunk, C taken), so the first taker refills. A
-  // returned item at or past `total` ends the caller's loop.
-  for (;;) {
-    const unsigned long long old = atomicAdd(sq, 1ull);
-    const uint64_t base = old >> 32;
-    const uint32_t taken = (uint32_t)old;
-    if (taken < C) return base + taken < total ? base + taken : total;
-    if (taken == C) {
-      uint64_t nb = atomicAdd(counter, C);
-      if (nb > total) nb = total;
-      atomicExch(sq, ((unsigned long long)nb << 32) | 1ull);
-      return nb;
-    }
-    // another warp is refilling the chunk
-    uint32_t spins = 0;
-    while ((*(volatile unsigned long long*)sq >> 32) == base) {
-      if (++spins > kSpinLimit) {
-        report(status, GC_ERR_TIMEOUT, 0xffffffffu);
-        return total;
-      }
-      __nanosleep(20);
+  // output bases of the lines
+  {
+    const uint64_t oat = (lane < np) ? rec_at(ws.rec, s0 + lane).out_at : 0ull;
+    const uint64_t ob = __shfl_sync(kFull, oat, p_l);
+    if (act) {
+      ws.lout[lane] = ob + 32ull * q;
+      ws.lnv[lane] = nv;
     }
   }
+  __syncwarp();
+  for (uint32_t ln = 0; ln < nl; ++ln) {
+    const uint64_t ob = ws.lout[ln];
+    const uint32_t n = ws.lnv[ln];
+    const uint32_t v = ws.tb[ln * 32 + lane];
+    if (lane < n) a.out_pool[ob + lane] = v;
+  }
+  __syncwarp();
 }
 
-template <int KIND, int K, bool BATCH>
+template <int KIND, int K, bool RESTORE>
 __global__ void __launch_bounds__(512) k_decode(DecodeArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ unsigned long long s_queue;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   WarpSmem<K>& ws = reinterpret_cast<WarpSmem<K>*>(smem_raw)[threadIdx.x >> 5];
   const uint32_t lane = lane_id();
-  uint64_t total = a.one_ntiles;
-  if (BATCH) {
-    total = *(volatile const unsigned long long*)a.work_count;
-    if (total > a.work_cap) total = a.work_cap;
+  uint64_t total = a.count[0];
+  if (total > a.work_cap) total = a.work_cap;
+  const bool lookback = RESTORE && a.count[1] != 0;
+  const uint32_t C = lookback ? 1u : a.claim;
+  if (lane < kFly) mbar_init(&ws.mbar[lane], 1);
+  // row entries start in range (a parser stopped by a corrupt stream leaves
+  // earlier, in-range entries behind, never garbage)
+  for (uint32_t i = lane; i < (uint32_t)Geo<K>::PROWS; i += 32) {
+    ws.rw[i] = 0;
+    ws.rs[i] = 0;
   }
-  const uint32_t C = a.claim * (blockDim.x >> 5);
-  if (threadIdx.x == 0) s_queue = (0xffffffffull << 32) | C;  // empty: the first taker refills
-  __syncthreads();
-  uint64_t prev_list = ~0ull, prev_t = ~0ull;
-  uint32_t prev_incl = 0;
+  fence_mbar_init();
+  __syncwarp();
+
+  uint32_t s_claimed = 0, s_issued = 0, s_done = 0;  // positions in this warp's record sequence
+  uint32_t head = 0, tail = 0;                        // ring positions (bytes, monotonic)
+  bool more = true;
+  bool failed = false;
   for (;;) {
-    uint64_t item = 0;
-    if (lane == 0) item = take_item(&s_queue, a.counters, total, C, a.status);
-    item = __shfl_sync(kFull, item, 0);
-    if (item >= total) break;
-    ListRef L;
-    uint64_t t, list;
-    gc_tile rec = {0, 0, 0, 0};
-    uint32_t where;
-    bool skip = false;
-    if (!BATCH) {
-      L = a.one;
-      t = item;
-      list = 0;
-      where = (uint32_t)item;
-      if (t > 0) {
-        const gc_tile* p = a.one_tiles + t;
-        rec.lane_bit = p->lane_bit;
-        rec.ctrl_bit = p->ctrl_bit;
-        rec.exc_off = p->exc_off;
-        rec.row_skip = p->row_skip;
-      }
-    } else {
-      const uint4* wp = reinterpret_cast<const uint4*>(a.work + item);
-      const uint4 q0 = __ldg(wp), q1 = __ldg(wp + 1), q2 = __ldg(wp + 2), q3 = __ldg(wp + 3);
-      const uint64_t ctrl_off = q0.x | ((uint64_t)q0.y << 32);
-      const uint64_t data_off = q0.z | ((uint64_t)q0.w << 32);
-      const uint64_t out_off = q1.x | ((uint64_t)q1.y << 32);
-      const uint32_t n = q1.z;
-      t = q1.w;
-      rec.lane_bit = q2.x | ((uint64_t)q2.y << 32);
-      rec.ctrl_bit = q2.z | ((uint64_t)q2.w << 32);
-      rec.exc_off = q3.x;
-      rec.row_skip = q3.y;
-      list = q3.z;
-      where = q3.z;
-      L.ctrl = a.ctrl_pool + ctrl_off;
-      L.ctrl_bytes = ctrl_off < a.ctrl_pool_bytes ? a.ctrl_pool_bytes - ctrl_off : 0;
-      L.data = a.data_pool + data_off;
-      L.data_words = data_off < a.data_pool_words ? a.data_pool_words - data_off : 0;
-      L.out = a.out_pool + out_off;
-      L.n = n;
-      if (q3.z == 0xffffffffu) {
-        skip = true;  // an empty slot (the plan overflowed its table)
-      } else if (out_off + n > a.out_pool_len || (data_off % K) != 0) {
-        if (lane == 0) report(a.status, GC_ERR_INVALID, where);
-        skip = true;
+    // claim records
+    if (more && s_claimed - s_done + C <= (uint32_t)kSeq) {
+      uint32_t x = 0;
+      if (lane == 0) x = atomicAdd(a.counter, C);
+      x = __shfl_sync(kFull, x, 0);
+      const uint32_t cnt = (uint64_t)x < total ? (uint32_t)min64(C, total - x) : 0u;
+      if (cnt == 0) {
+        more = false;
+      } else {
+        if (lane < cnt) {
+          const uint4* src = reinterpret_cast<const uint4*>(a.work + x + lane);
+          uint4* dst = ws.rec[(s_claimed + lane) % kSeq];
+          dst[0] = __ldg(src);
+          dst[1] = __ldg(src + 1);
+          dst[2] = __ldg(src + 2);
+          dst[3] = __ldg(src + 3);
+          ws.item[(s_claimed + lane) % kSeq] = x + lane;
+        }
+        __syncwarp();
+        s_claimed += cnt;
       }
     }
-    if (skip || t * kTileInts >= L.n) {
-      // nothing to decode; keep the chain of prefixes alive
-      if (a.restore && lane == 0) st_release(a.lb + item, kFlagPrefix);
-      prev_list = ~0ull;
+    // stage claimed tiles while the ring and the mbarriers allow
+    while (s_issued < s_claimed && s_issued - s_done < (uint32_t)kFly) {
+      const gc_work& w = rec_at(ws.rec, s_issued);
+      const uint32_t f = s_issued % kFly;
+      uint32_t dbytes = 0, cb = 0, xb = 0;
+      if (w_live<K>(w, a)) {
+        dbytes = w_vecs(w.shape) * K * 4;
+        const int64_t ws0 = (int64_t)w.ctrl_at + w.win_at;
+        cb = w.win_len < kCtrlCap ? w.win_len : (uint32_t)kCtrlCap;
+        if (ws0 < 0 || (ws0 & 15) || (uint64_t)ws0 + cb > a.ctrl_pool_bytes) cb = 0;
+        if (KIND == GC_PFD) {
+          const uint64_t xs = (w.ctrl_at + w.exc_at) & ~15ull;
+          xb = w.exc_len;
+          if (xb > (uint32_t)kExcCap || xs + xb > a.ctrl_pool_bytes) xb = 0;
+        }
+      }
+      const uint32_t need = (dbytes + cb + xb + 127u) & ~127u;
+      if (head == tail) head = tail = (head + kRing - 1) / kRing * kRing;  // empty: restart at offset 0
+      const uint32_t pos = head % kRing;
+      const uint32_t pad = (pos + need > (uint32_t)kRing) ? kRing - pos : 0u;
+      if (head + pad + need - tail > (uint32_t)kRing) break;  // the ring is full
+      const uint32_t start = head + pad;
+      const uint32_t off = start % kRing;
+      head = start + need;
+      if (lane == 0) {
+        ws.at[f] = off;
+        ws.end[f] = head;
+        ws.cst[f] = (uint16_t)cb;
+        ws.xst[f] = (uint16_t)xb;
+        fence_proxy_async();
+        mbar_expect_tx(&ws.mbar[f], dbytes + cb + xb);
+        if (dbytes) bulk_g2s(ws.ring + off, a.data_pool + w.data_at, dbytes, &ws.mbar[f]);
+        if (cb) bulk_g2s(ws.ring + off + dbytes, a.ctrl_pool + (w.ctrl_at + w.win_at), cb, &ws.mbar[f]);
+        if (xb)
+          bulk_g2s(ws.ring + off + dbytes + cb, a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull), xb, &ws.mbar[f]);
+      }
+      __syncwarp();
+      ++s_issued;
+    }
+    if (s_done == s_issued) {
+      if (!more && s_issued == s_claimed) break;
       continue;
     }
-    const bool chained = (list == prev_list) && (t == prev_t + 1);
-    prev_incl = decode_tile<KIND, K>(a, L, rec, t, item, where, chained, prev_incl, ws);
-    prev_list = list;
-    prev_t = t;
+    // a pack: records from s_done on while their lines fit 32
+    uint32_t np = 0, nl = 0;
+    while (s_done + np < s_issued && np < 32) {
+      const gc_work& w = rec_at(ws.rec, s_done + np);
+      const uint32_t lines = w_live<K>(w, a) ? (w_nint(w.shape) + 31) / 32 : 0u;
+      if (nl + lines > 32) break;
+      nl += lines;
+      ++np;
+    }
+    // wait for their copies
+    for (uint32_t p = 0; p < np && !failed; ++p) {
+      const uint32_t s = s_done + p;
+      uint32_t spins = 0;
+      while (!mbar_try_wait(&ws.mbar[s % kFly], (s / kFly) & 1u)) {
+        if (++spins > kSpinLimit) {
+          failed = true;
+          break;
+        }
+      }
+    }
+    if (__any_sync(kFull, failed)) {
+      // a copy never completed: stop this warp (its records stay undecoded)
+      if (lane == 0) report(a.status, GC_ERR_TIMEOUT, 0xfffffffeu);
+      break;
+    }
+    for (uint32_t p = 0; p < np; ++p) {
+      const gc_work& w = rec_at(ws.rec, s_done + p);
+      if (w.list != 0xffffffffu && !w_live<K>(w, a) && lane == 0)
+        report(a.status, w.out_at + w_nint(w.shape) > a.out_pool_len ? GC_ERR_INVALID : GC_ERR_CORRUPT, w.list);
+    }
+    decode_pack<KIND, K, RESTORE>(a, ws, s_done, np, nl);
+    s_done += np;
+    tail = ws.end[(s_done - 1) % kFly];
   }
+  (void)tail;
 }
 
-// Batched plan, pass 1: one thread per list reserves a contiguous range of
-// work items for the list's tiles (one atomic per warp) and writes (list,
-// tile) into each record. A list's tiles are consecutive items, so a tile's
-// predecessor is always claimed before it.
-__global__ void k_plan_reserve(const gc_list* lists, uint64_t nlists, uint32_t k, gc_work* work, uint64_t cap,
-                               unsigned long long* count, uint32_t* status) {
+// --------------------------------------------------------------- the plan
+
+struct PlanArgs {
+  uint32_t kind, k, cg, ld;
+  const gc_list* lists;  // NULL: the single list `one`
+  gc_list one;
+  uint64_t nlists;
+  const gc_tile* tiles;  // batch: tile t >= 1 of a list at tile_off + t - 1; single: tile t at t
+  uint64_t ntiles;
+  const uint8_t* ctrl_pool;
+  uint64_t ctrl_pool_bytes;
+  gc_work* work;
+  uint64_t cap;
+  unsigned long long* count;  // [0] records, [1] records needing look-back
+  uint32_t* status;
+};
+
+__device__ __forceinline__ gc_list plan_list(const PlanArgs& a, uint64_t i) { return a.lists ? a.lists[i] : a.one; }
+
+// Pass 1: one thread per list reserves a contiguous range of records for the
+// list's tiles (one atomic per warp) and writes (list, tile) into each. A
+// list's tiles are consecutive records.
+__global__ void k_plan_reserve(PlanArgs a) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = lane_id();
   uint64_t nt = 0;
-  if (i < nlists) {
-    const uint64_t n = lists[i].n;
-    const uint64_t R = (n + k - 1) / k;
-    const uint64_t tr = kTileInts / k;
+  if (i < a.nlists) {
+    const uint64_t n = plan_list(a, i).n;
+    const uint64_t R = (n + a.k - 1) / a.k;
+    const uint64_t tr = kTileInts / a.k;
     nt = (R + tr - 1) / tr;
   }
   const uint64_t incl = warp_incl_sum(nt);
   unsigned long long b = 0;
-  if (lane == 31) b = atomicAdd(count, (unsigned long long)incl);
+  if (lane == 31) b = atomicAdd(a.count, (unsigned long long)incl);
   const uint64_t base = __shfl_sync(kFull, b, 31) + incl - nt;
-  if (i >= nlists) return;
-  const bool fits = base + nt <= cap;
-  if (!fits) report(status, GC_ERR_NOSPACE, (uint32_t)i);
-  for (uint64_t t = 0; t < nt && base + t < cap; ++t) {
-    gc_work* w = work + base + t;
+  if (i >= a.nlists) return;
+  const bool fits = base + nt <= a.cap;
+  if (!fits) report(a.status, GC_ERR_NOSPACE, (uint32_t)i);
+  for (uint64_t t = 0; t < nt && base + t < a.cap; ++t) {
+    gc_work* w = a.work + base + t;
     w->tile = (uint32_t)t;
     w->list = fits ? (uint32_t)i : 0xffffffffu;
   }
 }
 
-// Pass 2: one thread per work item fills in the list's descriptor and the
-// tile's record (tile 0 starts at the list's first unit).
-__global__ void k_plan_fill(const gc_list* lists, uint64_t nlists, const gc_tile* tiles, uint64_t ntiles,
-                            gc_work* work, uint64_t cap, const unsigned long long* count, uint32_t* status) {
+__device__ __forceinline__ bool plan_tile(const PlanArgs& a, const gc_list& d, uint64_t t, gc_tile* r) {
+  if (t == 0) {
+    *r = gc_tile{0, 0, 0, 0, 0, GC_TILE_BASE};
+    return true;
+  }
+  const uint64_t ti = a.lists ? (uint64_t)d.tile_off + t - 1 : t;
+  if (!a.tiles || ti >= a.ntiles) return false;
+  *r = a.tiles[ti];
+  return true;
+}
+
+__device__ __forceinline__ uint64_t al16(uint64_t x) { return x & ~15ull; }
+
+// Pass 2: one thread per record fills in the list's areas, the tile's first
+// unit and skip entry, and the exact ranges of the tile's streams: data
+// vectors from the unit's first word to the word holding the tile's last
+// row (the next tile's first unit, plus the part of it before that tile
+// when the unit straddles the two); control bytes per codec.
+__global__ void k_plan_fill(PlanArgs a) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint64_t total = *count;
-  if (total > cap) total = cap;
+  uint64_t total = a.count[0];
+  if (total > a.cap) total = a.cap;
   if (i >= total) return;
-  gc_work w = work[i];
-  if (w.list >= nlists) {
-    w = gc_work{0, 0, 0, 0, 0, 0, 0, 0, 0, 0xffffffffu, 0};
-    work[i] = w;
+  gc_work w = a.work[i];
+  const gc_work empty = {0, 0, 0, 0, 0, 0, 0xffffffffu, 0, 0, 0, 0, 0, 0};
+  if (w.list == 0xffffffffu || w.list >= a.nlists) {
+    a.work[i] = empty;
     return;
   }
-  const gc_list d = lists[w.list];
-  w.ctrl_off = d.ctrl_off;
-  w.data_off = d.data_off;
-  w.out_off = d.out_off;
-  w.n = d.n;
-  w.lane_bit = w.ctrl_bit = 0;
-  w.exc_off = w.row_skip = 0;
-  w.reserved = 0;
-  if (w.tile > 0) {
-    const uint64_t ti = (uint64_t)d.tile_off + w.tile - 1;
-    if (ti < ntiles) {
-      const gc_tile r = tiles[ti];
-      w.lane_bit = r.lane_bit;
-      w.ctrl_bit = r.ctrl_bit;
-      w.exc_off = r.exc_off;
-      w.row_skip = r.row_skip;
-    } else {
-      report(status, GC_ERR_CORRUPT, w.list);
-      w.n = 0;  // decodes nothing
-    }
+  const gc_list d = plan_list(a, w.list);
+  const uint64_t k = a.k, TR = kTileInts / k;
+  const uint64_t t = w.tile;
+  const uint64_t n = d.n;
+  const uint64_t R = (n + k - 1) / k;
+  const uint64_t nt = (R + TR - 1) / TR;
+  const uint64_t row0 = t * TR;
+  const uint64_t rows = min64(TR, R - row0);
+  gc_tile r0, r1;
+  const bool last = t + 1 >= nt;
+  bool ok = plan_tile(a, d, t, &r0);
+  if (!last) ok = ok && plan_tile(a, d, t + 1, &r1);
+  const uint64_t cbytes = d.ctrl_bytes;
+  // data vectors, from the word that holds the tile's first row (a Group-AFOR
+  // frame may start rows before the tile)
+  uint64_t first_bit = r0.lane_bit;
+  if (a.kind == GC_AFOR && r0.row_skip) {
+    const uint64_t fb = r0.ctrl_bit >> 3;
+    const uint64_t at = d.ctrl_off + fb;
+    const uint32_t byte = (fb < cbytes && at < a.ctrl_pool_bytes) ? a.ctrl_pool[at] : 0xffu;
+    first_bit += (uint64_t)r0.row_skip * ((byte & 63u) <= 32 ? (byte & 63u) : 32u);
   }
-  work[i] = w;
-}
-
-// ------------------------------------------------------- tile index build
-// The paper's format stores no tile records. They follow from the control
-// area alone: split it into chunks, sum (rows, lane bits, exception bytes)
-// per chunk, scan the chunk sums, and walk each chunk again from its prefix,
-// writing a record for every tile whose first row falls in a unit.
-
-struct UnitAgg {
-  uint64_t rows, lbits, xbytes;
-};
-
-struct IndexArgs {
-  uint32_t kind, k, cg, ld;
-  const uint8_t* ctrl;
-  uint64_t ctrl_bytes;
-  uint64_t n, R;
-  uint64_t nunits;   // units (fixed-size control) or control bytes (unary)
-  uint64_t nchunks;
-  gc_tile* tiles;
-  uint64_t ntiles;
-  UnitAgg* block_sums;
-  uint32_t* status;
-};
-
-constexpr int kChunkUnits = 64;  // units per chunk (fixed-size control)
-constexpr int kChunkBytes = 8;   // control bytes per chunk (unary)
-constexpr int kIndexThreads = 256;
-
-// Walk one chunk. With emit = false only the sums; with emit = true starting
-// from `base`, write the tile records.
-__device__ UnitAgg walk_chunk(const IndexArgs& a, uint64_t c, bool emit, UnitAgg base) {
-  UnitAgg s = {0, 0, 0};
-  const uint64_t tr = kTileInts / a.k;
-  auto put = [&](uint64_t row, uint64_t urows, uint64_t lbit, uint64_t cbit, uint64_t xoff) {
-    // tiles whose first row lies in [row, row + urows)
-    uint64_t t = (row + tr - 1) / tr;
-    for (; t * tr < row + urows && t < a.ntiles; ++t) {
-      gc_tile g;
-      g.lane_bit = lbit;
-      g.ctrl_bit = cbit;
-      g.exc_off = (uint32_t)xoff;
-      g.row_skip = (uint32_t)(t * tr - row);
-      a.tiles[t] = g;
-    }
-  };
-  if (a.kind == GC_SCHEME && a.ld != GC_LD_BINARY) {
-    // unary: units are zeros; a chunk owns the descriptors whose closing
-    // zero lies in its bytes
-    const uint64_t b0 = c * kChunkBytes;
-    const uint64_t b1 = (b0 + kChunkBytes) < a.ctrl_bytes ? (b0 + kChunkBytes) : a.ctrl_bytes;
-    const bool iu = a.ld == GC_LD_IU;
-    // previous zero before the chunk (CU only; within 32 bits unless at 0)
-    int64_t prev = -1;
-    if (!iu && b0 > 0) {
-      for (int64_t p = (int64_t)b0 * 8 - 1; p >= 0 && p >= (int64_t)b0 * 8 - 40; --p)
-        if (!((a.ctrl[p >> 3] >> (p & 7)) & 1)) { prev = p; break; }
-    }
-    uint64_t row = base.rows, lb = base.lbits;
-    for (uint64_t by = b0; by < b1; ++by) {
-      const uint32_t byte = a.ctrl[by];
-      if (iu) prev = (int64_t)by * 8 - 1;
-      for (uint32_t bit = 0; bit < 8; ++bit) {
-        if ((byte >> bit) & 1u) continue;
-        const int64_t p = (int64_t)by * 8 + bit;
-        const uint64_t u = (uint64_t)(p - prev);
-        if (emit && row < a.R) put(row, 1, lb, (uint64_t)(prev + 1), 0);
-        ++row;
-        lb += a.cg * u;
-        s.rows += 1;
-        s.lbits += a.cg * u;
-        prev = p;
-      }
-    }
-    return s;
-  }
-  const uint64_t u0 = c * kChunkUnits;
-  const uint64_t u1 = (u0 + kChunkUnits) < a.nunits ? (u0 + kChunkUnits) : a.nunits;
-  uint64_t row = base.rows, lb = base.lbits, xo = base.xbytes;
-  const uint64_t nf = (a.R + kPfdFrameRows - 1) / kPfdFrameRows;
-  const uint32_t pb = (kPfdFrameRows * a.k) <= 256 ? 1u : 2u;
-  for (uint64_t u = u0; u < u1; ++u) {
-    uint64_t urows, lbits, xb = 0, cbit;
-    if (a.kind == GC_SIMPLE) {
-      const uint32_t sel = (a.ctrl[u >> 1] >> ((u & 1) * 4)) & 15u;
-      if (sel > 9) {
-        if (emit && row < a.R) report(a.status, GC_ERR_CORRUPT, (uint32_t)u);
-        urows = 32;
-        lbits = 32;
+  const uint64_t v0 = first_bit >> 5;
+  uint64_t v1 = d.data_words / k;
+  if (!last) {
+    uint64_t straddle = 0;
+    if (r1.row_skip) {
+      if (a.kind == GC_SIMPLE) {
+        straddle = 32;
+      } else if (a.kind == GC_AFOR) {
+        const uint64_t fb = r1.ctrl_bit >> 3;
+        const uint64_t at = d.ctrl_off + fb;
+        const uint32_t byte = (fb < cbytes && at < a.ctrl_pool_bytes) ? a.ctrl_pool[at] : 0xffu;
+        straddle = (uint64_t)r1.row_skip * ((byte & 63u) <= 32 ? (byte & 63u) : 32u);
       } else {
-        urows = sel_num(sel);
-        lbits = 32;
+        straddle = 32ull * r1.row_skip;
       }
-      cbit = 4 * u;
-    } else if (a.kind == GC_SCHEME) {
-      const uint32_t width = 5 - log2_cg(a.cg);
-      cbit = bin_ld_pos(u, a.cg);
-      const uint32_t v = read_ctrl_bits(a.ctrl, a.ctrl_bytes, cbit, width) + 1;
-      urows = 1;
-      lbits = (uint64_t)a.cg * v;
-    } else if (a.kind == GC_AFOR) {
-      const uint32_t byte = a.ctrl[u];
-      const uint32_t code = byte >> 6, b = byte & 63u;
-      if (code > 2 || b > 32) {
-        if (emit && row < a.R) report(a.status, GC_ERR_CORRUPT, (uint32_t)u);
-        urows = 32;
-        lbits = 0;
-      } else {
-        urows = 8u << code;
-        lbits = urows * b;
-      }
-      cbit = 8 * u;
-    } else {
-      const uint32_t hdr = read_le(a.ctrl, a.ctrl_bytes, 4 * u, 4);
-      const uint32_t b = hdr & 63u, wc = (hdr >> 6) & 3u, e = hdr >> 8;
-      urows = kPfdFrameRows;
-      lbits = (uint64_t)kPfdFrameRows * (b > 32 ? 0 : b);
-      xb = (uint64_t)e * (pb + (1u << (wc > 2 ? 2 : wc)));
-      cbit = 32 * u;
-      (void)nf;
     }
-    if (emit && row < a.R) put(row, urows, lb, cbit, xo);
-    row += urows;
-    lb += lbits;
-    xo += xb;
-    s.rows += urows;
-    s.lbits += lbits;
-    s.xbytes += xb;
+    const uint64_t e = r1.lane_bit + straddle;
+    v1 = min64((e + 31) >> 5, v1);
   }
-  return s;
-}
-
-__device__ __forceinline__ UnitAgg agg_add(UnitAgg x, UnitAgg y) {
-  return UnitAgg{x.rows + y.rows, x.lbits + y.lbits, x.xbytes + y.xbytes};
-}
-
-// Block-wide exclusive scan of UnitAgg (256 threads); returns the exclusive
-// value and writes the block total.
-__device__ UnitAgg block_excl_scan(UnitAgg v, UnitAgg* total) {
-  __shared__ UnitAgg warp_tot[kIndexThreads / 32];
-  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
-  UnitAgg inc;
-  inc.rows = warp_incl_sum(v.rows);
-  inc.lbits = warp_incl_sum(v.lbits);
-  inc.xbytes = warp_incl_sum(v.xbytes);
-  if (lane == 31) warp_tot[w] = inc;
-  __syncthreads();
-  UnitAgg wbase = {0, 0, 0}, tot = {0, 0, 0};
-  for (int i = 0; i < kIndexThreads / 32; ++i) {
-    if (i < (int)w) wbase = agg_add(wbase, warp_tot[i]);
-    tot = agg_add(tot, warp_tot[i]);
+  if (v1 < v0 || v1 - v0 > TR + 1 || (d.data_off % k) != 0) ok = false;
+  // control bytes [cs, ce) of the tile (and the PFD exception records)
+  uint64_t cs = 0, ce = cbytes, xs = 0, xe = 0;
+  const uint64_t nf = (R + kPfdFrameRows - 1) / kPfdFrameRows;
+  switch (a.kind) {
+    case GC_SIMPLE:
+      cs = r0.ctrl_bit >> 3;
+      if (!last) ce = (r1.ctrl_bit >> 3) + 1;
+      break;
+    case GC_SCHEME:
+      if (a.ld == GC_LD_BINARY) {
+        cs = bin_ld_pos(row0, a.cg) >> 3;
+        ce = bin_ld_bytes(row0 + rows, a.cg);
+      } else {
+        cs = r0.ctrl_bit >> 3;
+        if (!last) ce = (r1.ctrl_bit + 7) >> 3;
+      }
+      break;
+    case GC_AFOR:
+      cs = r0.ctrl_bit >> 3;
+      if (!last) ce = (r1.ctrl_bit >> 3) + 1;
+      break;
+    default:
+      cs = 4 * (row0 / kPfdFrameRows);
+      ce = 4 * ((row0 + rows + kPfdFrameRows - 1) / kPfdFrameRows);
+      xs = 4 * nf + r0.exc_off;
+      xe = last ? cbytes : 4 * nf + r1.exc_off;
+      break;
   }
-  __syncthreads();
-  *total = tot;
-  return UnitAgg{wbase.rows + inc.rows - v.rows, wbase.lbits + inc.lbits - v.lbits,
-                 wbase.xbytes + inc.xbytes - v.xbytes};
-}
-
-__global__ void __launch_bounds__(kIndexThreads) k_index_sums(IndexArgs a) {
-  const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  UnitAgg v = {0, 0, 0};
-  if (c < a.nchunks) v = walk_chunk(a, c, false, v);
-  UnitAgg tot;
-  block_excl_scan(v, &tot);
-  if (threadIdx.x == 0) a.block_sums[blockIdx.x] = tot;
-}
-
-// One block: exclusive scan of the block sums in place.
-__global__ void __launch_bounds__(kIndexThreads) k_index_scan(UnitAgg* sums, uint64_t nblocks) {
-  UnitAgg carry = {0, 0, 0};
-  for (uint64_t b0 = 0; b0 < nblocks; b0 += kIndexThreads) {
-    const uint64_t i = b0 + threadIdx.x;
-    UnitAgg v = i < nblocks ? sums[i] : UnitAgg{0, 0, 0};
-    UnitAgg tot;
-    UnitAgg ex = block_excl_scan(v, &tot);
-    if (i < nblocks) sums[i] = agg_add(carry, ex);
-    carry = agg_add(carry, tot);
-    __syncthreads();
+  ce = min64(ce, cbytes);
+  if (cs > ce) ok = false;
+  const uint64_t pool_end = al16(a.ctrl_pool_bytes);
+  const uint64_t wlo = al16(d.ctrl_off + cs);
+  uint64_t whi = min64(al16(d.ctrl_off + ce + 15), pool_end);
+  if (whi < wlo) whi = wlo;
+  uint64_t xlen = 0;
+  if (a.kind == GC_PFD && xe > xs) {
+    const uint64_t xlo = al16(d.ctrl_off + xs);
+    const uint64_t xhi = al16(d.ctrl_off + xe + 15);
+    xlen = xhi <= pool_end ? xhi - xlo : 0;  // all of the tile's records, or none
+    if (xlen > 0xfff0) xlen = 0;
   }
-}
-
-__global__ void __launch_bounds__(kIndexThreads) k_index_emit(IndexArgs a) {
-  const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  UnitAgg v = {0, 0, 0};
-  if (c < a.nchunks) v = walk_chunk(a, c, false, v);
-  UnitAgg tot;
-  UnitAgg ex = block_excl_scan(v, &tot);
-  if (c < a.nchunks) walk_chunk(a, c, true, agg_add(a.block_sums[blockIdx.x], ex));
+  if (xe < xs || xe > cbytes) ok = false;
+  if (d.ctrl_off + cbytes > a.ctrl_pool_bytes) ok = false;
+  if (!ok) {
+    report(a.status, GC_ERR_CORRUPT, w.list);
+    a.work[i] = empty;
+    return;
+  }
+  const bool has_base = (r0.flags & GC_TILE_BASE) != 0;
+  const bool publish = !last && !(r1.flags & GC_TILE_BASE);
+  if (t > 0 && !has_base) {
+    // warp-aggregated count of records that take their prefix by look-back
+    atomicAdd(a.count + 1, 1ull);
+  }
+  const uint32_t nint = (uint32_t)min64(kTileInts, n - t * kTileInts);
+  w.ctrl_at = d.ctrl_off;
+  w.data_at = d.data_off + v0 * k;
+  w.out_at = d.out_off + t * kTileInts;
+  w.ctrl_bit = r0.ctrl_bit;
+  w.ctrl_bytes = (uint32_t)cbytes;
+  w.base = has_base ? r0.base : 0;
+  w.exc_at = (uint32_t)xs;
+  w.win_at = (int32_t)((int64_t)wlo - (int64_t)d.ctrl_off);
+  w.win_len = (uint16_t)min64(whi - wlo, 0xfff0);
+  w.exc_len = (uint16_t)xlen;
+  w.shape = (nint - 1) | ((uint32_t)(v1 - v0) << GC_WORK_VEC_SHIFT) | ((uint32_t)(first_bit & 31) << GC_WORK_BIT_SHIFT) |
+            ((r0.row_skip & 31u) << GC_WORK_SKIP_SHIFT) | (has_base ? (uint32_t)GC_WORK_HAS_BASE : 0u) |
+            (publish ? (uint32_t)GC_WORK_PUBLISH : 0u);
+  a.work[i] = w;
 }
 
 }  // namespace gcdev
@@ -874,27 +1082,35 @@ using namespace gcdev;
 
 namespace {
 
-template <int K>
-size_t warp_smem() { return sizeof(WarpSmem<K>); }
-
 constexpr uint32_t kMaxWarps = 16;     // warps per block (launch bounds: 512 threads)
-constexpr uint32_t kDefaultWarps = 8;
-constexpr uint32_t kMaxClaim = 64;     // work items per claim
-constexpr uint32_t kDefaultClaim = 4;
+constexpr uint32_t kDefaultWarps = 4;
+constexpr uint32_t kMaxClaim = 32;     // records per claim
+constexpr uint32_t kDefaultClaim = 8;
+constexpr uint64_t kHdr = 256;         // scratch header: claim counter, record counts
 
-template <int KIND, int K, bool BATCH>
-cudaError_t launch_decode_t(const DecodeArgs& a, uint32_t warps, uint32_t blocks_per_sm, uint64_t work,
-                            cudaStream_t s) {
-  auto fn = k_decode<KIND, K, BATCH>;
-  const size_t smem = warps * warp_smem<K>();
+template <int KIND, int K, bool RESTORE>
+cudaError_t launch_t(const DecodeArgs& a, uint32_t warps, uint32_t blocks_per_sm, uint64_t work, cudaStream_t s) {
+  auto fn = k_decode<KIND, K, RESTORE>;
   // the shared-memory limit only grows, and the occupancy is fixed per
   // (device, warps): both are cached so a launch costs one API call
   static size_t smem_limit[64] = {};
   static int cached_occ[64][kMaxWarps + 1] = {};
+  static int optin[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const bool cache = dev >= 0 && dev < 64;
+  // a block holds as many warps as its shared memory allows
+  int max_smem = cache ? optin[dev] : 0;
+  if (max_smem == 0) {
+    e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (cache) optin[dev] = max_smem;
+  }
+  const uint32_t fit = (uint32_t)(max_smem / sizeof(WarpSmem<K>));
+  if (fit == 0) return cudaErrorInvalidConfiguration;
+  if (warps > fit) warps = fit;
+  const size_t smem = warps * sizeof(WarpSmem<K>);
   if (!cache || smem > smem_limit[dev]) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -911,20 +1127,20 @@ cudaError_t launch_decode_t(const DecodeArgs& a, uint32_t warps, uint32_t blocks
   uint32_t bps = blocks_per_sm ? blocks_per_sm : (uint32_t)occ;
   if (bps > (uint32_t)occ) bps = (uint32_t)occ;
   uint64_t grid = (uint64_t)bps * sms;
-  const uint64_t need = (work + (uint64_t)warps * a.claim - 1) / ((uint64_t)warps * a.claim);
-  if (!BATCH && grid > need) grid = need ? need : 1;
+  const uint64_t need = (work + warps - 1) / warps;  // at least one record per warp
+  if (grid > need) grid = need ? need : 1;
   fn<<<(unsigned)grid, warps * 32, smem, s>>>(a);
   gc_host::count_launch();
   return cudaGetLastError();
 }
 
-template <bool BATCH>
-cudaError_t launch_decode(uint32_t kind, uint32_t k, const DecodeArgs& a, uint32_t warps, uint32_t bps,
-                          uint64_t work, cudaStream_t s) {
-#define GC_DISPATCH(KIND)                                                           \
-  if (kind == KIND) {                                                                \
-    if (k == 4) return launch_decode_t<KIND, 4, BATCH>(a, warps, bps, work, s);      \
-    return launch_decode_t<KIND, 32, BATCH>(a, warps, bps, work, s);                 \
+template <bool RESTORE>
+cudaError_t launch_r(uint32_t kind, uint32_t k, const DecodeArgs& a, uint32_t warps, uint32_t bps, uint64_t work,
+                     cudaStream_t s) {
+#define GC_DISPATCH(KIND)                                                      \
+  if (kind == KIND) {                                                           \
+    if (k == 4) return launch_t<KIND, 4, RESTORE>(a, warps, bps, work, s);      \
+    return launch_t<KIND, 32, RESTORE>(a, warps, bps, work, s);                 \
   }
   GC_DISPATCH(GC_SIMPLE)
   GC_DISPATCH(GC_SCHEME)
@@ -934,6 +1150,11 @@ cudaError_t launch_decode(uint32_t kind, uint32_t k, const DecodeArgs& a, uint32
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_decode(uint32_t kind, uint32_t k, bool restore, const DecodeArgs& a, uint32_t warps, uint32_t bps,
+                          uint64_t work, cudaStream_t s) {
+  return restore ? launch_r<true>(kind, k, a, warps, bps, work, s) : launch_r<false>(kind, k, a, warps, bps, work, s);
+}
+
 // Launch shape from the caller's request (NULL = defaults); GC_ERR_INVALID
 // for a shape out of range.
 gc_status launch_shape(const gc_launch* l, uint32_t* warps, uint32_t* bps, uint32_t* claim) {
@@ -941,70 +1162,76 @@ gc_status launch_shape(const gc_launch* l, uint32_t* warps, uint32_t* bps, uint3
   *bps = 0;
   *claim = kDefaultClaim;
   if (!l) return GC_OK;
-  if (l->warps_per_block < 1 || l->warps_per_block > kMaxWarps) return GC_ERR_INVALID;
-  if (l->items_per_claim > kMaxClaim) return GC_ERR_INVALID;
-  *warps = l->warps_per_block;
+  if (l->warps_per_block > kMaxWarps || l->items_per_claim > kMaxClaim) return GC_ERR_INVALID;
+  if (l->warps_per_block) *warps = l->warps_per_block;
   *bps = l->blocks_per_sm;
   if (l->items_per_claim) *claim = l->items_per_claim;
   return GC_OK;
 }
 
-uint64_t index_nunits(const gc_codec& c, uint64_t R, uint64_t ctrl_bytes) {
-  switch (c.kind) {
-    case GC_SIMPLE: return 2 * ctrl_bytes;
-    case GC_SCHEME: return c.ld == GC_LD_BINARY ? R : ctrl_bytes;
-    case GC_AFOR: return ctrl_bytes;
-    default: return (R + kPfdFrameRows - 1) / kPfdFrameRows;
-  }
-}
-
-uint64_t index_chunks(const gc_codec& c, uint64_t nunits) {
-  if (c.kind == GC_SCHEME && c.ld != GC_LD_BINARY) return (nunits + kChunkBytes - 1) / kChunkBytes;
-  return (nunits + kChunkUnits - 1) / kChunkUnits;
-}
-
-uint64_t index_scratch(const gc_codec& c, uint64_t n) {
-  // bound the control bytes by the encoder's maximum
-  uint64_t cc = 0, dc = 0, nt = 0;
-  gc_max_encoded_size(&c, n, &cc, &dc, &nt);
-  const uint64_t R = (n + c.k - 1) / c.k;
-  const uint64_t chunks = index_chunks(c, index_nunits(c, R, cc));
-  const uint64_t blocks = (chunks + kIndexThreads - 1) / kIndexThreads;
-  return gc_host::align_up(blocks * sizeof(UnitAgg) + 64, 256) + gc_host::align_up(nt * sizeof(gc_tile), 256);
-}
-
-gc_status build_tiles_impl(const gc_codec& c, const uint8_t* ctrl, uint64_t ctrl_bytes, uint64_t n,
-                           gc_tile* tiles, UnitAgg* sums, uint32_t* status, cudaStream_t s) {
-  const uint64_t R = (n + c.k - 1) / c.k;
-  const uint64_t tr = kTileInts / c.k;
-  const uint64_t nt = (R + tr - 1) / tr;
-  if (nt == 0) return GC_OK;
-  IndexArgs a;
+gc_status plan_impl(const gc_codec& c, const gc_list* lists, const gc_list* one, uint64_t nlists,
+                    const gc_tile* tiles, uint64_t ntiles, const uint8_t* ctrl_pool, uint64_t ctrl_pool_bytes,
+                    gc_work* work, uint64_t cap, uint64_t* count, uint32_t* status, cudaStream_t s) {
+  if (cudaMemsetAsync(count, 0, 16, s) != cudaSuccess) return GC_ERR_CUDA;
+  if (nlists == 0) return GC_OK;
+  PlanArgs a = {};
   a.kind = c.kind;
   a.k = c.k;
   a.cg = c.cg;
   a.ld = c.ld;
-  a.ctrl = ctrl;
-  a.ctrl_bytes = ctrl_bytes;
-  a.n = n;
-  a.R = R;
-  a.nunits = index_nunits(c, R, ctrl_bytes);
-  if (c.kind == GC_PFD && 4 * a.nunits > ctrl_bytes) return GC_ERR_INVALID;
-  if (c.kind == GC_SCHEME && c.ld == GC_LD_BINARY && bin_ld_bytes(R, c.cg) > ctrl_bytes) return GC_ERR_INVALID;
-  a.nchunks = index_chunks(c, a.nunits);
+  a.lists = lists;
+  if (one) a.one = *one;
+  a.nlists = nlists;
   a.tiles = tiles;
-  a.ntiles = nt;
-  a.block_sums = sums;
+  a.ntiles = tiles ? ntiles : 0;
+  a.ctrl_pool = ctrl_pool;
+  a.ctrl_pool_bytes = ctrl_pool ? ctrl_pool_bytes : 0;
+  a.work = work;
+  a.cap = cap;
+  a.count = reinterpret_cast<unsigned long long*>(count);
   a.status = status;
-  const uint64_t blocks = (a.nchunks + kIndexThreads - 1) / kIndexThreads;
-  if (blocks == 0) return GC_ERR_INVALID;
-  // tile 0 is always all zeros; emit writes it too when unit 0 exists
-  cudaMemsetAsync(tiles, 0, sizeof(gc_tile), s);
-  k_index_sums<<<(unsigned)blocks, kIndexThreads, 0, s>>>(a);
-  k_index_scan<<<1, kIndexThreads, 0, s>>>(sums, blocks);
-  k_index_emit<<<(unsigned)blocks, kIndexThreads, 0, s>>>(a);
-  gc_host::count_launch(3);
+  k_plan_reserve<<<(unsigned)((nlists + 255) / 256), 256, 0, s>>>(a);
+  gc_host::count_launch();
+  if (cap) {
+    k_plan_fill<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(a);
+    gc_host::count_launch();
+  }
   return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+}
+
+gc_status decode_plan_impl(const gc_codec& c, const gc_work* work, const uint64_t* count, uint64_t work_cap,
+                           const uint8_t* ctrl_pool, uint64_t ctrl_pool_bytes, const uint32_t* data_pool,
+                           uint64_t data_pool_words, uint32_t* out_pool, uint64_t out_pool_len, int restore,
+                           uint32_t warps, uint32_t bps, uint32_t claim, unsigned char* scratch, uint32_t* status,
+                           cudaStream_t s) {
+  uint32_t* counter = reinterpret_cast<uint32_t*>(scratch);
+  unsigned long long* lb = reinterpret_cast<unsigned long long*>(scratch + kHdr);
+  if (cudaMemsetAsync(scratch, 0, 64, s) != cudaSuccess) return GC_ERR_CUDA;
+  if (restore && cudaMemsetAsync(lb, 0, work_cap * 8, s) != cudaSuccess) return GC_ERR_CUDA;
+  DecodeArgs a = {};
+  a.work = work;
+  a.count = reinterpret_cast<const unsigned long long*>(count);
+  a.work_cap = work_cap;
+  a.ctrl_pool = ctrl_pool;
+  a.ctrl_pool_bytes = ctrl_pool_bytes;
+  a.data_pool = data_pool;
+  a.data_pool_words = data_pool_words;
+  a.out_pool = out_pool;
+  a.out_pool_len = out_pool_len;
+  a.counter = counter;
+  a.lb = restore ? lb : nullptr;
+  a.cg = c.cg;
+  a.ld = c.ld;
+  a.claim = claim;
+  a.status = status;
+  const cudaError_t e = launch_decode(c.kind, c.k, restore != 0, a, warps, bps, work_cap, s);
+  return e == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+}
+
+uint64_t tiles_of(const gc_codec& c, uint64_t n) {
+  const uint64_t R = (n + c.k - 1) / c.k;
+  const uint64_t tr = kTileInts / c.k;
+  return (R + tr - 1) / tr;
 }
 
 }  // namespace
@@ -1015,32 +1242,18 @@ gc_status gc_decode_scratch_size(const gc_codec* codec, uint64_t n, int have_til
   gc_status st = gc_host::check_codec(codec);
   if (st != GC_OK) return st;
   if (!bytes) return GC_ERR_INVALID;
-  const uint64_t R = (n + codec->k - 1) / codec->k;
-  const uint64_t tr = kTileInts / codec->k;
-  const uint64_t nt = (R + tr - 1) / tr;
-  uint64_t b = gc_host::align_up(64, 256) + gc_host::align_up(nt * 8, 256);  // counters + look-back
-  if (!have_tiles) b += index_scratch(*codec, n);
+  const uint64_t nt = tiles_of(*codec, n);
+  // header (counter, counts) | plan | look-back words | [tile index, its scratch]
+  uint64_t b = kHdr + gc_host::align_up(nt * sizeof(gc_work), 256) + gc_host::align_up(nt * 8, 256);
+  if (!have_tiles)
+    b += gc_host::align_up(nt * sizeof(gc_tile), 256) + gc_host::align_up(gc_host::index_sums_bytes(*codec, n), 256);
   *bytes = b;
   return GC_OK;
 }
 
-gc_status gc_build_tiles(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes, uint64_t n,
-                         gc_tile* d_tiles, void* d_scratch, uint64_t scratch_bytes, uint32_t* d_status,
-                         void* stream) {
-  gc_host::reset_launches();
-  gc_status st = gc_host::check_codec(codec);
-  if (st != GC_OK) return st;
-  if (n == 0) return GC_OK;
-  if ((!d_ctrl && ctrl_bytes) || !d_tiles || !d_scratch) return GC_ERR_INVALID;
-  if (scratch_bytes < index_scratch(*codec, n)) return GC_ERR_NOSPACE;
-  return build_tiles_impl(*codec, d_ctrl, ctrl_bytes, n, d_tiles, (UnitAgg*)d_scratch, d_status,
-                          (cudaStream_t)stream);
-}
-
-gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes,
-                    const uint32_t* d_data, uint64_t data_words, uint64_t n, const gc_tile* d_tiles,
-                    uint32_t* d_out, int restore_docids, void* d_scratch, uint64_t scratch_bytes,
-                    uint32_t* d_status, void* stream) {
+gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes, const uint32_t* d_data,
+                    uint64_t data_words, uint64_t n, const gc_tile* d_tiles, uint32_t* d_out, int restore_docids,
+                    void* d_scratch, uint64_t scratch_bytes, uint32_t* d_status, void* stream) {
   gc_host::reset_launches();
   gc_status st = gc_host::check_codec(codec);
   if (st != GC_OK) return st;
@@ -1049,45 +1262,48 @@ gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_
   // words); a non-empty one needs a pointer
   if ((!d_ctrl && ctrl_bytes) || (!d_data && data_words) || !d_out || !d_scratch) return GC_ERR_INVALID;
   if (((uintptr_t)d_data & 15) != 0) return GC_ERR_INVALID;
+  if (n > 0xffffffffull || ctrl_bytes > 0xffffffffull || data_words > 0xffffffffull) return GC_ERR_UNSUPPORTED;
   uint64_t need = 0;
   gc_decode_scratch_size(codec, n, d_tiles != nullptr, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
   cudaStream_t s = (cudaStream_t)stream;
-  const uint64_t R = (n + codec->k - 1) / codec->k;
-  const uint64_t tr = kTileInts / codec->k;
-  const uint64_t nt = (R + tr - 1) / tr;
-  if (nt > 0xffffffffull - kMaxClaim * kMaxWarps) return GC_ERR_UNSUPPORTED;
+  const uint64_t nt = tiles_of(*codec, n);
   unsigned char* base = (unsigned char*)d_scratch;
-  uint32_t* counters = (uint32_t*)base;
-  unsigned long long* lb = (unsigned long long*)(base + gc_host::align_up(64, 256));
-  unsigned char* rest = base + gc_host::align_up(64, 256) + gc_host::align_up(nt * 8, 256);
-  const gc_tile* tiles = d_tiles;
+  uint64_t* count = reinterpret_cast<uint64_t*>(base + 64);
+  gc_work* work = reinterpret_cast<gc_work*>(base + kHdr + gc_host::align_up(nt * 8, 256));
+  unsigned char* rest = base + kHdr + gc_host::align_up(nt * 8, 256) + gc_host::align_up(nt * sizeof(gc_work), 256);
   uint32_t launches = 0;
+  const gc_tile* tiles = d_tiles;
   if (!tiles) {
-    const uint64_t chunks_bytes = index_scratch(*codec, n) - gc_host::align_up(nt * sizeof(gc_tile), 256);
-    gc_tile* built = (gc_tile*)(rest + chunks_bytes);
-    st = build_tiles_impl(*codec, d_ctrl, ctrl_bytes, n, built, (UnitAgg*)rest, d_status, s);
+    gc_tile* built = reinterpret_cast<gc_tile*>(rest);
+    void* sums = rest + gc_host::align_up(nt * sizeof(gc_tile), 256);
+    st = gc_host::build_tiles(*codec, d_ctrl, ctrl_bytes, n, built, sums, d_status, s);
     if (st != GC_OK) return st;
     launches += gc_host::launches();
     tiles = built;
   }
-  if (cudaMemsetAsync(base, 0, gc_host::align_up(64, 256) + (restore_docids ? nt * 8 : 0), s) != cudaSuccess)
-    return GC_ERR_CUDA;
-  DecodeArgs a = {};
-  a.one = ListRef{d_ctrl, ctrl_bytes, d_data, data_words, d_out, n};
-  a.one_tiles = tiles;
-  a.one_ntiles = nt;
-  a.counters = counters;
-  a.lb = lb;
-  a.cg = codec->cg;
-  a.ld = codec->ld;
-  a.restore = restore_docids;
-  a.status = d_status;
-  a.claim = kDefaultClaim;
+  // control bytes are staged from 16-byte boundaries: the pool starts at the
+  // boundary at or below d_ctrl (never below the allocation that holds it)
+  const uint8_t* pool = reinterpret_cast<const uint8_t*>((uintptr_t)d_ctrl & ~(uintptr_t)15);
+  const uint64_t lead = d_ctrl ? (uint64_t)(d_ctrl - pool) : 0;
+  gc_list one;
+  one.ctrl_off = lead;
+  one.data_off = 0;
+  one.out_off = 0;
+  one.n = (uint32_t)n;
+  one.tile_off = 0;
+  one.ctrl_bytes = (uint32_t)ctrl_bytes;
+  one.data_words = (uint32_t)data_words;
   gc_host::reset_launches();
-  cudaError_t e = launch_decode<false>(codec->kind, codec->k, a, kDefaultWarps, 0, nt, s);
+  st = plan_impl(*codec, nullptr, &one, 1, tiles, nt, pool, lead + ctrl_bytes, work, nt, count, d_status, s);
+  if (st != GC_OK) return st;
+  launches += gc_host::launches();
+  // the look-back words sit right after the header, as gc_decode_plan expects
+  gc_host::reset_launches();
+  st = decode_plan_impl(*codec, work, count, nt, pool, lead + ctrl_bytes, d_data, data_words, d_out, n,
+                        restore_docids, kDefaultWarps, 0, kDefaultClaim, base, d_status, s);
   gc_host::count_launch(launches);
-  return e == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+  return st;
 }
 
 gc_status gc_decode_paper(const gc_codec* codec, const uint8_t* d_buf, uint64_t buf_bytes, uint64_t n,
@@ -1096,41 +1312,71 @@ gc_status gc_decode_paper(const gc_codec* codec, const uint8_t* d_buf, uint64_t 
   gc_status st = gc_host::check_codec(codec);
   if (st != GC_OK) return st;
   if (!d_buf || buf_bytes < 4) return GC_ERR_INVALID;
+  if (((uintptr_t)d_buf & 15) != 0) return GC_ERR_INVALID;
   uint32_t off_words = 0;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(&off_words, d_buf, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return GC_ERR_CUDA;
   const uint64_t doff = 4ull * off_words;
   if (doff < 4 || doff > buf_bytes || (doff & 15)) return GC_ERR_CORRUPT;
-  return gc_decode(codec, d_buf + 4, doff - 4, (const uint32_t*)(d_buf + doff), (buf_bytes - doff) / 4, n,
-                   nullptr, d_out, restore_docids, d_scratch, scratch_bytes, d_status, stream);
+  // the control area starts at byte 4 of the buffer: decode from a view
+  // whose control pool is the buffer itself (16-byte aligned) and whose list
+  // control area starts at offset 4
+  gc_host::reset_launches();
+  if (n == 0) return GC_OK;
+  if (!d_out || !d_scratch) return GC_ERR_INVALID;
+  if (n > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  uint64_t need = 0;
+  gc_decode_scratch_size(codec, n, 0, &need);
+  if (scratch_bytes < need) return GC_ERR_NOSPACE;
+  const uint64_t ctrl_bytes = doff - 4;
+  const uint32_t* data = reinterpret_cast<const uint32_t*>(d_buf + doff);
+  const uint64_t data_words = (buf_bytes - doff) / 4;
+  const uint64_t nt = tiles_of(*codec, n);
+  unsigned char* base = (unsigned char*)d_scratch;
+  uint64_t* count = reinterpret_cast<uint64_t*>(base + 64);
+  gc_work* work = reinterpret_cast<gc_work*>(base + kHdr + gc_host::align_up(nt * 8, 256));
+  unsigned char* rest = base + kHdr + gc_host::align_up(nt * 8, 256) + gc_host::align_up(nt * sizeof(gc_work), 256);
+  gc_tile* built = reinterpret_cast<gc_tile*>(rest);
+  void* sums = rest + gc_host::align_up(nt * sizeof(gc_tile), 256);
+  st = gc_host::build_tiles(*codec, d_buf + 4, ctrl_bytes, n, built, sums, d_status, s);
+  if (st != GC_OK) return st;
+  uint32_t launches = gc_host::launches();
+  gc_list one;
+  one.ctrl_off = 4;
+  one.data_off = 0;
+  one.out_off = 0;
+  one.n = (uint32_t)n;
+  one.tile_off = 0;
+  one.ctrl_bytes = (uint32_t)ctrl_bytes;
+  one.data_words = (uint32_t)data_words;
+  gc_host::reset_launches();
+  st = plan_impl(*codec, nullptr, &one, 1, built, nt, d_buf, doff, work, nt, count, d_status, s);
+  if (st != GC_OK) return st;
+  launches += gc_host::launches();
+  gc_host::reset_launches();
+  st = decode_plan_impl(*codec, work, count, nt, d_buf, doff, data, data_words, d_out, n, restore_docids,
+                        kDefaultWarps, 0, kDefaultClaim, base, d_status, s);
+  gc_host::count_launch(launches);
+  return st;
 }
 
 gc_status gc_plan_batch(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists, const gc_tile* d_tile_pool,
-                        uint64_t tile_pool_len, gc_work* d_work, uint64_t work_cap, uint64_t* d_count,
-                        uint32_t* d_status, void* stream) {
+                        uint64_t tile_pool_len, const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
+                        gc_work* d_work, uint64_t work_cap, uint64_t* d_count, uint32_t* d_status, void* stream) {
   gc_host::reset_launches();
   gc_status st = gc_host::check_codec(codec);
   if (st != GC_OK) return st;
   if (!d_count || (nlists && (!d_lists || !d_work))) return GC_ERR_INVALID;
   if (nlists > 0xffffffffull || work_cap > 0xffffffffull) return GC_ERR_UNSUPPORTED;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(d_count, 0, 8, s) != cudaSuccess) return GC_ERR_CUDA;
-  if (nlists == 0) return GC_OK;
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d_count);
-  k_plan_reserve<<<(unsigned)((nlists + 255) / 256), 256, 0, s>>>(d_lists, nlists, codec->k, d_work, work_cap, cnt,
-                                                                  d_status);
-  if (work_cap)
-    k_plan_fill<<<(unsigned)((work_cap + 255) / 256), 256, 0, s>>>(d_lists, nlists, d_tile_pool,
-                                                                   d_tile_pool ? tile_pool_len : 0, d_work,
-                                                                   work_cap, cnt, d_status);
-  gc_host::count_launch(work_cap ? 2 : 1);
-  return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+  if (((uintptr_t)d_work & 15) != 0) return GC_ERR_INVALID;
+  return plan_impl(*codec, d_lists, nullptr, nlists, d_tile_pool, tile_pool_len, d_ctrl_pool, ctrl_pool_bytes, d_work,
+                   work_cap, d_count, d_status, (cudaStream_t)stream);
 }
 
 gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes) {
   if (!bytes) return GC_ERR_INVALID;
-  *bytes = gc_host::align_up(64, 256) + gc_host::align_up(work_cap * 8, 256);
+  *bytes = kHdr + gc_host::align_up(work_cap * 8, 256);
   return GC_OK;
 }
 
@@ -1146,39 +1392,18 @@ gc_status gc_decode_plan(const gc_codec* codec, const gc_work* d_work, const uin
   if (!d_work || !d_count || (!d_ctrl_pool && ctrl_pool_bytes) || (!d_data_pool && data_pool_words) ||
       !d_out_pool || !d_scratch)
     return GC_ERR_INVALID;
-  if (((uintptr_t)d_data_pool & 15) != 0 || ((uintptr_t)d_work & 15) != 0) return GC_ERR_INVALID;
-  if (work_cap > 0xffffffffull - kMaxClaim * kMaxWarps) return GC_ERR_UNSUPPORTED;
+  if (((uintptr_t)d_data_pool & 15) != 0 || ((uintptr_t)d_ctrl_pool & 15) != 0 || ((uintptr_t)d_work & 15) != 0)
+    return GC_ERR_INVALID;
+  if (work_cap > 0xffffffffull - kMaxClaim * 64ull) return GC_ERR_UNSUPPORTED;
   uint64_t need = 0;
   gc_decode_plan_scratch_size(work_cap, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
   uint32_t warps, bps, claim;
   st = launch_shape(launch, &warps, &bps, &claim);
   if (st != GC_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  unsigned char* base = (unsigned char*)d_scratch;
-  uint32_t* counters = (uint32_t*)base;
-  unsigned long long* lb = (unsigned long long*)(base + gc_host::align_up(64, 256));
-  if (cudaMemsetAsync(base, 0, 64, s) != cudaSuccess) return GC_ERR_CUDA;
-  if (restore_docids && cudaMemsetAsync(lb, 0, work_cap * 8, s) != cudaSuccess) return GC_ERR_CUDA;
-  DecodeArgs a = {};
-  a.work = d_work;
-  a.work_count = reinterpret_cast<const unsigned long long*>(d_count);
-  a.work_cap = work_cap;
-  a.ctrl_pool = d_ctrl_pool;
-  a.ctrl_pool_bytes = ctrl_pool_bytes;
-  a.data_pool = d_data_pool;
-  a.data_pool_words = data_pool_words;
-  a.out_pool = d_out_pool;
-  a.out_pool_len = out_pool_len;
-  a.counters = counters;
-  a.lb = lb;
-  a.cg = codec->cg;
-  a.ld = codec->ld;
-  a.claim = claim;
-  a.restore = restore_docids;
-  a.status = d_status;
-  cudaError_t e = launch_decode<true>(codec->kind, codec->k, a, warps, bps, work_cap, s);
-  return e == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+  return decode_plan_impl(*codec, d_work, d_count, work_cap, d_ctrl_pool, ctrl_pool_bytes, d_data_pool,
+                          data_pool_words, d_out_pool, out_pool_len, restore_docids, warps, bps, claim,
+                          (unsigned char*)d_scratch, d_status, (cudaStream_t)stream);
 }
 
 gc_status gc_decode_batch_scratch_size(uint64_t nlists, uint64_t max_tiles, uint64_t* bytes) {
@@ -1186,7 +1411,7 @@ gc_status gc_decode_batch_scratch_size(uint64_t nlists, uint64_t max_tiles, uint
   if (!bytes) return GC_ERR_INVALID;
   uint64_t dec = 0;
   gc_decode_plan_scratch_size(max_tiles, &dec);
-  *bytes = gc_host::align_up(64, 256) + gc_host::align_up(max_tiles * sizeof(gc_work), 256) + dec;
+  *bytes = kHdr + gc_host::align_up(max_tiles * sizeof(gc_work), 256) + dec;
   return GC_OK;
 }
 
@@ -1203,8 +1428,8 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
   if (!d_lists || (!d_ctrl_pool && ctrl_pool_bytes) || (!d_data_pool && data_pool_words) || !d_out_pool ||
       !d_scratch)
     return GC_ERR_INVALID;
-  if (((uintptr_t)d_data_pool & 15) != 0) return GC_ERR_INVALID;
-  if (max_tiles > 0xffffffffull - kMaxClaim * kMaxWarps || nlists > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  if (((uintptr_t)d_data_pool & 15) != 0 || ((uintptr_t)d_ctrl_pool & 15) != 0) return GC_ERR_INVALID;
+  if (max_tiles > 0xffffffffull - kMaxClaim * 64ull || nlists > 0xffffffffull) return GC_ERR_UNSUPPORTED;
   uint64_t need = 0;
   gc_decode_batch_scratch_size(nlists, max_tiles, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
@@ -1212,16 +1437,17 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
   st = launch_shape(launch, &warps, &bps, &claim);
   if (st != GC_OK) return st;
   unsigned char* base = (unsigned char*)d_scratch;
-  uint64_t* count = (uint64_t*)base;
-  gc_work* work = (gc_work*)(base + gc_host::align_up(64, 256));
-  unsigned char* rest = base + gc_host::align_up(64, 256) + gc_host::align_up(max_tiles * sizeof(gc_work), 256);
-  st = gc_plan_batch(codec, d_lists, nlists, d_tile_pool, tile_pool_len, work, max_tiles, count, d_status, stream);
+  uint64_t* count = reinterpret_cast<uint64_t*>(base + 64);
+  gc_work* work = reinterpret_cast<gc_work*>(base + kHdr);
+  unsigned char* rest = base + kHdr + gc_host::align_up(max_tiles * sizeof(gc_work), 256);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = plan_impl(*codec, d_lists, nullptr, nlists, d_tile_pool, tile_pool_len, d_ctrl_pool, ctrl_pool_bytes, work,
+                 max_tiles, count, d_status, s);
   if (st != GC_OK) return st;
   const uint32_t planned = gc_host::launches();
-  uint64_t dec = 0;
-  gc_decode_plan_scratch_size(max_tiles, &dec);
-  st = gc_decode_plan(codec, work, count, max_tiles, d_ctrl_pool, ctrl_pool_bytes, d_data_pool, data_pool_words,
-                      d_out_pool, out_pool_len, restore_docids, launch, rest, dec, d_status, stream);
+  gc_host::reset_launches();
+  st = decode_plan_impl(*codec, work, count, max_tiles, d_ctrl_pool, ctrl_pool_bytes, d_data_pool, data_pool_words,
+                        d_out_pool, out_pool_len, restore_docids, warps, bps, claim, rest, d_status, s);
   gc_host::count_launch(planned);
   return st;
 }

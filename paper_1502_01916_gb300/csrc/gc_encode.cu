@@ -14,6 +14,8 @@
 //     8/16/32 rows by dynamic programming, one thread per list.
 //   - Group-PFD (Sec 6.2, Steps 1-4): one warp per 32-row frame finds b,
 //     the exceptions and their width.
+// Tile records also carry skip entries (Sec 7.5 keeps a docID every so many
+// postings): the docID before each tile, from per-tile gap sums and a scan.
 // Row maxima are the effective widths of the k ints of each row (Sec 4.2).
 // Lists are laid out back to back; tile records for tiles >= 1 (or all
 // tiles, for a single list) are written by the same passes.
@@ -38,6 +40,7 @@ struct Enc {
   uint32_t kind, k, cg, ld, T, tr;
   uint32_t include_tile0;
   uint64_t nlists, Rtot, Utot;  // Utot: codec units index space
+  uint64_t Atot;                // tiles of all lists, tile 0 included
   const uint32_t* gaps;
   // per list
   const uint32_t* n;
@@ -45,6 +48,8 @@ struct Enc {
   const uint64_t* rowbase;   // nlists + 1
   const uint64_t* tilebase;  // nlists + 1
   const uint64_t* ubase;     // nlists + 1 (PFD frames, AFOR blocks + 1, GS segments)
+  const uint64_t* abase;     // nlists + 1: first tile of each list, tile 0 included
+  uint64_t* tsum;            // Atot + 1: gap sum per tile, then its exclusive scan
   uint64_t* csize;           // nlists + 1: control bytes, then exclusive offsets
   uint64_t* dsize;           // nlists + 1: data words, then exclusive offsets
   uint64_t* aux;             // nlists + 1: GS selectors / AFOR frames per list, then offsets
@@ -94,6 +99,8 @@ __device__ __forceinline__ void put_tile(const Enc& e, uint64_t list, uint64_t t
   g.ctrl_bit = ctrl_bit;
   g.exc_off = (uint32_t)exc;
   g.row_skip = (uint32_t)skip;
+  g.base = 0;  // written by k_put_bases
+  g.flags = t == 0 ? GC_TILE_BASE : 0u;
   e.tiles[tile_slot(e, list, t)] = g;
 }
 
@@ -228,6 +235,8 @@ __global__ void k_lists_out(Enc e) {
     d.out_off = e.in_off[i];
     d.n = e.n[i];
     d.tile_off = (uint32_t)e.tilebase[i];
+    d.ctrl_bytes = (uint32_t)(e.csize[i + 1] - e.csize[i]);
+    d.data_words = (uint32_t)(e.dsize[i + 1] - e.dsize[i]);
     e.lists[i] = d;
   }
   if (i == 0) {
@@ -235,6 +244,33 @@ __global__ void k_lists_out(Enc e) {
     e.totals[1] = e.dsize[e.nlists];
     e.totals[2] = e.tilebase[e.nlists];
   }
+}
+
+// Skip entries: one warp per tile (tile 0 included) sums the tile's gaps;
+// after an exclusive scan of the sums over all tiles, the base of tile t of
+// list L is its scanned value minus that of the list's tile 0 (sums of
+// uint32 gaps modulo 2^32, the docID before the tile, Sec 2.1.1).
+__global__ void k_tile_sums(Enc e) {
+  const uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (g >= e.Atot) return;  // uniform per warp
+  const uint64_t L = find_list(e.abase, e.nlists, g);
+  const uint64_t i0 = (g - e.abase[L]) * 1024;
+  const uint64_t i1 = min64(e.n[L], i0 + 1024);
+  uint32_t s = 0;
+  for (uint64_t i = i0 + lane_id(); i < i1; i += 32) s += e.gaps[e.in_off[L] + i];
+  s = warp_sum(s);
+  if (lane_id() == 0) e.tsum[g] = s;
+}
+
+__global__ void k_put_bases(Enc e) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= e.Atot || !e.tiles) return;
+  const uint64_t L = find_list(e.abase, e.nlists, g);
+  const uint64_t t = g - e.abase[L];
+  if (t == 0 && !e.include_tile0) return;
+  gc_tile* r = e.tiles + tile_slot(e, L, t);
+  r->base = (uint32_t)(e.tsum[g] - e.tsum[e.abase[L]]);
+  r->flags = GC_TILE_BASE;
 }
 
 // ------------------------------------------------------- Group-PFD
@@ -686,8 +722,8 @@ struct Bump {
 };
 
 struct Plan {
-  uint64_t nlists = 0, Rtot = 0, Utot = 0, tiles = 0, ctrl_cap = 0, data_cap = 0;
-  std::vector<uint64_t> rowbase, tilebase, ubase;
+  uint64_t nlists = 0, Rtot = 0, Utot = 0, tiles = 0, ctrl_cap = 0, data_cap = 0, Atot = 0;
+  std::vector<uint64_t> rowbase, tilebase, ubase, abase;
 };
 
 Plan make_plan(const gc_codec& c, const uint32_t* h_n, uint64_t nlists, bool include0) {
@@ -696,14 +732,17 @@ Plan make_plan(const gc_codec& c, const uint32_t* h_n, uint64_t nlists, bool inc
   p.rowbase.resize(nlists + 1);
   p.tilebase.resize(nlists + 1);
   p.ubase.resize(nlists + 1);
+  p.abase.resize(nlists + 1);
   const uint64_t k = c.k, tr = 1024 / k;
-  uint64_t rb = 0, tb = 0, ub = 0;
+  uint64_t rb = 0, tb = 0, ub = 0, ab = 0;
   for (uint64_t i = 0; i < nlists; ++i) {
     p.rowbase[i] = rb;
     p.tilebase[i] = tb;
     p.ubase[i] = ub;
+    p.abase[i] = ab;
     const uint64_t R = (h_n[i] + k - 1) / k;
     const uint64_t nt = (R + tr - 1) / tr;
+    ab += nt;
     rb += R;
     tb += include0 ? nt : (nt ? nt - 1 : 0);
     switch (c.kind) {
@@ -720,6 +759,8 @@ Plan make_plan(const gc_codec& c, const uint32_t* h_n, uint64_t nlists, bool inc
   p.rowbase[nlists] = rb;
   p.tilebase[nlists] = tb;
   p.ubase[nlists] = ub;
+  p.abase[nlists] = ab;
+  p.Atot = ab;
   p.Rtot = rb;
   p.Utot = ub;
   p.tiles = tb;
@@ -729,7 +770,7 @@ Plan make_plan(const gc_codec& c, const uint32_t* h_n, uint64_t nlists, bool inc
 // Lay out the scratch (base == nullptr: size only).
 uint64_t layout(const gc_codec& c, const Plan& p, unsigned char* base, Enc& e, uint64_t** tmp,
                 uint32_t** d_n, uint64_t** d_in_off, uint64_t** d_rowbase, uint64_t** d_tilebase,
-                uint64_t** d_ubase) {
+                uint64_t** d_ubase, uint64_t** d_abase) {
   Bump b{base};
   const uint64_t L = p.nlists;
   *d_n = b.take<uint32_t>(L);
@@ -737,13 +778,15 @@ uint64_t layout(const gc_codec& c, const Plan& p, unsigned char* base, Enc& e, u
   *d_rowbase = b.take<uint64_t>(L + 1);
   *d_tilebase = b.take<uint64_t>(L + 1);
   *d_ubase = b.take<uint64_t>(L + 1);
+  *d_abase = b.take<uint64_t>(L + 1);
+  e.tsum = b.take<uint64_t>(p.Atot + 1);
   e.csize = b.take<uint64_t>(L + 1);
   e.dsize = b.take<uint64_t>(L + 1);
   e.aux = b.take<uint64_t>(L + 1);
   e.eb = b.take<uint8_t>(p.Rtot + 1);
   e.rlist = b.take<uint32_t>(p.Rtot + 1);
   const uint64_t R1 = p.Rtot + 1, U1 = p.Utot + 1;
-  uint64_t scan_n = L + 1;
+  uint64_t scan_n = std::max(L + 1, p.Atot + 1);
   switch (c.kind) {
     case GC_PFD:
       e.s0 = b.take<uint64_t>(U1);
@@ -797,10 +840,10 @@ gc_status encode_impl(const gc_codec& c, const uint32_t* d_gaps, const uint32_t*
   Enc e = {};
   uint64_t* tmp;
   uint32_t* dn;
-  uint64_t *din, *drb, *dtb, *dub;
-  const uint64_t need = layout(c, p, nullptr, e, &tmp, &dn, &din, &drb, &dtb, &dub);
+  uint64_t *din, *drb, *dtb, *dub, *dab;
+  const uint64_t need = layout(c, p, nullptr, e, &tmp, &dn, &din, &drb, &dtb, &dub, &dab);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
-  layout(c, p, (unsigned char*)d_scratch, e, &tmp, &dn, &din, &drb, &dtb, &dub);
+  layout(c, p, (unsigned char*)d_scratch, e, &tmp, &dn, &din, &drb, &dtb, &dub, &dab);
   e.kind = c.kind;
   e.k = c.k;
   e.cg = c.cg;
@@ -817,6 +860,8 @@ gc_status encode_impl(const gc_codec& c, const uint32_t* d_gaps, const uint32_t*
   e.rowbase = drb;
   e.tilebase = dtb;
   e.ubase = dub;
+  e.abase = dab;
+  e.Atot = p.Atot;
   e.ctrl = d_ctrl;
   e.data = d_data;
   e.tiles = d_tiles;
@@ -830,6 +875,7 @@ gc_status encode_impl(const gc_codec& c, const uint32_t* d_gaps, const uint32_t*
   cudaMemcpyAsync(drb, p.rowbase.data(), (nlists + 1) * 8, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(dtb, p.tilebase.data(), (nlists + 1) * 8, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(dub, p.ubase.data(), (nlists + 1) * 8, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(dab, p.abase.data(), (nlists + 1) * 8, cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(d_ctrl, 0, gc_host::align_up(p.ctrl_cap, 4) < ctrl_cap ? gc_host::align_up(p.ctrl_cap, 4) : ctrl_cap, s);
   cudaMemsetAsync(d_data, 0, p.data_cap * 4, s);
   if (p.Rtot) {
@@ -918,15 +964,17 @@ gc_status encode_impl(const gc_codec& c, const uint32_t* d_gaps, const uint32_t*
       }
       break;
   }
-  if (d_lists || d_totals) {
-    Enc e2 = e;
-    if (!d_lists) {
-      // single list: only the totals
-    }
-    if (d_lists) {
-      k_lists_out<<<lb, kT, 0, s>>>(e2);
-      gc_host::count_launch();
-    }
+  if (d_tiles && p.Atot) {
+    e.tiles = d_tiles;
+    k_tile_sums<<<blocks_for(p.Atot * 32), kT, 0, s>>>(e);
+    gc_host::count_launch();
+    scan_u64(e.tsum, p.Atot, tmp, s);
+    k_put_bases<<<blocks_for(p.Atot), kT, 0, s>>>(e);
+    gc_host::count_launch();
+  }
+  if (d_lists) {
+    k_lists_out<<<lb, kT, 0, s>>>(e);
+    gc_host::count_launch();
   }
   return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;
 }
@@ -951,8 +999,8 @@ gc_status gc_encode_batch_scratch_size(const gc_codec* codec, const uint32_t* h_
   Enc e = {};
   uint64_t* tmp;
   uint32_t* dn;
-  uint64_t *din, *drb, *dtb, *dub;
-  *bytes = layout(*codec, p, nullptr, e, &tmp, &dn, &din, &drb, &dtb, &dub);
+  uint64_t *din, *drb, *dtb, *dub, *dab;
+  *bytes = layout(*codec, p, nullptr, e, &tmp, &dn, &din, &drb, &dtb, &dub, &dab);
   return GC_OK;
 }
 
@@ -1000,9 +1048,9 @@ gc_status gc_encode(const gc_codec* codec, const uint32_t* d_gaps, uint64_t n, u
   Enc e = {};
   uint64_t* tmp;
   uint32_t* dn;
-  uint64_t *din, *drb, *dtb, *dub;
+  uint64_t *din, *drb, *dtb, *dub, *dab;
   const Plan p = make_plan(*codec, &n32, 1, true);
-  layout(*codec, p, (unsigned char*)d_scratch, e, &tmp, &dn, &din, &drb, &dtb, &dub);
+  layout(*codec, p, (unsigned char*)d_scratch, e, &tmp, &dn, &din, &drb, &dtb, &dub, &dab);
   k_single_sizes<<<1, 1, 0, s>>>(e.csize, e.dsize, d_sizes);
   gc_host::count_launch();
   return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;

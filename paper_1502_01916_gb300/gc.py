@@ -22,6 +22,8 @@ import torch
 
 __all__ = [
     "SIMPLE", "SCHEME", "AFOR", "PFD", "LD_BINARY", "LD_CU", "LD_IU", "TILE_INTS", "TILE_BYTES", "LIST_BYTES",
+    "TILE_BASE", "WORK_VEC_SHIFT", "WORK_BIT_SHIFT", "WORK_SKIP_SHIFT", "WORK_HAS_BASE", "WORK_PUBLISH",
+    "TILE_DTYPE", "LIST_DTYPE", "WORK_DTYPE",
     "WORK_BYTES", "GcError", "gc_work", "gc_plan_batch", "gc_decode_plan_scratch_size", "gc_decode_plan", "Plan",
     "plan_index",
     "gc_codec", "gc_tile", "gc_list", "gc_launch", "library_path", "load", "make_codec",
@@ -61,12 +63,14 @@ class gc_codec(ctypes.Structure):
 
 class gc_tile(ctypes.Structure):
     _fields_ = [("lane_bit", ctypes.c_uint64), ("ctrl_bit", ctypes.c_uint64),
-                ("exc_off", ctypes.c_uint32), ("row_skip", ctypes.c_uint32)]
+                ("exc_off", ctypes.c_uint32), ("row_skip", ctypes.c_uint32),
+                ("base", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class gc_list(ctypes.Structure):
     _fields_ = [("ctrl_off", ctypes.c_uint64), ("data_off", ctypes.c_uint64),
-                ("out_off", ctypes.c_uint64), ("n", ctypes.c_uint32), ("tile_off", ctypes.c_uint32)]
+                ("out_off", ctypes.c_uint64), ("n", ctypes.c_uint32), ("tile_off", ctypes.c_uint32),
+                ("ctrl_bytes", ctypes.c_uint32), ("data_words", ctypes.c_uint32)]
 
 
 class gc_launch(ctypes.Structure):
@@ -75,10 +79,24 @@ class gc_launch(ctypes.Structure):
 
 
 class gc_work(ctypes.Structure):
-    _fields_ = [("ctrl_off", ctypes.c_uint64), ("data_off", ctypes.c_uint64), ("out_off", ctypes.c_uint64),
-                ("n", ctypes.c_uint32), ("tile", ctypes.c_uint32), ("lane_bit", ctypes.c_uint64),
-                ("ctrl_bit", ctypes.c_uint64), ("exc_off", ctypes.c_uint32), ("row_skip", ctypes.c_uint32),
-                ("list", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+    _fields_ = [("ctrl_at", ctypes.c_uint64), ("data_at", ctypes.c_uint64), ("out_at", ctypes.c_uint64),
+                ("ctrl_bit", ctypes.c_uint64), ("ctrl_bytes", ctypes.c_uint32), ("tile", ctypes.c_uint32),
+                ("list", ctypes.c_uint32), ("base", ctypes.c_uint32), ("exc_at", ctypes.c_uint32),
+                ("win_at", ctypes.c_int32), ("shape", ctypes.c_uint32), ("win_len", ctypes.c_uint16),
+                ("exc_len", ctypes.c_uint16)]
+
+
+TILE_BASE = 1
+WORK_VEC_SHIFT, WORK_BIT_SHIFT, WORK_SKIP_SHIFT = 10, 19, 24
+WORK_HAS_BASE, WORK_PUBLISH = 1 << 29, 1 << 30
+TILE_DTYPE = np.dtype([("lane_bit", "<u8"), ("ctrl_bit", "<u8"), ("exc_off", "<u4"), ("row_skip", "<u4"),
+                       ("base", "<u4"), ("flags", "<u4")])
+LIST_DTYPE = np.dtype([("ctrl_off", "<u8"), ("data_off", "<u8"), ("out_off", "<u8"), ("n", "<u4"),
+                       ("tile_off", "<u4"), ("ctrl_bytes", "<u4"), ("data_words", "<u4")])
+WORK_DTYPE = np.dtype([("ctrl_at", "<u8"), ("data_at", "<u8"), ("out_at", "<u8"), ("ctrl_bit", "<u8"),
+                       ("ctrl_bytes", "<u4"), ("tile", "<u4"), ("list", "<u4"), ("base", "<u4"),
+                       ("exc_at", "<u4"), ("win_at", "<i4"), ("shape", "<u4"), ("win_len", "<u2"),
+                       ("exc_len", "<u2")])
 
 
 TILE_BYTES = ctypes.sizeof(gc_tile)
@@ -121,7 +139,7 @@ def load():
             "gc_decode_batch_scratch_size": (_I, [_U64, _U64, _U64P]),
             "gc_decode_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I, _U64,
                                      ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
-            "gc_plan_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V]),
+            "gc_plan_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V]),
             "gc_decode_plan_scratch_size": (_I, [_U64, _U64P]),
             "gc_decode_plan": (_I, [_CP, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I,
                                     ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
@@ -260,11 +278,11 @@ def gc_decode_batch(codec, d_lists, nlists, d_ctrl_pool, d_data_pool, d_tile_poo
                                   _ptr(d_status), _stream(stream)), "gc_decode_batch")
 
 
-def gc_plan_batch(codec, d_lists, nlists, d_tile_pool, d_work, d_count, d_status, stream=None):
+def gc_plan_batch(codec, d_lists, nlists, d_tile_pool, d_ctrl_pool, d_work, d_count, d_status, stream=None):
     tile_len = d_tile_pool.numel() // TILE_BYTES if d_tile_pool is not None else 0
     _check(load().gc_plan_batch(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_tile_pool), tile_len,
-                                _ptr(d_work), d_work.numel() // WORK_BYTES, _ptr(d_count), _ptr(d_status),
-                                _stream(stream)), "gc_plan_batch")
+                                _ptr(d_ctrl_pool), d_ctrl_pool.numel(), _ptr(d_work), d_work.numel() // WORK_BYTES,
+                                _ptr(d_count), _ptr(d_status), _stream(stream)), "gc_plan_batch")
 
 
 def gc_decode_plan_scratch_size(work_cap: int) -> int:
@@ -410,7 +428,7 @@ class Index:
     codec: gc_codec
     lengths: np.ndarray      # uint32 per list
     out_offsets: np.ndarray  # uint64 per list: first output int
-    lists: torch.Tensor      # nlists * 32 bytes
+    lists: torch.Tensor      # nlists * 40 bytes (gc_list)
     ctrl: torch.Tensor
     data: torch.Tensor
     tiles: torch.Tensor
@@ -477,7 +495,7 @@ def _bounds(codec: gc_codec, h_n: np.ndarray):
 class Plan:
     """The work plan of an index (gc_plan_batch): one gc_work per tile."""
     work: torch.Tensor   # max_tiles * 64 bytes
-    count: torch.Tensor  # one int64: the number of tiles
+    count: torch.Tensor  # two int64: tiles, tiles that take their prefix by look-back
 
     def nbytes(self) -> int:
         return self.work.numel()
@@ -487,9 +505,9 @@ def plan_index(index: Index, status=None, stream=None) -> Plan:
     """Build the index's work plan on the device (gc_plan_batch)."""
     dev = index.data.device
     work = torch.empty(max(1, index.max_tiles) * WORK_BYTES, dtype=torch.uint8, device=dev)
-    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    count = torch.zeros(2, dtype=torch.int64, device=dev)
     st = new_status(dev) if status is None else status
-    gc_plan_batch(index.codec, index.lists, index.nlists, index.tiles, work, count, st, stream)
+    gc_plan_batch(index.codec, index.lists, index.nlists, index.tiles, index.ctrl, work, count, st, stream)
     check_status(st, "gc_plan_batch")
     return Plan(work, count)
 

@@ -47,9 +47,15 @@ def test_library_exports_every_declared_symbol(gc):
 
 def test_struct_sizes_match_header(gc):
     assert ctypes.sizeof(gc.gc_codec) == 24
-    assert ctypes.sizeof(gc.gc_tile) == 24
-    assert ctypes.sizeof(gc.gc_list) == 32
-    assert O.TILE_DTYPE.itemsize == 24
+    assert ctypes.sizeof(gc.gc_tile) == 32
+    assert ctypes.sizeof(gc.gc_list) == 40
+    assert ctypes.sizeof(gc.gc_work) == 64
+    assert ctypes.sizeof(gc.gc_launch) == 12
+    assert O.TILE_DTYPE.itemsize == 32
+    assert gc.TILE_DTYPE == O.TILE_DTYPE
+    assert gc.LIST_DTYPE.itemsize == 40 and gc.WORK_DTYPE.itemsize == 64
+    for name, _ in gc.gc_work._fields_:
+        assert getattr(gc.gc_work, name).offset == gc.WORK_DTYPE.fields[name][1], name
 
 
 @pytest.mark.parametrize("zeta", [0.0, 0.01, 0.05, 0.1, 0.125, 0.3, 0.5, 0.99, 1.0, 2.0])
@@ -89,16 +95,15 @@ def test_bad_codec_rejected_on_host(gc, bad):
 def test_decode_rejects_missing_buffers_and_misaligned_data(gc):
     lib = gc.load()
     c = gc.make_codec(gc.SIMPLE, 32)
-    buf = (ctypes.c_uint8 * 64)()
-    base = ctypes.addressof(buf)
+    buf = (ctypes.c_uint8 * 96)()
+    base = (ctypes.addressof(buf) + 15) // 16 * 16
     # NULL output
     assert lib.gc_decode(ctypes.byref(c), base, 4, base, 4, 10, None, None, 1, base, 1 << 20, None, None) == 1
     # data not 16-byte aligned
-    mis = (base + 15) // 16 * 16 + 4
+    mis = base + 4
     assert lib.gc_decode(ctypes.byref(c), base, 4, mis, 4, 10, None, base, 1, base, 1 << 20, None, None) == 1
     # scratch too small
-    assert lib.gc_decode(ctypes.byref(c), base, 4, (base + 15) // 16 * 16, 4, 10, None, base, 1, base, 0,
-                         None, None) == 2
+    assert lib.gc_decode(ctypes.byref(c), base, 4, base, 4, 10, None, base, 1, base, 0, None, None) == 2
     # n = 0 is a no-op
     assert lib.gc_decode(ctypes.byref(c), None, 0, None, 0, 0, None, None, 1, None, 0, None, None) == 0
 

@@ -79,12 +79,16 @@ def test_decode_matches_oracle(gc, c):
         assert (want_gaps == g).all()
         want_ids = O.prefix_sum(want_gaps)
         tiles_ref = O.tile_index(oc, ctrl, n)
+        tiles_skip = O.tile_index(oc, ctrl, n, g)
         d_ctrl, d_data = upload_u8(ctrl), upload_u32(data)
         enc = gc.EncodedList(gcc, n, d_ctrl, d_data[:len(data)], upload_u8(tiles_ref.view(np.uint8)))
         got = gc.as_u32(gc.decode(enc, restore_docids=False))
         assert (got == want_gaps).all(), f"gaps n={n}"
         got = gc.as_u32(gc.decode(enc, restore_docids=True))
-        assert (got == want_ids).all(), f"docids n={n}"
+        assert (got == want_ids).all(), f"docids by look-back n={n}"
+        enc_s = gc.EncodedList(gcc, n, d_ctrl, d_data[:len(data)], upload_u8(tiles_skip.view(np.uint8)))
+        got = gc.as_u32(gc.decode(enc_s, restore_docids=True))
+        assert (got == want_ids).all(), f"docids from skip entries n={n}"
         built = gc.build_tiles(gcc, d_ctrl, n).cpu().numpy()
         assert built.tobytes() == tiles_ref.tobytes(), f"tile index n={n}"
         got = gc.as_u32(gc.decode(enc, restore_docids=True, use_tiles=False))
@@ -156,7 +160,7 @@ def test_encode_byte_identical(gc, c):
         enc = gc.encode(gcc, g)
         assert enc.ctrl.cpu().numpy().tobytes() == ctrl.tobytes(), f"control n={n}"
         assert (gc.as_u32(enc.data) == data).all(), f"data n={n}"
-        assert enc.tiles.cpu().numpy().tobytes() == O.tile_index(oc, ctrl, n).tobytes(), f"tiles n={n}"
+        assert enc.tiles.cpu().numpy().tobytes() == O.tile_index(oc, ctrl, n, g).tobytes(), f"tiles n={n}"
 
 
 # ------------------------------------------------------------------- batch
@@ -177,8 +181,7 @@ def test_batch_encode_decode(gc, c):
     oc, gcc = pair(gc, c)
     lens, gaps, off = small_index(11 + c[1])
     idx = gc.encode_index(gcc, upload_u32(gaps), lens)
-    lists = idx.lists.cpu().numpy().view(np.dtype([("ctrl_off", "<u8"), ("data_off", "<u8"), ("out_off", "<u8"),
-                                                    ("n", "<u4"), ("tile_off", "<u4")]))
+    lists = idx.lists.cpu().numpy().view(gc.LIST_DTYPE)
     ctrl_pool = idx.ctrl.cpu().numpy()
     data_pool = gc.as_u32(idx.data)
     tiles_pool = idx.tiles.cpu().numpy().view(O.TILE_DTYPE)
@@ -188,9 +191,10 @@ def test_batch_encode_decode(gc, c):
         ctrl, data = O.encode(oc, g)
         d = lists[i]
         assert int(d["n"]) == n and int(d["out_off"]) == int(off[i])
+        assert int(d["ctrl_bytes"]) == len(ctrl) and int(d["data_words"]) == len(data), f"sizes list {i}"
         assert ctrl_pool[d["ctrl_off"]:d["ctrl_off"] + len(ctrl)].tobytes() == ctrl.tobytes(), f"list {i}"
         assert (data_pool[d["data_off"]:d["data_off"] + len(data)] == data).all(), f"list {i}"
-        tref = O.tile_index(oc, ctrl, n)
+        tref = O.tile_index(oc, ctrl, n, g)
         if len(tref) > 1:
             got_t = tiles_pool[d["tile_off"]:d["tile_off"] + len(tref) - 1]
             assert got_t.tobytes() == tref[1:].tobytes(), f"tiles list {i}"
@@ -201,7 +205,7 @@ def test_batch_encode_decode(gc, c):
     assert (gc.as_u32(out)[:len(gaps)] == gaps).all()
 
 
-@pytest.mark.parametrize("warps,bps,claim", [(1, 1, 1), (4, 2, 2), (8, 0, 0), (16, 0, 7), (2, 1, 64)])
+@pytest.mark.parametrize("warps,bps,claim", [(1, 1, 1), (4, 2, 2), (8, 0, 0), (16, 0, 7), (2, 1, 32)])
 @pytest.mark.parametrize("k", [4, 32])
 def test_batch_launch_shapes(gc, warps, bps, claim, k):
     """The result does not depend on the launch shape or the claim size, with
@@ -213,37 +217,91 @@ def test_batch_launch_shapes(gc, warps, bps, claim, k):
     out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps, claim))
     assert (gc.as_u32(out)[:len(gaps)] == want).all()
     plan = gc.plan_index(idx)
-    assert int(plan.count.item()) == idx.max_tiles
+    assert int(plan.count[0].item()) == idx.max_tiles
+    assert int(plan.count[1].item()) == 0  # every tile has its skip entry
     for _ in range(2):
         out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps, claim), plan=plan)
         assert (gc.as_u32(out)[:len(gaps)] == want).all()
 
 
-def test_plan_records(gc):
-    """Each plan record carries its list's descriptor and its tile's record,
-    lists in order and tiles in order inside a list."""
-    oc, gcc = pair(gc, (O.SIMPLE, 4, 0, 0, 0.1))
-    lens, gaps, off = small_index(8, nlists=40)
+def test_launch_shape_out_of_range_rejected(gc):
+    """Claims of more than 32 tiles or blocks of more than 16 warps are
+    refused on the host, before any launch."""
+    _, gcc = pair(gc, (O.SIMPLE, 32, 0, 0, 0.1))
+    lens, gaps, off = small_index(4, nlists=20)
     idx = gc.encode_index(gcc, upload_u32(gaps), lens)
-    plan = gc.plan_index(idx)
-    w = plan.work.cpu().numpy().view(np.dtype([("ctrl_off", "<u8"), ("data_off", "<u8"), ("out_off", "<u8"),
-                                                ("n", "<u4"), ("tile", "<u4"), ("lane_bit", "<u8"),
-                                                ("ctrl_bit", "<u8"), ("exc_off", "<u4"), ("row_skip", "<u4"),
-                                                ("list", "<u4"), ("reserved", "<u4")]))
-    ntiles = [-(-(-(-int(n) // 4)) // 256) for n in lens]
-    seen = {}
-    for r in w[:int(plan.count.item())]:
-        seen.setdefault(int(r["list"]), []).append(r)
-    assert sorted(seen) == [i for i in range(len(lens)) if ntiles[i] > 0]
-    for i, recs in seen.items():
-        assert [int(r["tile"]) for r in recs] == list(range(ntiles[i]))
-        ctrl, _ = O.encode(oc, gaps[off[i]:off[i + 1]])
-        tref = O.tile_index(oc, ctrl, int(lens[i]))
-        for r in recs:
-            assert int(r["n"]) == int(lens[i]) and int(r["out_off"]) == int(off[i])
-            t = tref[int(r["tile"])]
-            assert (int(r["lane_bit"]), int(r["ctrl_bit"]), int(r["exc_off"]), int(r["row_skip"])) == \
-                (int(t["lane_bit"]), int(t["ctrl_bit"]), int(t["exc_off"]), int(t["row_skip"]))
+    for bad in (gc.gc_launch(4, 0, 33), gc.gc_launch(17, 0, 1)):
+        with pytest.raises(gc.GcError) as ei:
+            gc.decode_index(idx, launch=bad)
+        assert ei.value.code == 1
+
+
+def test_plan_records(gc):
+    """Each plan record carries its list's areas, its tile's first unit and
+    skip entry, and staging ranges inside the list; lists in order, a list's
+    tiles at consecutive records."""
+    for c in [(O.SIMPLE, 4, 0, 0, 0.1), (O.PFD, 32, 0, 0, 0.1), (O.AFOR, 32, 0, 0, 0.1)]:
+        oc, gcc = pair(gc, c)
+        k = c[1]
+        lens, gaps, off = small_index(8, nlists=40)
+        idx = gc.encode_index(gcc, upload_u32(gaps), lens)
+        lists = idx.lists.cpu().numpy().view(gc.LIST_DTYPE)
+        plan = gc.plan_index(idx)
+        w = plan.work.cpu().numpy().view(gc.WORK_DTYPE)
+        ntiles = [-(-(-(-int(n) // k)) // (1024 // k)) for n in lens]
+        seen = {}
+        recs = w[:int(plan.count[0].item())]
+        for j, r in enumerate(recs):
+            seen.setdefault(int(r["list"]), []).append(j)
+        assert sorted(seen) == [i for i in range(len(lens)) if ntiles[i] > 0]
+        for i, js in seen.items():
+            assert js == list(range(js[0], js[0] + ntiles[i])), "a list's tiles are consecutive records"
+            g = gaps[off[i]:off[i + 1]]
+            ctrl, data = O.encode(oc, g)
+            tref = O.tile_index(oc, ctrl, int(lens[i]), g)
+            d = lists[i]
+            for t, j in enumerate(js):
+                r = recs[j]
+                sh = int(r["shape"])
+                assert int(r["tile"]) == t
+                assert int(r["ctrl_at"]) == int(d["ctrl_off"]) and int(r["ctrl_bytes"]) == len(ctrl)
+                assert int(r["out_at"]) == int(off[i]) + 1024 * t
+                assert (sh & 1023) + 1 == min(1024, int(lens[i]) - 1024 * t)
+                assert int(r["ctrl_bit"]) == int(tref[t]["ctrl_bit"])
+                skip = int(tref[t]["row_skip"])
+                first = int(tref[t]["lane_bit"])  # lane bit of the tile's first row
+                if c[0] == O.AFOR and skip:
+                    first += skip * (int(ctrl[int(tref[t]["ctrl_bit"]) >> 3]) & 63)
+                assert (sh >> gc.WORK_BIT_SHIFT) & 31 == first & 31
+                assert (sh >> gc.WORK_SKIP_SHIFT) & 31 == skip
+                assert int(r["data_at"]) == int(d["data_off"]) + (first >> 5) * k
+                vecs = (sh >> gc.WORK_VEC_SHIFT) & 511
+                assert vecs <= 1024 // k + 1
+                assert int(r["data_at"]) + vecs * k <= int(d["data_off"]) + len(data)
+                assert sh & gc.WORK_HAS_BASE and int(r["base"]) == int(tref[t]["base"])
+                assert (int(r["ctrl_at"]) + int(r["win_at"])) % 16 == 0 and int(r["win_len"]) % 16 == 0
+                assert not sh & gc.WORK_PUBLISH
+
+
+def test_batch_without_skip_entries_uses_look_back(gc):
+    """An index whose tile records carry no bases (as gc_build_tiles would
+    give): every tile after a list's first takes its prefix by look-back,
+    claimed one at a time, and the docIDs are the same."""
+    for c in [(O.SIMPLE, 32, 0, 0, 0.1), (O.PFD, 4, 0, 0, 0.1), (O.SCHEME, 32, 8, 2, 0.1)]:
+        oc, gcc = pair(gc, c)
+        lens, gaps, off = small_index(21 + c[1], nlists=120)
+        idx = gc.encode_index(gcc, upload_u32(gaps), lens)
+        t = idx.tiles.view(torch.int32).view(-1, 8)
+        t[:, 6] = 0  # base
+        t[:, 7] = 0  # flags
+        plan = gc.plan_index(idx)
+        assert int(plan.count[1].item()) == len(idx.tiles) // gc.TILE_BYTES
+        want = np.concatenate([O.prefix_sum(gaps[off[i]:off[i + 1]]) for i in range(len(lens))])
+        for launch in (None, gc.gc_launch(2, 1, 4)):
+            out = gc.decode_index(idx, launch=launch, plan=plan)
+            assert (gc.as_u32(out)[:len(gaps)] == want).all()
+        out = gc.decode_index(idx)
+        assert (gc.as_u32(out)[:len(gaps)] == want).all()
 
 
 def test_batch_overflow_reports_nospace(gc):
@@ -273,5 +331,8 @@ def test_mixed_2_26_single_list(gc, c):
     assert (gc.as_u32(enc.data) == data).all()
     got = gc.as_u32(gc.decode(enc, restore_docids=False))
     assert (got == g).all()
+    want = O.prefix_sum(g)
     got = gc.as_u32(gc.decode(enc, restore_docids=True))
-    assert (got == O.prefix_sum(g)).all()
+    assert (got == want).all()
+    got = gc.as_u32(gc.decode(enc, restore_docids=True, use_tiles=False))  # 2^16 tiles by look-back
+    assert (got == want).all()

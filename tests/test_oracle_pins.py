@@ -501,6 +501,33 @@ def test_tile_index_consistent_with_units(codec):
     assert t == len(tiles)
 
 
+@pytest.mark.parametrize("k", [4, 32])
+def test_tile_skip_entries_are_prefix_sums(k):
+    """Sections 2.1.1 and 7.5: the skip entry of tile t is the docID just
+    before it, the running sum of the gaps modulo 2^32 at int 1024*t - 1
+    (numpy's cumulative sum in 64 bits, reduced), 0 for tile 0; the control
+    area alone gives no entry but tile 0's."""
+    codec = O.Codec(O.PFD, k)
+    n = 1024 * 9 + 17
+    g = synth.uniform_u32(3, n, 1 << 20, 1 << 30)  # sums pass 2^32: the wrap is exercised
+    ctrl, _ = O.encode(codec, g)
+    plain = O.tile_index(codec, ctrl, n)
+    skip = O.tile_index(codec, ctrl, n, g)
+    cum = np.cumsum(g.astype(np.uint64)) & 0xFFFFFFFF
+    want = [0] + [int(cum[1024 * t - 1]) for t in range(1, len(skip))]
+    assert [int(x) for x in skip["base"]] == want
+    assert (skip["flags"] == 1).all()
+    assert int(plain["flags"][0]) == 1 and not plain["flags"][1:].any() and not plain["base"].any()
+    for f in ("lane_bit", "ctrl_bit", "exc_off", "row_skip"):
+        assert (plain[f] == skip[f]).all()
+    # a tile decoded on its own, plus its entry, gives the list's docIDs there
+    ids = O.prefix_sum(g)
+    for t in range(len(skip)):
+        seg = g[1024 * t:1024 * (t + 1)]
+        local = np.cumsum(seg.astype(np.uint64)) + int(skip["base"][t])
+        assert (local.astype(np.uint64) & 0xFFFFFFFF == ids[1024 * t:1024 * t + len(seg)]).all()
+
+
 # ------------------------------------------------------------- generators
 
 def test_xoshiro_matches_published_definition():
