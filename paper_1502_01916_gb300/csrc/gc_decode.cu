@@ -32,13 +32,22 @@ namespace gcdev {
 
 constexpr unsigned long long kFlagAgg = 1ull << 32;
 constexpr unsigned long long kFlagPrefix = 2ull << 32;
-constexpr uint32_t kSpinLimit = 1u << 22;  // ~0.5 s of polling
+constexpr uint64_t kWaitNs = 1000000000ull;  // a wait gives up after 1 s
 
-constexpr int kRing = 8192;     // staging ring bytes per warp
-constexpr int kSeq = 32;        // claimed records kept per warp
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr int kRing = 6144;     // staging ring bytes per warp (one tile needs at most 5760)
+constexpr int kSeq = 16;        // claimed records kept per warp
 constexpr int kFly = 16;        // tiles staged at once per warp (one mbarrier each)
 constexpr int kCtrlCap = 512;   // control bytes staged per tile at most
 constexpr int kExcCap = 1024;   // exception bytes staged per tile (all or none)
+
+constexpr int kPadVec = 34;     // k = 32: data vectors of a pack, re-laid at 33 words each
+constexpr int kPad = 33;        // words per re-laid vector (one bank apart per vector)
 
 template <int K>
 struct Geo {
@@ -46,18 +55,27 @@ struct Geo {
   static constexpr int RPL = 32 / K;         // rows per 32-int line (K = 4: 8, K = 32: 1)
   static constexpr int PROWS = 32 * RPL;     // row entries of a pack
   static constexpr int MAXVEC = TR + 1;      // data vectors a tile spans at most
+  // k = 32: the pack's data re-laid at 33 words per vector; k = 4: a 32 x 32
+  // transpose buffer
+  static constexpr int TBW = K == 32 ? kPadVec * kPad : 32 * 32;
+
 };
 
 template <int K>
 struct __align__(128) WarpSmem {
   uint8_t ring[kRing];                   // staged tiles (data 128-byte aligned)
-  uint32_t tb[32 * 32];                  // line-major transpose buffer
+  uint32_t tb[Geo<K>::TBW];              // re-laid data / transpose buffer
   uint4 rec[kSeq][4];                    // claimed records
   unsigned long long mbar[kFly];
   uint32_t item[kSeq];                   // plan index of each claimed record
   uint32_t at[kFly];                     // ring offset of each staged tile
   uint32_t end[kFly];                    // ring position after its allocation
   uint16_t cst[kFly], xst[kFly];         // control / exception bytes staged
+  uint8_t flines[kFly];                  // 32-int lines of each staged tile (0: not decoded)
+  uint8_t fvecs[kFly];                   // data vectors staged for it
+  unsigned long long iout[32];           // pack item (by rank among decoded ones): first output int
+  uint32_t inint[32];                    // its ints
+  uint32_t ibase[32];                    // its docID base
   uint32_t rw[Geo<K>::PROWS];            // row: ring word of its first word (lane 0)
   uint32_t rs[Geo<K>::PROWS];            // row: shift | width << 8
   uint32_t xm[32];                       // line: Group-PFD exception slots
@@ -165,22 +183,43 @@ template <int K>
 struct RowSink {
   uint32_t* rw;
   uint32_t* rs;
-  uint32_t word0;     // ring word of the tile's first staged word
-  uint32_t bit0;      // lane bit of the tile's first unit in that word
+  uint32_t word0;     // buffer word of the tile's first staged word
+  uint32_t stride;    // buffer words per data vector (K staged, 33 re-laid)
+  uint32_t bit0;      // lane bit of the tile's first row in that word
   uint32_t vec_bits;  // 32 * staged vectors
 
   __device__ __forceinline__ void put(uint32_t q, uint32_t rb, uint32_t w, bool& ok) const {
     const uint32_t b = bit0 + rb;
-    if (b + w > vec_bits) {
-      ok = false;
-      rw[q] = word0;
-      rs[q] = 0;
-      return;
-    }
-    rw[q] = word0 + (b >> 5) * K;
-    rs[q] = (b & 31u) | (w << 8);
+    const bool bad = b + w > vec_bits;
+    ok = ok && !bad;
+    rw[q] = word0 + (bad ? 0u : (b >> 5) * stride);
+    rs[q] = bad ? 0u : ((b & 31u) | (w << 8));
   }
 };
+
+// Rows [lo, hi) of a tile that a batch of up to 32 units covers, one unit
+// per lane in order: the unit of lane u starts at row `start` (tile-relative,
+// may be negative), its rows are `w` bits wide, and its first row is at lane
+// bit `lb` (from the tile's first row). Lane q takes row r0 + q of each
+// chunk of 32 rows: the units that start before the chunk, plus those that
+// start in it at or before row r0 + q (a bit set over the chunk), give its
+// unit, whose start, width and first bit come by shuffle.
+template <int K>
+__device__ __forceinline__ void emit_rows(int32_t start, uint32_t w, uint32_t lb, int32_t lo, int32_t hi,
+                                          const RowSink<K>& out, bool& ok) {
+  const uint32_t lane = lane_id();
+  for (int32_t r0 = lo; r0 < hi; r0 += 32) {
+    const uint32_t before = __popc(__ballot_sync(kFull, start < r0));
+    const int32_t d = start - r0;
+    const uint32_t M = __reduce_or_sync(kFull, (d >= 0 && d < 32) ? 1u << d : 0u);
+    const int32_t r = r0 + (int32_t)lane;
+    const uint32_t u = before + __popc(M & (0xffffffffu >> (31u - lane))) - 1u;
+    const int32_t st = __shfl_sync(kFull, start, u & 31u);
+    const uint32_t wu = __shfl_sync(kFull, w, u & 31u);
+    const uint32_t lbu = __shfl_sync(kFull, lb, u & 31u);
+    if (r < hi) out.put((uint32_t)r, lbu + (uint32_t)(r - st) * wu, wu, ok);
+  }
+}
 
 // ---------------------------------------------------------------- parsers
 // Each fills rows 0..rows-1 of the tile (tile-relative) and returns false
@@ -189,7 +228,7 @@ struct RowSink {
 // Table III selectors, 4 bits each, low nibble first; selector u holds NUM
 // rows of BW bits in one 32-bit word of every lane (Sec 4.1.1, 4.3).
 template <int K>
-__device__ bool parse_simple(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip, uint32_t rows,
+__device__ __forceinline__ bool parse_simple(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip, uint32_t rows,
                              const RowSink<K>& out) {
   const uint32_t lane = lane_id();
   const uint64_t u0 = ctrl_bit >> 2;
@@ -203,13 +242,11 @@ __device__ bool parse_simple(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip
     const uint32_t bw = bad ? 0u : sel_bw(sel);
     const uint32_t incl = warp_incl_sum(num);
     const int32_t start = cov + (int32_t)(incl - num);
-    if (start < (int32_t)rows) {
-      if (bad) ok = false;
-      const int32_t a = start > 0 ? start : 0;
-      const int32_t b = (start + (int32_t)num) < (int32_t)rows ? start + (int32_t)num : (int32_t)rows;
-      for (int32_t q = a; q < b; ++q) out.put((uint32_t)q, 32u * (c + lane) + (uint32_t)(q - start) * bw, bw, ok);
-    }
-    cov += (int32_t)__shfl_sync(kFull, incl, 31);
+    if (bad && start < (int32_t)rows) ok = false;
+    const int32_t end = cov + (int32_t)__shfl_sync(kFull, incl, 31);
+    emit_rows<K>(start, bw, 32u * (c + lane), cov > 0 ? cov : 0, end < (int32_t)rows ? end : (int32_t)rows, out,
+                 ok);
+    cov = end;
   }
   return __all_sync(kFull, ok);
 }
@@ -217,7 +254,7 @@ __device__ bool parse_simple(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip
 // Binary length descriptors at fixed positions (Sec 5.2.1(b)); the width of
 // row r is CG * (descriptor + 1) (Eq. 2).
 template <int K>
-__device__ bool parse_scheme_binary(const CtrlView& C, uint64_t row0, uint32_t rows, uint32_t cg,
+__device__ __forceinline__ bool parse_scheme_binary(const CtrlView& C, uint64_t row0, uint32_t rows, uint32_t cg,
                                     const RowSink<K>& out) {
   const uint32_t lane = lane_id();
   const uint32_t width = 5 - log2_cg(cg);
@@ -249,7 +286,7 @@ __device__ bool parse_scheme_binary(const CtrlView& C, uint64_t row0, uint32_t r
 // first bit; trailing ones of a byte are padding. While the windows lie in
 // the staged control bytes only those are read; past them, 32 at a time.
 template <int K>
-__device__ bool parse_scheme_unary(const CtrlView& C, uint64_t P0, uint32_t rows, uint32_t cg, bool iu,
+__device__ __forceinline__ bool parse_scheme_unary(const CtrlView& C, uint64_t P0, uint32_t rows, uint32_t cg, bool iu,
                                    const RowSink<K>& out) {
   const uint32_t lane = lane_id();
   const uint64_t A = P0 & ~7ull;
@@ -336,7 +373,7 @@ __device__ bool parse_scheme_unary(const CtrlView& C, uint64_t P0, uint32_t rows
 // staged data starts at the tile's first row, so offsets are taken from
 // there (the frame's first `skip` rows, skip * b bits, are not staged).
 template <int K>
-__device__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip, uint32_t rows,
+__device__ __forceinline__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip, uint32_t rows,
                            const RowSink<K>& out) {
   const uint32_t lane = lane_id();
   const uint64_t f0 = ctrl_bit >> 3;
@@ -349,19 +386,16 @@ __device__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip, 
     const uint32_t code = byte >> 6, b = byte & 63u;
     const bool bad = code > 2 || b > 32;
     const uint32_t F = bad ? 32u : (8u << code);
-    const uint32_t lbits = bad ? 0u : F * b;
+    const uint32_t bb = bad ? 0u : b;
+    const uint32_t lbits = F * bb;
     const uint32_t inclF = warp_incl_sum(F);
     const uint32_t inclL = warp_incl_sum(lbits);
     const int32_t start = cov + (int32_t)(inclF - F);
-    const uint32_t lstart = lcarry + inclL - lbits;
-    if (start < (int32_t)rows) {
-      if (bad) ok = false;
-      const int32_t a = start > 0 ? start : 0;
-      const int32_t e = (start + (int32_t)F) < (int32_t)rows ? start + (int32_t)F : (int32_t)rows;
-      for (int32_t q = a; q < e; ++q)
-        out.put((uint32_t)q, lstart + (uint32_t)(q - start) * (bad ? 0u : b), bad ? 0u : b, ok);
-    }
-    cov += (int32_t)__shfl_sync(kFull, inclF, 31);
+    if (bad && start < (int32_t)rows) ok = false;
+    const int32_t end = cov + (int32_t)__shfl_sync(kFull, inclF, 31);
+    emit_rows<K>(start, bb, lcarry + inclL - lbits, cov > 0 ? cov : 0, end < (int32_t)rows ? end : (int32_t)rows,
+                 out, ok);
+    cov = end;
     lcarry += __shfl_sync(kFull, inclL, 31);
   }
   return __all_sync(kFull, ok);
@@ -373,7 +407,7 @@ __device__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit, uint32_t skip, 
 // at exc_at. Rows go to the sink; every exception sets its slot's bit in the
 // mask of its line, and each line gets the address of its frame's values.
 template <int K>
-__device__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows, const RowSink<K>& out,
+__device__ __forceinline__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows, const RowSink<K>& out,
                           WarpSmem<K>& ws, uint32_t line0, uint32_t nlines) {
   constexpr uint32_t pb = (kPfdFrameRows * K) <= 256 ? 1u : 2u;
   constexpr uint32_t LPF = K;  // lines per frame (32 rows of K ints)
@@ -457,14 +491,16 @@ __device__ uint32_t look_back(const unsigned long long* lb, uint64_t item, uint6
     bool timed_out = false;
     if (dist <= t && dist <= item) {
       s = ld_acquire(lb + item - dist);
-      uint32_t spins = 0;
-      while ((s >> 32) == 0) {
-        if (++spins > kSpinLimit) {
-          timed_out = true;
-          break;
+      if ((s >> 32) == 0) {
+        const uint64_t t0 = now_ns();
+        while ((s >> 32) == 0) {
+          if (now_ns() - t0 > kWaitNs) {
+            timed_out = true;
+            break;
+          }
+          __nanosleep(32);
+          s = ld_acquire(lb + item - dist);
         }
-        __nanosleep(32);
-        s = ld_acquire(lb + item - dist);
       }
     }
     if (__any_sync(kFull, timed_out)) {
@@ -563,6 +599,7 @@ __device__ void decode_pack(const DecodeArgs& a, WarpSmem<K>& ws, uint32_t s0, u
     out.rw = ws.rw + line0 * RPL;
     out.rs = ws.rs + line0 * RPL;
     out.word0 = at / 4;
+    out.stride = K;
     out.bit0 = w_bit0(w.shape);
     out.vec_bits = 32 * vecs;
     const uint32_t rows = (nint + K - 1) / K;
@@ -760,15 +797,248 @@ __device__ void decode_pack(const DecodeArgs& a, WarpSmem<K>& ws, uint32_t s0, u
   __syncwarp();
 }
 
+// One Group-PFD exception value of `wb` bytes (little-endian), wherever its
+// frame's values are (staged window or global memory). Out of line: it runs
+// once per exception, and keeping it out of the unrolled loop keeps that
+// loop small.
+__device__ __noinline__ uint32_t exc_value(const uint8_t* p, uint32_t wb) {
+  uint32_t x = p[0];
+  if (wb > 1) x |= (uint32_t)p[1] << 8;
+  if (wb > 2) x |= ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+  return x;
+}
+
+// The k = 32 pack decoder. Each staged tile's data vectors are first re-laid
+// at 33 words per vector, so that the rows of a pack, one per lane, sit in
+// different banks whichever vectors they start in; lane l then reads line l
+// (one row of 32 ints) in natural column order with fixed offsets, and its
+// running sum is directly the prefix within the line.
+template <int KIND, bool RESTORE>
+__device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0, uint32_t np, uint32_t nl) {
+  const uint32_t lane = lane_id();
+
+  // items: lane p < np holds item p
+  const uint32_t fp = (s0 + lane) % kFly;
+  const uint32_t my_lines = lane < np ? ws.flines[fp] : 0u;
+  const uint32_t my_vecs = lane < np ? ws.fvecs[fp] : 0u;
+  const uint32_t my_line0 = warp_incl_sum(my_lines) - my_lines;
+  const uint32_t my_vec0 = warp_incl_sum(my_vecs) - my_vecs;
+  const bool my_live = my_lines > 0;
+  const uint32_t live = __ballot_sync(kFull, my_live);
+  const uint32_t heads = __reduce_or_sync(kFull, my_live ? 1u << my_line0 : 0u);
+  uint32_t my_item = 0, my_tile = 0, my_base = 0, my_shape = 0, my_list = 0xffffffffu;
+  uint64_t my_out = 0;
+  if (lane < np) {
+    const gc_work& w = rec_at(ws.rec, s0 + lane);
+    my_item = ws.item[(s0 + lane) % kSeq];
+    my_tile = w.tile;
+    my_base = w.base;
+    my_shape = w.shape;
+    my_list = w.list;
+    my_out = w.out_at;
+  }
+  const bool my_dead = lane < np && !my_live && my_list != 0xffffffffu;
+  const uint32_t my_rank = __popc(live & ((1u << lane) - 1u));
+  if (my_live) {
+    ws.iout[my_rank] = my_out;
+    ws.inint[my_rank] = w_nint(my_shape);
+  }
+  if (KIND == GC_PFD) ws.xm[lane] = 0;
+
+  // 1. per tile: re-lay its data vectors at 33 words per vector, and turn
+  // its control patterns into one (word, shift, width) entry per row
+  for (uint32_t lm = live; lm; lm &= lm - 1) {
+    const uint32_t p = __ffs(lm) - 1;
+    const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
+    const uint32_t rows = __shfl_sync(kFull, my_lines, p);
+    const uint32_t v0 = __shfl_sync(kFull, my_vec0, p);
+    const gc_work& w = rec_at(ws.rec, s0 + p);
+    const uint32_t f = (s0 + p) % kFly;
+    const uint32_t at = ws.at[f];
+    const uint32_t vecs = ws.fvecs[f];
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(ws.ring + at) + lane;
+      uint32_t* dst = ws.tb + v0 * kPad + lane;
+#pragma unroll 4
+      for (uint32_t v = 0; v < vecs; ++v) dst[v * kPad] = src[v * 32];
+    }
+    const uint32_t dbytes = vecs * 32 * 4;
+    CtrlView C;
+    C.g = a.ctrl_pool + w.ctrl_at;
+    C.size = w.ctrl_bytes;
+    C.s1 = ws.ring + at + dbytes;
+    C.lo1 = w.win_at;
+    C.len1 = ws.cst[f];
+    C.s2 = ws.ring + at + dbytes + ws.cst[f];
+    C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
+    C.len2 = ws.xst[f];
+    RowSink<32> out;
+    out.rw = ws.rw + line0;
+    out.rs = ws.rs + line0;
+    out.word0 = v0 * kPad;
+    out.stride = kPad;
+    out.bit0 = w_bit0(w.shape);
+    out.vec_bits = 32 * vecs;
+    bool ok;
+    if (KIND == GC_SIMPLE) {
+      ok = parse_simple<32>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
+    } else if (KIND == GC_SCHEME) {
+      const uint64_t row0 = (uint64_t)w.tile * Geo<32>::TR;
+      if (a.ld == GC_LD_BINARY) ok = parse_scheme_binary<32>(C, row0, rows, a.cg, out);
+      else ok = parse_scheme_unary<32>(C, w.ctrl_bit, rows, a.cg, a.ld == GC_LD_IU, out);
+    } else if (KIND == GC_AFOR) {
+      ok = parse_afor<32>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
+    } else {
+      ok = parse_pfd<32>(C, w.tile, w.exc_at, rows, out, ws, line0, rows);
+    }
+    if (!ok && lane == 0) report(a.status, GC_ERR_CORRUPT, w.list);
+  }
+  __syncwarp();
+
+  // 2. lane l extracts line l (row l of the pack): ints in column order
+  const bool act = lane < nl;
+  const uint32_t upto = heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
+  const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;  // its item among the decoded ones
+  const uint32_t lhead = act ? 31u - __clz(upto) : 0u;          // the item's first line
+  const uint32_t ent = act ? ws.rw[lane] : 0u;
+  const uint32_t sw = act ? ws.rs[lane] : 0u;
+  const uint32_t sh = sw & 31u, wd = sw >> 8;
+  const uint32_t msk = low_mask(wd);
+  const bool cross = sh + wd > 32;
+  const uint32_t* P = ws.tb + ent;
+  uint32_t xm = 0;
+  const uint8_t* xp = nullptr;
+  uint32_t xwb = 1;
+  if (KIND == GC_PFD) {
+    // the tile is one frame: exceptions before this line in it
+    xm = act ? ws.xm[lane] : 0u;
+    const uint32_t cnt = __popc(xm);
+    uint32_t v = cnt;
+    bool f = !act || lane == lhead;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, v, o);
+      const bool g = __shfl_up_sync(kFull, f, o);
+      if (lane >= (uint32_t)o && !f) {
+        v += y;
+        f = g;
+      }
+    }
+    if (xm) {
+      xwb = ws.xw[lane];
+      xp = reinterpret_cast<const uint8_t*>(ws.xv[lane]) + (size_t)(v - cnt) * xwb;
+    }
+  }
+  uint32_t r[32];
+  uint32_t R = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t lo = P[j];
+    uint32_t hi = 0;
+    if (KIND != GC_SIMPLE && cross) hi = P[kPad + j];  // Group-Simple values never cross a word
+    uint32_t v = __funnelshift_r(lo, hi, sh) & msk;
+    if (KIND == GC_PFD && ((xm >> j) & 1u)) {
+      v = exc_value(xp, xwb);
+      xp += xwb;
+    }
+    if (RESTORE) {
+      R += v;
+      r[j] = R;
+    } else {
+      r[j] = v;
+    }
+  }
+
+  // 3. docIDs: segmented scan of line totals, then each item's base
+  uint32_t k0 = 0;
+  if (RESTORE) {
+    const uint32_t T = R;
+    uint32_t v = act ? T : 0u;
+    bool f = !act || lane == lhead;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, v, o);
+      const bool g = __shfl_up_sync(kFull, f, o);
+      if (lane >= (uint32_t)o && !f) {
+        v += y;
+        f = g;
+      }
+    }
+    const uint32_t E = v - (act ? T : 0u);
+    const uint32_t lastl = my_live ? my_line0 + my_lines - 1 : 0u;
+    const uint32_t tot = __shfl_sync(kFull, v, lastl);
+    const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
+    const bool needs_lb = my_live && my_tile > 0 && !has_base;
+    uint32_t base = has_base ? my_base : 0u;
+    if (a.lb) {
+      if (my_live && !needs_lb && (my_shape & GC_WORK_PUBLISH))
+        st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(base + tot));
+      if (my_dead) st_release(a.lb + my_item, kFlagPrefix);  // its error is reported
+      if (needs_lb) st_release(a.lb + my_item, kFlagAgg | tot);
+    }
+    for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
+      const uint32_t p = __ffs(pend) - 1;
+      const uint32_t it = __shfl_sync(kFull, my_item, p);
+      const uint32_t tl = __shfl_sync(kFull, my_tile, p);
+      const uint32_t lst = __shfl_sync(kFull, my_list, p);
+      const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
+      if (lane == p) {
+        base = ex;
+        if (a.lb) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(ex + tot));
+      }
+    }
+    if (my_live) ws.ibase[my_rank] = base;
+    __syncwarp();
+    k0 = E + (act ? ws.ibase[rank] : 0u);
+  }
+
+  // the re-laid data is read: its buffer takes the results, line l at word
+  // 33 l (no two lanes share a bank)
+  __syncwarp();
+  if (act) {
+    uint32_t* T = ws.tb + lane * kPad;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) T[j] = r[j] + k0;
+    ws.lout[lane] = ws.iout[rank] + 32ull * (lane - lhead);
+    const uint32_t left = ws.inint[rank] - 32u * (lane - lhead);
+    ws.lnv[lane] = left < 32u ? left : 32u;
+  }
+  __syncwarp();
+
+  // 4. 128-byte stores, line by line
+  if (heads == 1u) {
+    // one tile: its lines are consecutive in the output
+    uint32_t* o = a.out_pool + ws.iout[0] + lane;
+    const uint32_t n = ws.inint[0];
+    if (n == (uint32_t)kTileInts) {
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) o[rr * 32] = ws.tb[rr * kPad + lane];
+    } else {
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr)
+        if ((uint32_t)rr * 32u + lane < n) o[rr * 32] = ws.tb[rr * kPad + lane];
+    }
+  } else {
+    for (uint32_t ln = 0; ln < nl; ++ln) {
+      const uint64_t ob = ws.lout[ln];
+      const uint32_t n = ws.lnv[ln];
+      const uint32_t v = ws.tb[ln * kPad + lane];
+      if (lane < n) a.out_pool[ob + lane] = v;
+    }
+  }
+  __syncwarp();
+}
+
 template <int KIND, int K, bool RESTORE>
-__global__ void __launch_bounds__(512) k_decode(DecodeArgs a) {
+__global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   WarpSmem<K>& ws = reinterpret_cast<WarpSmem<K>*>(smem_raw)[threadIdx.x >> 5];
   const uint32_t lane = lane_id();
   uint64_t total = a.count[0];
   if (total > a.work_cap) total = a.work_cap;
   const bool lookback = RESTORE && a.count[1] != 0;
-  const uint32_t C = lookback ? 1u : a.claim;
+  // a claim must fit the record slots, or the warp could never claim again
+  const uint32_t C = lookback ? 1u : (a.claim < 1u ? 1u : a.claim > (uint32_t)kSeq ? (uint32_t)kSeq : a.claim);
   if (lane < kFly) mbar_init(&ws.mbar[lane], 1);
   // row entries start in range (a parser stopped by a corrupt stream leaves
   // earlier, in-range entries behind, never garbage)
@@ -811,7 +1081,10 @@ __global__ void __launch_bounds__(512) k_decode(DecodeArgs a) {
       const gc_work& w = rec_at(ws.rec, s_issued);
       const uint32_t f = s_issued % kFly;
       uint32_t dbytes = 0, cb = 0, xb = 0;
-      if (w_live<K>(w, a)) {
+      const bool live = w_live<K>(w, a);
+      if (!live && w.list != 0xffffffffu && lane == 0)
+        report(a.status, w.out_at + w_nint(w.shape) > a.out_pool_len ? GC_ERR_INVALID : GC_ERR_CORRUPT, w.list);
+      if (live) {
         dbytes = w_vecs(w.shape) * K * 4;
         const int64_t ws0 = (int64_t)w.ctrl_at + w.win_at;
         cb = w.win_len < kCtrlCap ? w.win_len : (uint32_t)kCtrlCap;
@@ -835,6 +1108,8 @@ __global__ void __launch_bounds__(512) k_decode(DecodeArgs a) {
         ws.end[f] = head;
         ws.cst[f] = (uint16_t)cb;
         ws.xst[f] = (uint16_t)xb;
+        ws.flines[f] = (uint8_t)(live ? (w_nint(w.shape) + 31) / 32 : 0u);
+        ws.fvecs[f] = (uint8_t)(dbytes / (K * 4));
         fence_proxy_async();
         mbar_expect_tx(&ws.mbar[f], dbytes + cb + xb);
         if (dbytes) bulk_g2s(ws.ring + off, a.data_pool + w.data_at, dbytes, &ws.mbar[f]);
@@ -850,22 +1125,26 @@ __global__ void __launch_bounds__(512) k_decode(DecodeArgs a) {
       continue;
     }
     // a pack: records from s_done on while their lines fit 32
-    uint32_t np = 0, nl = 0;
+    uint32_t np = 0, nl = 0, nv = 0;
     while (s_done + np < s_issued && np < 32) {
-      const gc_work& w = rec_at(ws.rec, s_done + np);
-      const uint32_t lines = w_live<K>(w, a) ? (w_nint(w.shape) + 31) / 32 : 0u;
-      if (nl + lines > 32) break;
+      const uint32_t f = (s_done + np) % kFly;
+      const uint32_t lines = ws.flines[f];
+      const uint32_t vecs = ws.fvecs[f];
+      if (nl + lines > 32 || (K == 32 && nv + vecs > (uint32_t)kPadVec)) break;
       nl += lines;
+      nv += vecs;
       ++np;
     }
     // wait for their copies
     for (uint32_t p = 0; p < np && !failed; ++p) {
       const uint32_t s = s_done + p;
-      uint32_t spins = 0;
-      while (!mbar_try_wait(&ws.mbar[s % kFly], (s / kFly) & 1u)) {
-        if (++spins > kSpinLimit) {
-          failed = true;
-          break;
+      if (!mbar_try_wait(&ws.mbar[s % kFly], (s / kFly) & 1u)) {
+        const uint64_t t0 = now_ns();
+        while (!mbar_try_wait(&ws.mbar[s % kFly], (s / kFly) & 1u)) {
+          if (now_ns() - t0 > kWaitNs) {
+            failed = true;
+            break;
+          }
         }
       }
     }
@@ -874,12 +1153,8 @@ __global__ void __launch_bounds__(512) k_decode(DecodeArgs a) {
       if (lane == 0) report(a.status, GC_ERR_TIMEOUT, 0xfffffffeu);
       break;
     }
-    for (uint32_t p = 0; p < np; ++p) {
-      const gc_work& w = rec_at(ws.rec, s_done + p);
-      if (w.list != 0xffffffffu && !w_live<K>(w, a) && lane == 0)
-        report(a.status, w.out_at + w_nint(w.shape) > a.out_pool_len ? GC_ERR_INVALID : GC_ERR_CORRUPT, w.list);
-    }
-    decode_pack<KIND, K, RESTORE>(a, ws, s_done, np, nl);
+    if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, ws, s_done, np, nl);
+    else decode_pack<KIND, K, RESTORE>(a, ws, s_done, np, nl);
     s_done += np;
     tail = ws.end[(s_done - 1) % kFly];
   }
@@ -1084,7 +1359,7 @@ namespace {
 
 constexpr uint32_t kMaxWarps = 16;     // warps per block (launch bounds: 512 threads)
 constexpr uint32_t kDefaultWarps = 4;
-constexpr uint32_t kMaxClaim = 32;     // records per claim
+constexpr uint32_t kMaxClaim = kSeq;   // records per claim
 constexpr uint32_t kDefaultClaim = 8;
 constexpr uint64_t kHdr = 256;         // scratch header: claim counter, record counts
 

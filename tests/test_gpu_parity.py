@@ -205,7 +205,7 @@ def test_batch_encode_decode(gc, c):
     assert (gc.as_u32(out)[:len(gaps)] == gaps).all()
 
 
-@pytest.mark.parametrize("warps,bps,claim", [(1, 1, 1), (4, 2, 2), (8, 0, 0), (16, 0, 7), (2, 1, 32)])
+@pytest.mark.parametrize("warps,bps,claim", [(1, 1, 1), (4, 2, 2), (8, 0, 0), (16, 0, 7), (2, 1, 16)])
 @pytest.mark.parametrize("k", [4, 32])
 def test_batch_launch_shapes(gc, warps, bps, claim, k):
     """The result does not depend on the launch shape or the claim size, with
@@ -225,12 +225,12 @@ def test_batch_launch_shapes(gc, warps, bps, claim, k):
 
 
 def test_launch_shape_out_of_range_rejected(gc):
-    """Claims of more than 32 tiles or blocks of more than 16 warps are
+    """Claims of more than 16 tiles or blocks of more than 16 warps are
     refused on the host, before any launch."""
     _, gcc = pair(gc, (O.SIMPLE, 32, 0, 0, 0.1))
     lens, gaps, off = small_index(4, nlists=20)
     idx = gc.encode_index(gcc, upload_u32(gaps), lens)
-    for bad in (gc.gc_launch(4, 0, 33), gc.gc_launch(17, 0, 1)):
+    for bad in (gc.gc_launch(4, 0, 17), gc.gc_launch(17, 0, 1)):
         with pytest.raises(gc.GcError) as ei:
             gc.decode_index(idx, launch=bad)
         assert ei.value.code == 1
