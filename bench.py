@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--nlists", type=int, default=1_000_000)
+    p.add_argument("--zipf-c", type=float, default=0.0,
+                   help="C of the rank law L_r = C r^-1.1 (0 = the 1.5e9-posting index); a smaller C makes "
+                        "the small case that ncu captures")
     p.add_argument("--codecs", default="simple,pfd")
     p.add_argument("--k", type=int, default=32)
     p.add_argument("--zeta", type=float, default=0.10)
@@ -65,14 +68,15 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def workload(nlists: int):
+def workload(nlists: int, zipf_c: float = 0.0):
     import synth
-    gaps, off, lengths = synth.zipf_index(nlists, UNIVERSE, 0)
+    gaps, off, lengths = synth.zipf_index(nlists, UNIVERSE, 0, C=zipf_c or synth.ZIPF_C)
     return gaps, off, lengths
 
 
 def workload_name(a) -> str:
-    return (f"zipf-index: {a.nlists} lists, universe {UNIVERSE}, Zipf(1.1) lengths in [1, 2^22], "
+    c = f", C={a.zipf_c:g}" if a.zipf_c else ""
+    return (f"zipf-index: {a.nlists} lists, universe {UNIVERSE}, Zipf(1.1) lengths in [1, 2^22]{c}, "
             f"uniform docIDs; k={a.k}; batched persistent decode + docID prefix sum")
 
 
@@ -211,7 +215,7 @@ def main():
             dist.barrier()
 
     t0 = time.time()
-    gaps, off, lengths = workload(a.nlists)
+    gaps, off, lengths = workload(a.nlists, a.zipf_c)
     t_gen = time.time() - t0
     total_ints = int(off[-1])
     d_gaps = torch.from_numpy(gaps.view(np.int32)).to(dev)
