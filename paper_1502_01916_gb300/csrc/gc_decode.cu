@@ -76,6 +76,7 @@ struct __align__(128) WarpSmem {
   unsigned long long iout[32];           // pack item (by rank among decoded ones): first output int
   uint32_t inint[32];                    // its ints
   uint32_t ibase[32];                    // its docID base
+  uint32_t ixb[32];                      // Group-PFD: its first exception value in the buffer's free tail
   uint32_t rw[Geo<K>::PROWS];            // row: ring word of its first word (lane 0)
   uint32_t rs[Geo<K>::PROWS];            // row: shift | width << 8
   uint32_t xm[32];                       // line: Group-PFD exception slots
@@ -408,7 +409,8 @@ __device__ __forceinline__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit,
 // mask of its line, and each line gets the address of its frame's values.
 template <int K>
 __device__ __forceinline__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows, const RowSink<K>& out,
-                          WarpSmem<K>& ws, uint32_t line0, uint32_t nlines) {
+                          WarpSmem<K>& ws, uint32_t line0, uint32_t nlines, uint32_t* xdst = nullptr,
+                          uint32_t xroom = 0, uint32_t* xtotal = nullptr) {
   constexpr uint32_t pb = (kPfdFrameRows * K) <= 256 ? 1u : 2u;
   constexpr uint32_t LPF = K;  // lines per frame (32 rows of K ints)
   const uint32_t lane = lane_id();
@@ -435,14 +437,18 @@ __device__ __forceinline__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64
     }
     xb = e * (pb + (1u << wcode));
   }
-  const uint32_t inclL = warp_incl_sum(32u * b);
-  const uint32_t inclX = warp_incl_sum(xb);
-  const uint32_t lstart = inclL - 32u * b;
-  const uint64_t xrec = exc_at + (inclX - xb);
-  if (lane < nfr && e && xrec + xb > C.size) {
+  const uint64_t xrec0 = exc_at + (warp_incl_sum(xb) - xb);
+  if (lane < nfr && e && xrec0 + xb > C.size) {
     ok = false;
     e = 0;
+    xb = 0;
   }
+  const uint32_t inclL = warp_incl_sum(32u * b);
+  const uint32_t lstart = inclL - 32u * b;
+  const uint32_t inclE = warp_incl_sum(e);
+  const uint32_t etot = __shfl_sync(kFull, inclE, 31);
+  const bool expand = xdst != nullptr && etot <= xroom;
+  if (xtotal) *xtotal = expand ? etot : 0xffffffffu;
   for (uint32_t fl = 0; fl < nfr; ++fl) {
     const uint32_t bf = __shfl_sync(kFull, b, fl);
     const uint32_t ls = __shfl_sync(kFull, lstart, fl);
@@ -452,20 +458,31 @@ __device__ __forceinline__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64
   for (uint32_t fl = 0; fl < nfr; ++fl) {
     const uint32_t ef = __shfl_sync(kFull, e, fl);
     const uint32_t lim = __shfl_sync(kFull, frows, fl) * K;
-    const uint64_t rec = __shfl_sync(kFull, xrec, fl);
+    const uint64_t rec = __shfl_sync(kFull, xrec0, fl);
     const uint32_t wb = 1u << __shfl_sync(kFull, wcode, fl);
+    const uint32_t xs = __shfl_sync(kFull, inclE - e, fl);  // exceptions of the tile before this frame
+    // the frame's record: ef positions, then ef values (all inside the list)
+    const uint8_t* rp = C.addr(rec, (uint64_t)ef * (pb + wb));
+    const uint8_t* vp = rp + (size_t)ef * pb;
     for (uint32_t x = lane; x < ef; x += 32) {
-      const uint32_t pos = C.le(rec + (uint64_t)x * pb, pb);
+      const uint32_t pos = pb == 1 ? (uint32_t)rp[x] : ((uint32_t)rp[2 * x] | ((uint32_t)rp[2 * x + 1] << 8));
       if (pos >= lim) {
         ok = false;
         continue;
       }
       const uint32_t i = fl * kPfdFrameRows * K + pos;  // tile-relative int
       atomicOr(&ws.xm[line0 + (i >> 5)], 1u << (i & 31u));
+      if (expand) {
+        const uint8_t* q = vp + (size_t)x * wb;
+        uint32_t v = q[0];
+        if (wb > 1) v |= (uint32_t)q[1] << 8;
+        if (wb > 2) v |= ((uint32_t)q[2] << 16) | ((uint32_t)q[3] << 24);
+        xdst[xs + x] = v;
+      }
     }
     const uint32_t ql = fl * LPF + lane;
     if (lane < LPF && ql < nlines) {
-      ws.xv[line0 + ql] = (unsigned long long)C.addr(rec + (uint64_t)ef * pb, (uint64_t)ef * wb);
+      ws.xv[line0 + ql] = (unsigned long long)vp;
       ws.xw[line0 + ql] = wb;
     }
   }
@@ -808,6 +825,38 @@ __device__ __noinline__ uint32_t exc_value(const uint8_t* p, uint32_t wb) {
   return x;
 }
 
+// One line (32 ints) of the k = 32 decoder in natural column order: word
+// (P[j], P[33 + j]) >> shift & mask, Group-PFD exceptions over their slots
+// (XMODE 0: none in the pack; 1: values staged as 32-bit words at X, in
+// column order; 2: values of xwb bytes at xp), and the running sum.
+template <int KIND, bool RESTORE, int XMODE>
+__device__ __forceinline__ void extract_line(const uint32_t* P, uint32_t sh, uint32_t msk, bool cross, uint32_t xm,
+                                             const uint32_t* X, const uint8_t* xp, uint32_t xwb, uint32_t (&r)[32],
+                                             uint32_t& R) {
+  R = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t lo = P[j];
+    uint32_t hi = 0;
+    if (KIND != GC_SIMPLE && cross) hi = P[kPad + j];  // Group-Simple values never cross a word
+    uint32_t v = __funnelshift_r(lo, hi, sh) & msk;
+    if (XMODE == 1) {
+      if ((xm >> j) & 1u) v = *X++;
+    } else if (XMODE == 2) {
+      if ((xm >> j) & 1u) {
+        v = exc_value(xp, xwb);
+        xp += xwb;
+      }
+    }
+    if (RESTORE) {
+      R += v;
+      r[j] = R;
+    } else {
+      r[j] = v;
+    }
+  }
+}
+
 // The k = 32 pack decoder. Each staged tile's data vectors are first re-laid
 // at 33 words per vector, so that the rows of a pack, one per lane, sit in
 // different banks whichever vectors they start in; lane l then reads line l
@@ -844,6 +893,12 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     ws.inint[my_rank] = w_nint(my_shape);
   }
   if (KIND == GC_PFD) ws.xm[lane] = 0;
+
+  // Group-PFD: the exception values of the pack go, as 32-bit words, to the
+  // part of the buffer past the re-laid vectors (when they all fit)
+  const uint32_t xfree0 = __shfl_sync(kFull, my_vec0 + my_vecs, 31) * kPad;
+  uint32_t xused = 0;
+  bool xfast = true;
 
   // 1. per tile: re-lay its data vectors at 33 words per vector, and turn
   // its control patterns into one (word, shift, width) entry per row
@@ -889,7 +944,12 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     } else if (KIND == GC_AFOR) {
       ok = parse_afor<32>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
     } else {
-      ok = parse_pfd<32>(C, w.tile, w.exc_at, rows, out, ws, line0, rows);
+      const uint32_t room = xfast && xfree0 + xused < (uint32_t)Geo<32>::TBW ? Geo<32>::TBW - xfree0 - xused : 0u;
+      uint32_t ex = 0;
+      ok = parse_pfd<32>(C, w.tile, w.exc_at, rows, out, ws, line0, rows, ws.tb + xfree0 + xused, room, &ex);
+      if (lane == 0) ws.ixb[__popc(live & ((1u << p) - 1u))] = xfree0 + xused;
+      if (ex == 0xffffffffu) xfast = false;
+      else xused += ex;
     }
     if (!ok && lane == 0) report(a.status, GC_ERR_CORRUPT, w.list);
   }
@@ -906,9 +966,7 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   const uint32_t msk = low_mask(wd);
   const bool cross = sh + wd > 32;
   const uint32_t* P = ws.tb + ent;
-  uint32_t xm = 0;
-  const uint8_t* xp = nullptr;
-  uint32_t xwb = 1;
+  uint32_t xm = 0, xfirst = 0;
   if (KIND == GC_PFD) {
     // the tile is one frame: exceptions before this line in it
     xm = act ? ws.xm[lane] : 0u;
@@ -924,29 +982,19 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
         f = g;
       }
     }
-    if (xm) {
-      xwb = ws.xw[lane];
-      xp = reinterpret_cast<const uint8_t*>(ws.xv[lane]) + (size_t)(v - cnt) * xwb;
-    }
+    xfirst = v - cnt;
   }
   uint32_t r[32];
   uint32_t R = 0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const uint32_t lo = P[j];
-    uint32_t hi = 0;
-    if (KIND != GC_SIMPLE && cross) hi = P[kPad + j];  // Group-Simple values never cross a word
-    uint32_t v = __funnelshift_r(lo, hi, sh) & msk;
-    if (KIND == GC_PFD && ((xm >> j) & 1u)) {
-      v = exc_value(xp, xwb);
-      xp += xwb;
-    }
-    if (RESTORE) {
-      R += v;
-      r[j] = R;
-    } else {
-      r[j] = v;
-    }
+  if (KIND != GC_PFD || !__any_sync(kFull, xm != 0)) {
+    extract_line<KIND, RESTORE, 0>(P, sh, msk, cross, 0u, nullptr, nullptr, 1u, r, R);
+  } else if (xfast) {
+    const uint32_t* X = ws.tb + (act ? ws.ixb[rank] : 0u) + xfirst;
+    extract_line<KIND, RESTORE, 1>(P, sh, msk, cross, xm, X, nullptr, 1u, r, R);
+  } else {
+    const uint32_t xwb = xm ? ws.xw[lane] : 1u;
+    const uint8_t* xp = xm ? reinterpret_cast<const uint8_t*>(ws.xv[lane]) + (size_t)xfirst * xwb : nullptr;
+    extract_line<KIND, RESTORE, 2>(P, sh, msk, cross, xm, nullptr, xp, xwb, r, R);
   }
 
   // 3. docIDs: segmented scan of line totals, then each item's base
