@@ -69,7 +69,7 @@ struct __align__(128) WarpSmem {
   unsigned long long mbar[kFly];
   uint32_t item[kSeq];                   // plan index of each claimed record
   uint32_t at[kFly];                     // ring offset of each staged tile
-  uint32_t end[kFly];                    // ring position after its allocation
+  uint32_t end[kFly];                    // ring bytes it gives back when decoded
   uint16_t cst[kFly], xst[kFly];         // control / exception bytes staged
   uint8_t flines[kFly];                  // 32-int lines of each staged tile (0: not decoded)
   uint8_t fvecs[kFly];                   // data vectors staged for it
@@ -1098,7 +1098,7 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
   __syncwarp();
 
   uint32_t s_claimed = 0, s_issued = 0, s_done = 0;  // positions in this warp's record sequence
-  uint32_t head = 0, tail = 0;                        // ring positions (bytes, monotonic)
+  uint32_t rpos = 0, used = 0;  // ring: next free offset, bytes held (padding included)
   bool more = true;
   bool failed = false;
   for (;;) {
@@ -1144,16 +1144,18 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
         }
       }
       const uint32_t need = (dbytes + cb + xb + 127u) & ~127u;
-      if (head == tail) head = tail = (head + kRing - 1) / kRing * kRing;  // empty: restart at offset 0
-      const uint32_t pos = head % kRing;
-      const uint32_t pad = (pos + need > (uint32_t)kRing) ? kRing - pos : 0u;
-      if (head + pad + need - tail > (uint32_t)kRing) break;  // the ring is full
-      const uint32_t start = head + pad;
-      const uint32_t off = start % kRing;
-      head = start + need;
+      if (used == 0) rpos = 0;  // empty: restart at offset 0
+      // a tile never wraps: it starts at offset 0 when it would run past the
+      // end (the bytes skipped at the end are held until it is decoded)
+      const bool wrap = rpos + need > (uint32_t)kRing;
+      const uint32_t pad = wrap ? kRing - rpos : 0u;
+      if (used + pad + need > (uint32_t)kRing) break;  // the ring is full
+      const uint32_t off = wrap ? 0u : rpos;
+      rpos = off + need;
+      used += pad + need;
       if (lane == 0) {
         ws.at[f] = off;
-        ws.end[f] = head;
+        ws.end[f] = pad + need;  // bytes the tile gives back
         ws.cst[f] = (uint16_t)cb;
         ws.xst[f] = (uint16_t)xb;
         ws.flines[f] = (uint8_t)(live ? (w_nint(w.shape) + 31) / 32 : 0u);
@@ -1203,10 +1205,9 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
     }
     if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, ws, s_done, np, nl);
     else decode_pack<KIND, K, RESTORE>(a, ws, s_done, np, nl);
+    for (uint32_t p = 0; p < np; ++p) used -= ws.end[(s_done + p) % kFly];
     s_done += np;
-    tail = ws.end[(s_done - 1) % kFly];
   }
-  (void)tail;
 }
 
 // --------------------------------------------------------------- the plan
