@@ -327,6 +327,30 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
                           const gc_launch* launch, void* d_scratch, uint64_t scratch_bytes,
                           uint32_t* d_status, void* stream);
 
+/* gc_decode for callers that cannot allocate device memory: code that runs
+ * while a stream is being captured into a CUDA graph (cudaMalloc is not
+ * allowed there), or latency-critical code that cannot afford the implicit
+ * device-wide synchronisation of cudaMalloc / cudaFree. The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ *
+ * Same arguments and results as gc_decode, without d_scratch: the scratch is
+ * a fixed 128 KiB array inside the library, which every GPU that loads the
+ * library holds until the process exits. It serves lists of at most
+ * GC_DECODE_STATIC_MAX_INTS ints; a longer list returns GC_ERR_NOSPACE at
+ * once (use gc_decode with caller scratch). The call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any
+ * stream capture. Every call on a device shares the one array, and each call
+ * clears what must start at zero before use: calls that overlap on the GPU
+ * (on two streams, or from two threads) race and must be ordered by the
+ * caller. */
+#define GC_DECODE_STATIC_MAX_INTS (1u << 20)
+gc_status gc_decode_static(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes,
+                           const uint32_t* d_data, uint64_t data_words, uint64_t n, const gc_tile* d_tiles,
+                           uint32_t* d_out, int restore_docids, uint32_t* d_status, void* stream);
+
 /* Number of kernels the last gc_* call on this host thread launched (for
  * launch accounting). */
 uint32_t gc_last_launch_count(void);

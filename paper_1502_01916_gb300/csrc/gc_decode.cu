@@ -23,6 +23,7 @@
 //      decoupled look-back;
 //   5. transposes the ints through shared memory and stores 128-byte rows.
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "gc_device.cuh"
@@ -1774,6 +1775,62 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
                         d_out_pool, out_pool_len, restore_docids, warps, bps, claim, rest, d_status, s);
   gc_host::count_launch(planned);
   return st;
+}
+
+// ------------------------------------------------- decoding without scratch
+
+}  // extern "C"
+
+namespace {
+
+// The scratch of gc_decode_static: one fixed array that every device which
+// loads the library holds until the process exits. 128 KiB covers the
+// scratch of gc_decode for GC_DECODE_STATIC_MAX_INTS ints of any codec, with
+// or without a tile index.
+constexpr uint64_t kStaticScratchBytes = 128ull << 10;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[64] = {};
+
+// The device address of g_static_scratch on the current device (in host code
+// the array's name is only a host-side stand-in). Looked up once per device.
+gc_status static_scratch(void** addr) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GC_ERR_CUDA;
+  if (dev < 0 || dev >= 64) return GC_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return GC_ERR_CUDA;
+    g_static_addr[dev] = p;
+  }
+  *addr = g_static_addr[dev];
+  return GC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gc_status gc_decode_static(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_bytes,
+                           const uint32_t* d_data, uint64_t data_words, uint64_t n, const gc_tile* d_tiles,
+                           uint32_t* d_out, int restore_docids, uint32_t* d_status, void* stream) {
+  gc_host::reset_launches();
+  gc_status st = gc_host::check_codec(codec);
+  if (st != GC_OK) return st;
+  if (n > GC_DECODE_STATIC_MAX_INTS) return GC_ERR_NOSPACE;
+  uint64_t need = 0;
+  gc_decode_scratch_size(codec, n, d_tiles != nullptr, &need);
+  if (need > kStaticScratchBytes) return GC_ERR_NOSPACE;
+  if (n == 0) return GC_OK;
+  void* scratch = nullptr;
+  st = static_scratch(&scratch);
+  if (st != GC_OK) return st;
+  // gc_decode clears what must start at zero (the claim counter, the
+  // look-back words, the plan's counts) before its kernels read them
+  return gc_decode(codec, d_ctrl, ctrl_bytes, d_data, data_words, n, d_tiles, d_out, restore_docids, scratch,
+                   kStaticScratchBytes, d_status, stream);
 }
 
 }  // extern "C"

@@ -29,7 +29,8 @@ __all__ = [
     "gc_codec", "gc_tile", "gc_list", "gc_launch", "library_path", "load", "make_codec",
     "gc_pfd_rows_for_zeta", "gc_max_encoded_size", "gc_encode_scratch_size", "gc_encode",
     "gc_encode_batch_scratch_size", "gc_encode_batch", "gc_decode_scratch_size", "gc_build_tiles",
-    "gc_decode", "gc_decode_paper", "gc_decode_batch_scratch_size", "gc_decode_batch",
+    "gc_decode", "gc_decode_paper", "gc_decode_batch_scratch_size", "gc_decode_batch", "gc_decode_static",
+    "DECODE_STATIC_MAX_INTS",
     "gc_last_launch_count", "gc_version", "EncodedList", "Index", "encode", "decode",
     "build_tiles", "decode_paper", "encode_index", "decode_index", "new_status", "check_status",
     "as_u32", "codec_name",
@@ -136,6 +137,7 @@ def load():
             "gc_build_tiles": (_I, [_CP, _V, _U64, _U64, _V, _V, _U64, _V, _V]),
             "gc_decode": (_I, [_CP, _V, _U64, _V, _U64, _U64, _V, _V, _I, _V, _U64, _V, _V]),
             "gc_decode_paper": (_I, [_CP, _V, _U64, _U64, _V, _I, _V, _U64, _V, _V]),
+            "gc_decode_static": (_I, [_CP, _V, _U64, _V, _U64, _U64, _V, _V, _I, _V, _V]),
             "gc_decode_batch_scratch_size": (_I, [_U64, _U64, _U64P]),
             "gc_decode_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I, _U64,
                                      ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
@@ -253,6 +255,17 @@ def gc_decode(codec, d_ctrl, ctrl_bytes, d_data, data_words, n, d_tiles, d_out, 
     _check(load().gc_decode(ctypes.byref(codec), _ptr(d_ctrl), ctrl_bytes, _ptr(d_data), data_words, n,
                             _ptr(d_tiles), _ptr(d_out), int(bool(restore_docids)), _ptr(d_scratch),
                             d_scratch.numel(), _ptr(d_status), _stream(stream)), "gc_decode")
+
+
+DECODE_STATIC_MAX_INTS = 1 << 20
+
+
+def gc_decode_static(codec, d_ctrl, ctrl_bytes, d_data, data_words, n, d_tiles, d_out, restore_docids, d_status,
+                     stream=None):
+    """gc_decode with the library's own fixed scratch (no allocation; n <= DECODE_STATIC_MAX_INTS)."""
+    _check(load().gc_decode_static(ctypes.byref(codec), _ptr(d_ctrl), ctrl_bytes, _ptr(d_data), data_words, n,
+                                   _ptr(d_tiles), _ptr(d_out), int(bool(restore_docids)), _ptr(d_status),
+                                   _stream(stream)), "gc_decode_static")
 
 
 def gc_decode_paper(codec, d_buf, n, d_out, restore_docids, d_scratch, d_status, stream=None):

@@ -106,6 +106,9 @@ def test_decode_rejects_missing_buffers_and_misaligned_data(gc):
     assert lib.gc_decode(ctypes.byref(c), base, 4, base, 4, 10, None, base, 1, base, 0, None, None) == 2
     # n = 0 is a no-op
     assert lib.gc_decode(ctypes.byref(c), None, 0, None, 0, 0, None, None, 1, None, 0, None, None) == 0
+    # the fixed-scratch decoder refuses a list above its limit before any CUDA call
+    assert lib.gc_decode_static(ctypes.byref(c), base, 4, base, 4, gc.DECODE_STATIC_MAX_INTS + 1, None, base, 1,
+                                None, None) == 2
 
 
 def test_scratch_sizes(gc):
