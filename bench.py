@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-list", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=0.5, help="trace length per request rate")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work budget per codec")
     return p.parse_args()
 
@@ -164,7 +166,7 @@ def reference_arm(a, rank, world):
     if rank != 0:
         return
     import synth
-    lengths = synth.zipf_index_lengths(a.nlists, 0)
+    lengths = synth.zipf_index_lengths(a.nlists, 0, a.zipf_c or synth.ZIPF_C)
     kinds = [CODECS[c][0] for c in a.codecs.split(",")]
     per_step = max(1.0, min(8.0, 150.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
@@ -385,6 +387,11 @@ def main():
     if not a.no_per_list:
         per_list = per_list_rate(gc, idxs, lengths, dev)
 
+    # serving: continuous batching over the resident index, Poisson arrivals
+    serving = None
+    if not a.no_serving:
+        serving = serving_rates(gc, idxs["pfd"] if "pfd" in idxs else next(iter(idxs.values())), a.serve_seconds)
+
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
         kinds_id = [CODECS[n][0] for n in idxs]
@@ -403,7 +410,7 @@ def main():
                    "launch": {"warps_per_block": a.warps or 4, "blocks_per_sm": a.bps or "max",
                               "items_per_claim": a.claim or 8},
                    "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},
-        "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list,
+        "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list, "serving": serving,
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(sum(launches.values()) * a.steps),
         "verified_full_output": verified, "setup_s": {"generate": t_gen, "encode": t_enc},
@@ -412,6 +419,28 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving_rates(gc, idx, seconds, rates=(1e4, 5e4, 2e5)):
+    """Requests of 2-8 lists (chosen with probability proportional to
+    length^0.5) arriving as a Poisson process, served by continuous batching
+    over the resident index; the lowest rate is also served with one decoder
+    launch per list. Latency is arrival to completion of the request's last
+    list."""
+    from paper_1502_01916_gb300 import serve
+    res = {"codec": gc.codec_name(idx.codec), "seconds": seconds, "rates": {}}
+    for rate in rates:
+        reqs = serve.poisson_trace(idx.lengths, rate, seconds, seed=int(rate))
+        srv = serve.Server(idx, arena_ints=1 << 29, streams=3)
+        wall, done = srv.run(reqs, time_limit=120.0)
+        summ = serve.latency_summary(done, wall, idx.lengths)
+        summ.update({"batches": srv.batches, "gpu_launches": srv.launches})
+        res["rates"][f"{int(rate)}"] = summ
+    rate = rates[0]
+    reqs = serve.poisson_trace(idx.lengths, rate, min(seconds, 0.2), seed=int(rate))
+    wall, done = serve.serve_one_launch_per_list(idx, reqs, time_limit=120.0)
+    res["one_launch_per_list"] = {"rate": int(rate), **serve.latency_summary(done, wall, idx.lengths)}
+    return res
 
 
 def per_list_rate(gc, idxs, lengths, dev, nsample=2000, seed=3):

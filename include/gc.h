@@ -285,6 +285,19 @@ gc_status gc_plan_batch(const gc_codec* codec, const gc_list* d_lists, uint64_t 
                         uint64_t ctrl_pool_bytes, gc_work* d_work, uint64_t work_cap, uint64_t* d_count,
                         uint32_t* d_status, void* stream);
 
+/* The work plan of a selection of an index's lists: what gc_plan_batch
+ * gives for the lists d_lists[d_sel[i]], i < nsel, each decoded to
+ * d_out_offs[i] of the output pool instead of its descriptor's out_off. A
+ * server builds one per batch of requests over a resident index (the
+ * selected lists' tiles are consecutive records, in selection order). A
+ * selection index >= nlists plans nothing for that entry. Records name the
+ * index's list (d_sel[i]). Other arguments, results and errors as for
+ * gc_plan_batch; asynchronous on `stream`, graph-capturable. */
+gc_status gc_plan_select(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists, const uint32_t* d_sel,
+                         const uint64_t* d_out_offs, uint64_t nsel, const gc_tile* d_tile_pool,
+                         uint64_t tile_pool_len, const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
+                         gc_work* d_work, uint64_t work_cap, uint64_t* d_count, uint32_t* d_status, void* stream);
+
 /* Scratch bytes gc_decode_plan needs for a plan of up to work_cap tiles. */
 gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes);
 

@@ -1217,7 +1217,10 @@ struct PlanArgs {
   uint32_t kind, k, cg, ld;
   const gc_list* lists;  // NULL: the single list `one`
   gc_list one;
-  uint64_t nlists;
+  uint64_t nlists;       // lists planned (the selection's length when sel is set)
+  const uint32_t* sel;   // optional: plan lists[sel[i]] for i < nlists ...
+  const uint64_t* outs;  // ... with their ints at outs[i] of the output pool
+  uint64_t nall;         // lists in `lists` (bounds the selection)
   const gc_tile* tiles;  // batch: tile t >= 1 of a list at tile_off + t - 1; single: tile t at t
   uint64_t ntiles;
   const uint8_t* ctrl_pool;
@@ -1228,7 +1231,17 @@ struct PlanArgs {
   uint32_t* status;
 };
 
-__device__ __forceinline__ gc_list plan_list(const PlanArgs& a, uint64_t i) { return a.lists ? a.lists[i] : a.one; }
+// The descriptor of planned list i (a selected list takes its output offset
+// from the selection); a selection index out of range gives an empty list.
+__device__ __forceinline__ gc_list plan_list(const PlanArgs& a, uint64_t i) {
+  if (!a.lists) return a.one;
+  if (!a.sel) return a.lists[i];
+  const uint32_t li = a.sel[i];
+  if (li >= a.nall) return gc_list{0, 0, 0, 0, 0, 0, 0};
+  gc_list d = a.lists[li];
+  d.out_off = a.outs[i];
+  return d;
+}
 
 // Pass 1: one thread per list reserves a contiguous range of records for the
 // list's tiles (one atomic per warp) and writes (list, tile) into each. A
@@ -1393,6 +1406,7 @@ __global__ void k_plan_fill(PlanArgs a) {
   w.win_at = (int32_t)((int64_t)wlo - (int64_t)d.ctrl_off);
   w.win_len = (uint16_t)min64(whi - wlo, 0xfff0);
   w.exc_len = (uint16_t)xlen;
+  if (a.sel) w.list = a.sel[w.list];  // records name the index's list
   w.shape = (nint - 1) | ((uint32_t)(v1 - v0) << GC_WORK_VEC_SHIFT) | ((uint32_t)(first_bit & 31) << GC_WORK_BIT_SHIFT) |
             ((r0.row_skip & 31u) << GC_WORK_SKIP_SHIFT) | (has_base ? (uint32_t)GC_WORK_HAS_BASE : 0u) |
             (publish ? (uint32_t)GC_WORK_PUBLISH : 0u);
@@ -1496,7 +1510,8 @@ gc_status launch_shape(const gc_launch* l, uint32_t* warps, uint32_t* bps, uint3
 
 gc_status plan_impl(const gc_codec& c, const gc_list* lists, const gc_list* one, uint64_t nlists,
                     const gc_tile* tiles, uint64_t ntiles, const uint8_t* ctrl_pool, uint64_t ctrl_pool_bytes,
-                    gc_work* work, uint64_t cap, uint64_t* count, uint32_t* status, cudaStream_t s) {
+                    gc_work* work, uint64_t cap, uint64_t* count, uint32_t* status, cudaStream_t s,
+                    const uint32_t* sel = nullptr, const uint64_t* outs = nullptr, uint64_t nall = 0) {
   if (cudaMemsetAsync(count, 0, 16, s) != cudaSuccess) return GC_ERR_CUDA;
   if (nlists == 0) return GC_OK;
   PlanArgs a = {};
@@ -1507,6 +1522,9 @@ gc_status plan_impl(const gc_codec& c, const gc_list* lists, const gc_list* one,
   a.lists = lists;
   if (one) a.one = *one;
   a.nlists = nlists;
+  a.sel = sel;
+  a.outs = outs;
+  a.nall = sel ? nall : nlists;
   a.tiles = tiles;
   a.ntiles = tiles ? ntiles : 0;
   a.ctrl_pool = ctrl_pool;
@@ -1697,6 +1715,20 @@ gc_status gc_plan_batch(const gc_codec* codec, const gc_list* d_lists, uint64_t 
   if (((uintptr_t)d_work & 15) != 0) return GC_ERR_INVALID;
   return plan_impl(*codec, d_lists, nullptr, nlists, d_tile_pool, tile_pool_len, d_ctrl_pool, ctrl_pool_bytes, d_work,
                    work_cap, d_count, d_status, (cudaStream_t)stream);
+}
+
+gc_status gc_plan_select(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists, const uint32_t* d_sel,
+                         const uint64_t* d_out_offs, uint64_t nsel, const gc_tile* d_tile_pool, uint64_t tile_pool_len,
+                         const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes, gc_work* d_work, uint64_t work_cap,
+                         uint64_t* d_count, uint32_t* d_status, void* stream) {
+  gc_host::reset_launches();
+  gc_status st = gc_host::check_codec(codec);
+  if (st != GC_OK) return st;
+  if (!d_count || (nsel && (!d_lists || !d_sel || !d_out_offs || !d_work))) return GC_ERR_INVALID;
+  if (nlists > 0xffffffffull || nsel > 0xffffffffull || work_cap > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  if (((uintptr_t)d_work & 15) != 0) return GC_ERR_INVALID;
+  return plan_impl(*codec, d_lists, nullptr, nsel, d_tile_pool, tile_pool_len, d_ctrl_pool, ctrl_pool_bytes, d_work,
+                   work_cap, d_count, d_status, (cudaStream_t)stream, d_sel, d_out_offs, nlists);
 }
 
 gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes) {

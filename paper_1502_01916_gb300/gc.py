@@ -24,7 +24,8 @@ __all__ = [
     "SIMPLE", "SCHEME", "AFOR", "PFD", "LD_BINARY", "LD_CU", "LD_IU", "TILE_INTS", "TILE_BYTES", "LIST_BYTES",
     "TILE_BASE", "WORK_VEC_SHIFT", "WORK_BIT_SHIFT", "WORK_SKIP_SHIFT", "WORK_HAS_BASE", "WORK_PUBLISH",
     "TILE_DTYPE", "LIST_DTYPE", "WORK_DTYPE",
-    "WORK_BYTES", "GcError", "gc_work", "gc_plan_batch", "gc_decode_plan_scratch_size", "gc_decode_plan", "Plan",
+    "WORK_BYTES", "GcError", "gc_work", "gc_plan_batch", "gc_plan_select", "gc_decode_plan_scratch_size",
+    "gc_decode_plan", "Plan",
     "plan_index",
     "gc_codec", "gc_tile", "gc_list", "gc_launch", "library_path", "load", "make_codec",
     "gc_pfd_rows_for_zeta", "gc_max_encoded_size", "gc_encode_scratch_size", "gc_encode",
@@ -142,6 +143,7 @@ def load():
             "gc_decode_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I, _U64,
                                      ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
             "gc_plan_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V]),
+            "gc_plan_select": (_I, [_CP, _V, _U64, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V]),
             "gc_decode_plan_scratch_size": (_I, [_U64, _U64P]),
             "gc_decode_plan": (_I, [_CP, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I,
                                     ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
@@ -296,6 +298,15 @@ def gc_plan_batch(codec, d_lists, nlists, d_tile_pool, d_ctrl_pool, d_work, d_co
     _check(load().gc_plan_batch(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_tile_pool), tile_len,
                                 _ptr(d_ctrl_pool), d_ctrl_pool.numel(), _ptr(d_work), d_work.numel() // WORK_BYTES,
                                 _ptr(d_count), _ptr(d_status), _stream(stream)), "gc_plan_batch")
+
+
+def gc_plan_select(codec, d_lists, nlists, d_sel, d_out_offs, nsel, d_tile_pool, d_ctrl_pool, d_work, d_count,
+                   d_status, stream=None):
+    tile_len = d_tile_pool.numel() // TILE_BYTES if d_tile_pool is not None else 0
+    _check(load().gc_plan_select(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_sel), _ptr(d_out_offs), nsel,
+                                 _ptr(d_tile_pool), tile_len, _ptr(d_ctrl_pool), d_ctrl_pool.numel(), _ptr(d_work),
+                                 d_work.numel() // WORK_BYTES, _ptr(d_count), _ptr(d_status), _stream(stream)),
+           "gc_plan_select")
 
 
 def gc_decode_plan_scratch_size(work_cap: int) -> int:
