@@ -31,9 +31,13 @@ if ROOT not in sys.path:
 
 UNIVERSE = 25_000_000
 CODECS = {"simple": (0, "Group-Simple"), "pfd": (3, "Group-PFD")}
-# DRAM bytes (read + write) per decode launch from one ncu capture, with the
-# hash of the kernel sources they were taken on; a stale hash reports null.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per decode launch of the default workload, from one
+# ncu capture (profiles/k_decode_zipf_index_dram.md), with the hash of the
+# kernel sources they were taken on; once the sources change, null.
+NCU_TRAFFIC = {
+    "simple": {"bytes": 2929310720 + 5942661632, "hash": "d0dd3f2f5321decc"},
+    "pfd": {"bytes": 2406914560 + 5939302400, "hash": "d0dd3f2f5321decc"},
+}
 
 
 def parse():
@@ -329,7 +333,8 @@ def main():
     dom = max(per_codec, key=lambda n: per_codec[n]["ms_per_launch"])
     kh = kernel_hash()
     traffic = NCU_TRAFFIC.get(dom)
-    traffic = traffic["bytes"] if traffic and traffic.get("hash") == kh else None
+    default_workload = a.nlists == 1_000_000 and not a.zipf_c and a.k == 32 and a.zeta == 0.10
+    traffic = traffic["bytes"] if traffic and traffic.get("hash") == kh and default_workload else None
     roofline = {"bound": "hbm", "kernel": f"k_decode<{CODECS[dom][1]}, k={a.k}, batched>",
                 "bytes_per_launch": per_codec[dom]["algorithmic_bytes"],
                 "achieved": per_codec[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
