@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--warps", type=int, default=0, help="warps per block (0 = library default)")
     p.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = as many as fit)")
     p.add_argument("--claim", type=int, default=0, help="tiles per claim (0 = library default)")
+    p.add_argument("--no-tune", action="store_true", help="library default launch shape instead of the autotuner's")
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-list", action="store_true")
@@ -238,10 +239,22 @@ def main():
     torch.cuda.empty_cache()
 
     out = torch.empty(total_ints, dtype=torch.int32, device=dev)
-    launch = gc.gc_launch(a.warps, a.bps, a.claim) if (a.warps or a.bps or a.claim) else None
     scratch = {n: torch.empty(gc.gc_decode_plan_scratch_size(i.max_tiles), dtype=torch.uint8, device=dev)
                for n, i in idxs.items()}
     status = {n: gc.new_status(dev) for n in idxs}
+    # launch shape per codec: given on the command line, the library default,
+    # or the autotuner's choice (timed on this index, before the timed region)
+    launches_cfg, tuned = {}, {}
+    for n, idx in idxs.items():
+        if a.warps or a.bps or a.claim:
+            launches_cfg[n] = gc.gc_launch(a.warps, a.bps, a.claim)
+        elif a.no_tune:
+            launches_cfg[n] = None
+        else:
+            from paper_1502_01916_gb300.tune import tune
+            launches_cfg[n], info = tune(idx, plans[n], use_cache=False)
+            tuned[n] = {"shape": [launches_cfg[n].warps_per_block, launches_cfg[n].blocks_per_sm,
+                                  launches_cfg[n].items_per_claim], "ms": info["ms"]}
 
     # correctness at full size: every docID against the host's prefix sums
     verified = None
@@ -252,7 +265,8 @@ def main():
         del cs
         verified = True
         for n, idx in idxs.items():
-            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, plan=plans[n])
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launches_cfg[n],
+                            plan=plans[n])
             if not np.array_equal(gc.as_u32(out), want):
                 verified = False
                 print(f"VERIFY FAILED for {n}", file=sys.stderr)
@@ -265,12 +279,12 @@ def main():
     graphs, launches = {}, {}
     for n, idx in idxs.items():
         with torch.cuda.stream(stream):
-            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, check=False,
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launches_cfg[n], check=False,
                             plan=plans[n])
         stream.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
-            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launch, check=False,
+            gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launches_cfg[n], check=False,
                             plan=plans[n])
         launches[n] = gc.gc_last_launch_count()
         graphs[n] = g
@@ -395,7 +409,8 @@ def main():
     # serving: continuous batching over the resident index, Poisson arrivals
     serving = None
     if not a.no_serving:
-        serving = serving_rates(gc, idxs["pfd"] if "pfd" in idxs else next(iter(idxs.values())), a.serve_seconds)
+        sn = "pfd" if "pfd" in idxs else next(iter(idxs))
+        serving = serving_rates(gc, idxs[sn], a.serve_seconds, launch=launches_cfg[sn])
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
@@ -412,8 +427,10 @@ def main():
                    "codecs": [CODECS[n][1] + (f" zeta={a.zeta}" if n == "pfd" else "") for n in idxs],
                    "k": a.k, "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "launch": {"warps_per_block": a.warps or 4, "blocks_per_sm": a.bps or "max",
-                              "items_per_claim": a.claim or 8},
+                   "launch": ({n: {"warps_per_block": l.warps_per_block, "blocks_per_sm": l.blocks_per_sm or "max",
+                                   "items_per_claim": l.items_per_claim} if l is not None else "library default"
+                               for n, l in launches_cfg.items()}),
+                   "autotuned": tuned or None,
                    "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},
         "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list, "serving": serving,
         "cpu_baseline": cpu, "clocks": clk,
@@ -426,7 +443,7 @@ def main():
         dist.destroy_process_group()
 
 
-def serving_rates(gc, idx, seconds, rates=(1e4, 5e4, 2e5)):
+def serving_rates(gc, idx, seconds, rates=(1e4, 5e4, 2e5), launch=None):
     """Requests of 2-8 lists (chosen with probability proportional to
     length^0.5) arriving as a Poisson process, served by continuous batching
     over the resident index; the lowest rate is also served with one decoder
@@ -436,7 +453,7 @@ def serving_rates(gc, idx, seconds, rates=(1e4, 5e4, 2e5)):
     res = {"codec": gc.codec_name(idx.codec), "seconds": seconds, "rates": {}}
     for rate in rates:
         reqs = serve.poisson_trace(idx.lengths, rate, seconds, seed=int(rate))
-        srv = serve.Server(idx, arena_ints=1 << 29, streams=3)
+        srv = serve.Server(idx, arena_ints=1 << 29, streams=3, launch=launch)
         wall, done = srv.run(reqs, time_limit=120.0)
         summ = serve.latency_summary(done, wall, idx.lengths)
         summ.update({"batches": srv.batches, "gpu_launches": srv.launches})

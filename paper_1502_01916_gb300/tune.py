@@ -1,0 +1,104 @@
+"""Autotuner of the persistent decoder's launch shape.
+
+The decoder's speed on a given index depends on how many warps share a block
+(shared memory per block, claims per SM) and on how many tiles a warp claims
+at once (atomics against the pipeline depth of its staging ring). This module
+times gc_decode_plan on the caller's resident index for a small grid of
+shapes, keeps the fastest, and caches it in a JSON file keyed by the device,
+the codec and the workload class (how long the index's lists are), so that a
+server or benchmark tunes once per kind of index.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import numpy as np
+
+from . import gc as _gc
+
+DEFAULT_CANDIDATES = [(w, 0, c) for w in (2, 4, 8) for c in (4, 8, 16)]
+_lock = threading.Lock()
+
+
+def workload_class(lengths) -> str:
+    """Short (most lists fit one tile), mixed, or long lists: the median
+    list length and the share of ints in lists of more than one tile."""
+    L = np.asarray(lengths, dtype=np.int64)
+    if len(L) == 0:
+        return "empty"
+    med = float(np.median(L))
+    multi = float(L[L > _gc.TILE_INTS].sum()) / max(1, int(L.sum()))
+    size = "short" if med < 64 else "mid" if med < 1024 else "long"
+    share = "multi" if multi > 0.5 else "single"
+    return f"{size}-{share}"
+
+
+def cache_key(device_name: str, codec, lengths, restore: bool) -> str:
+    return f"{device_name}|{_gc.codec_name(codec)}|{workload_class(lengths)}|{'ids' if restore else 'gaps'}"
+
+
+def default_cache_path() -> str:
+    base = os.environ.get("GC_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "gc_tune.json")
+    return base
+
+
+def load_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(path: str, cache: dict):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tune(index, plan=None, restore_docids: bool = True, candidates=None, reps: int = 3, cache_path: str | None = None,
+         use_cache: bool = True):
+    """The fastest launch shape for decoding `index` (a gc.Index) and its
+    timings. Returns (gc_launch, {"key", "best_ms", "ms": {shape: ms}, "cached"})."""
+    import torch
+    dev = index.data.device
+    name = torch.cuda.get_device_name(dev)
+    key = cache_key(name, index.codec, index.lengths, restore_docids)
+    path = cache_path or default_cache_path()
+    if use_cache:
+        with _lock:
+            hit = load_cache(path).get(key)
+        if hit:
+            w, b, c = hit["shape"]
+            return _gc.gc_launch(w, b, c), {"key": key, "best_ms": hit["ms"], "ms": {}, "cached": True}
+    plan = plan if plan is not None else _gc.plan_index(index)
+    out = torch.empty(max(1, index.total_ints), dtype=torch.int32, device=dev)
+    scratch = torch.empty(_gc.gc_decode_plan_scratch_size(index.max_tiles), dtype=torch.uint8, device=dev)
+    st = _gc.new_status(dev)
+    times = {}
+    for shape in candidates or DEFAULT_CANDIDATES:
+        launch = _gc.gc_launch(*shape)
+        _gc.decode_index(index, out=out, restore_docids=restore_docids, launch=launch, scratch=scratch, status=st,
+                         plan=plan, check=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for s, e in ev:
+            s.record()
+            _gc.decode_index(index, out=out, restore_docids=restore_docids, launch=launch, scratch=scratch,
+                             status=st, plan=plan, check=False)
+            e.record()
+        torch.cuda.synchronize(dev)
+        times[shape] = float(np.median([s.elapsed_time(e) for s, e in ev]))
+    _gc.check_status(st, "tuning decode")
+    best = min(times, key=times.get)
+    if use_cache:
+        with _lock:
+            cache = load_cache(path)
+            cache[key] = {"shape": list(best), "ms": times[best]}
+            save_cache(path, cache)
+    return _gc.gc_launch(*best), {"key": key, "best_ms": times[best],
+                                  "ms": {f"{w}x{b}x{c}": t for (w, b, c), t in times.items()}, "cached": False}
