@@ -317,8 +317,12 @@ def test_batch_overflow_reports_nospace(gc):
 
 # ------------------------------------------------------------ full sizes
 
-@pytest.mark.parametrize("c", [(O.SIMPLE, 4, 0, 0, 0.1), (O.PFD, 32, 0, 0, 0.1), (O.SCHEME, 32, 8, 2, 0.1)],
-                         ids=cid)
+CONFIG2 = [(O.SIMPLE, k, 0, 0, 0.1) for k in (4, 32)] + \
+    [(O.SCHEME, k, cg, ld, 0.1) for k in (4, 32) for cg, ld in [(1, 0), (1, 1), (8, 0), (8, 2), (8, 1)]] + \
+    [(O.AFOR, k, 0, 0, 0.1) for k in (4, 32)] + [(O.PFD, k, 0, 0, 0.1) for k in (4, 32)]
+
+
+@pytest.mark.parametrize("c", CONFIG2, ids=cid)
 def test_mixed_2_26_single_list(gc, c):
     """2^26 d-gaps (90% geometric mean 8, 10% uniform to 2^20, runs of 256):
     GPU encoding equals the oracle's; one-launch decode restores the gaps
@@ -336,3 +340,42 @@ def test_mixed_2_26_single_list(gc, c):
     assert (got == want).all()
     got = gc.as_u32(gc.decode(enc, restore_docids=True, use_tiles=False))  # 2^16 tiles by look-back
     assert (got == want).all()
+
+
+def _segmented_prefix(gaps, off, lengths):
+    """docIDs of every list of an index from its gaps (uint32 wraparound)."""
+    cs = np.cumsum(gaps, dtype=np.uint32)
+    starts = off[:-1].astype(np.int64)
+    before = np.where(starts > 0, cs[np.maximum(starts - 1, 0)], 0).astype(np.uint32)
+    return cs - np.repeat(before, lengths.astype(np.int64))
+
+
+@pytest.fixture(scope="module")
+def clustered_index():
+    """4,000,000 lists over 50M documents: log-normal lengths (median 12,
+    sigma 1.5), docIDs in clustered runs (mean 16) separated by jumps (mean
+    5000)."""
+    gaps, off, lengths = synth.clustered_short_index(4_000_000, 50_000_000, 0)
+    return gaps, off, lengths
+
+
+@pytest.mark.parametrize("c", [(O.SCHEME, 32, 8, 2, 0.1), (O.SCHEME, 32, 8, 0, 0.1), (O.PFD, 32, 0, 0, 0.01),
+                               (O.PFD, 32, 0, 0, 0.1), (O.PFD, 32, 0, 0, 0.3)], ids=cid)
+def test_clustered_short_lists_4m(gc, clustered_index, c):
+    """The clustered short-list index: every docID of one batched decode
+    equals the host's prefix sums, and a sample of lists is encoded exactly
+    as the oracle encodes it."""
+    oc, gcc = pair(gc, c)
+    gaps, off, lengths = clustered_index
+    idx = gc.encode_index(gcc, upload_u32(gaps), lengths)
+    out = gc.decode_index(idx, restore_docids=True)
+    want = _segmented_prefix(gaps, off, lengths)
+    assert (gc.as_u32(out)[:len(gaps)] == want).all()
+    lists = idx.lists.cpu().numpy().view(gc.LIST_DTYPE)
+    ctrl_pool, data_pool = idx.ctrl.cpu().numpy(), gc.as_u32(idx.data)
+    rng = np.random.default_rng(1)
+    for i in rng.choice(len(lengths), 300, replace=False).tolist():
+        ctrl, data = O.encode(oc, gaps[off[i]:off[i + 1]])
+        d = lists[i]
+        assert ctrl_pool[d["ctrl_off"]:d["ctrl_off"] + len(ctrl)].tobytes() == ctrl.tobytes(), f"list {i}"
+        assert (data_pool[d["data_off"]:d["data_off"] + len(data)] == data).all(), f"list {i}"
