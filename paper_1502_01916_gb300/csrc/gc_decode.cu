@@ -47,6 +47,8 @@ constexpr int kFly = 16;        // tiles staged at once per warp (one mbarrier e
 constexpr int kCtrlCap = 512;   // control bytes staged per tile at most
 constexpr int kExcCap = 1024;   // exception bytes staged per tile (all or none)
 
+static_assert(kFly == kSeq, "a claimed record's staging slot is its record slot");
+
 constexpr int kPadVec = 34;     // k = 32: data vectors of a pack, re-laid at 33 words each
 constexpr int kPad = 33;        // words per re-laid vector (one bank apart per vector)
 
@@ -72,8 +74,9 @@ struct __align__(128) WarpSmem {
   uint32_t at[kFly];                     // ring offset of each staged tile
   uint32_t end[kFly];                    // ring bytes it gives back when decoded
   uint16_t cst[kFly], xst[kFly];         // control / exception bytes staged
+  uint16_t need[kFly];                   // ring bytes it takes (all staged bytes, 128-byte rounded)
   uint8_t flines[kFly];                  // 32-int lines of each staged tile (0: not decoded)
-  uint8_t fvecs[kFly];                   // data vectors staged for it
+  uint16_t fvecs[kFly];                  // data vectors staged for it
   unsigned long long iout[32];           // pack item (by rank among decoded ones): first output int
   uint32_t inint[32];                    // its ints
   uint32_t ibase[32];                    // its docID base
@@ -864,15 +867,16 @@ __device__ __forceinline__ void extract_line(const uint32_t* P, uint32_t sh, uin
 // (one row of 32 ints) in natural column order with fixed offsets, and its
 // running sum is directly the prefix within the line.
 template <int KIND, bool RESTORE>
-__device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0, uint32_t np, uint32_t nl) {
+__device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0, uint32_t np, uint32_t nl,
+                              uint32_t lv, uint32_t lvi) {
   const uint32_t lane = lane_id();
 
-  // items: lane p < np holds item p
-  const uint32_t fp = (s0 + lane) % kFly;
-  const uint32_t my_lines = lane < np ? ws.flines[fp] : 0u;
-  const uint32_t my_vecs = lane < np ? ws.fvecs[fp] : 0u;
-  const uint32_t my_line0 = warp_incl_sum(my_lines) - my_lines;
-  const uint32_t my_vec0 = warp_incl_sum(my_vecs) - my_vecs;
+  // items: lane p < np holds item p, its lines and vectors (lv: lines |
+  // vectors << 16) and their inclusive sums over the pack (lvi)
+  const uint32_t my_lines = lv & 0xffffu;
+  const uint32_t my_vecs = lv >> 16;
+  const uint32_t my_line0 = (lvi & 0xffffu) - my_lines;
+  const uint32_t my_vec0 = (lvi >> 16) - my_vecs;
   const bool my_live = my_lines > 0;
   const uint32_t live = __ballot_sync(kFull, my_live);
   const uint32_t heads = __reduce_or_sync(kFull, my_live ? 1u << my_line0 : 0u);
@@ -897,7 +901,7 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
 
   // Group-PFD: the exception values of the pack go, as 32-bit words, to the
   // part of the buffer past the re-laid vectors (when they all fit)
-  const uint32_t xfree0 = __shfl_sync(kFull, my_vec0 + my_vecs, 31) * kPad;
+  const uint32_t xfree0 = __shfl_sync(kFull, lvi >> 16, np - 1) * kPad;
   uint32_t xused = 0;
   bool xfast = true;
 
@@ -972,18 +976,9 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     // the tile is one frame: exceptions before this line in it
     xm = act ? ws.xm[lane] : 0u;
     const uint32_t cnt = __popc(xm);
-    uint32_t v = cnt;
-    bool f = !act || lane == lhead;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, v, o);
-      const bool g = __shfl_up_sync(kFull, f, o);
-      if (lane >= (uint32_t)o && !f) {
-        v += y;
-        f = g;
-      }
-    }
-    xfirst = v - cnt;
+    const uint32_t V = warp_incl_sum(cnt);
+    const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
+    xfirst = V - cnt - (lhead ? Vb : 0u);
   }
   uint32_t r[32];
   uint32_t R = 0;
@@ -1001,19 +996,12 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   // 3. docIDs: segmented scan of line totals, then each item's base
   uint32_t k0 = 0;
   if (RESTORE) {
-    const uint32_t T = R;
-    uint32_t v = act ? T : 0u;
-    bool f = !act || lane == lhead;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, v, o);
-      const bool g = __shfl_up_sync(kFull, f, o);
-      if (lane >= (uint32_t)o && !f) {
-        v += y;
-        f = g;
-      }
-    }
-    const uint32_t E = v - (act ? T : 0u);
+    // (a plain scan, less the scan before the item's first line)
+    const uint32_t T = act ? R : 0u;
+    const uint32_t V = warp_incl_sum(T);
+    const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
+    const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
+    const uint32_t E = v - T;
     const uint32_t lastl = my_live ? my_line0 + my_lines - 1 : 0u;
     const uint32_t tot = __shfl_sync(kFull, v, lastl);
     const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
@@ -1078,6 +1066,35 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   __syncwarp();
 }
 
+// What staging a claimed record takes, found once when it is claimed: its
+// data vectors, control window and (Group-PFD) exception window, all in
+// the ring at 128-byte granularity; a record that fails its checks stages
+// nothing and decodes to nothing (its error is reported here).
+template <int KIND, int K>
+__device__ __forceinline__ void stage_sizes(const gc_work& w, const DecodeArgs& a, WarpSmem<K>& ws, uint32_t f) {
+  uint32_t dbytes = 0, cb = 0, xb = 0, lines = 0;
+  const bool live = w_live<K>(w, a);
+  if (!live && w.list != 0xffffffffu)
+    report(a.status, w.out_at + w_nint(w.shape) > a.out_pool_len ? GC_ERR_INVALID : GC_ERR_CORRUPT, w.list);
+  if (live) {
+    lines = (w_nint(w.shape) + 31) / 32;
+    dbytes = w_vecs(w.shape) * K * 4;
+    const int64_t ws0 = (int64_t)w.ctrl_at + w.win_at;
+    cb = w.win_len < kCtrlCap ? w.win_len : (uint32_t)kCtrlCap;
+    if (ws0 < 0 || (ws0 & 15) || (uint64_t)ws0 + cb > a.ctrl_pool_bytes) cb = 0;
+    if (KIND == GC_PFD) {
+      const uint64_t xs = (w.ctrl_at + w.exc_at) & ~15ull;
+      xb = w.exc_len;
+      if (xb > (uint32_t)kExcCap || xs + xb > a.ctrl_pool_bytes) xb = 0;
+    }
+  }
+  ws.need[f] = (uint16_t)((dbytes + cb + xb + 127u) & ~127u);
+  ws.cst[f] = (uint16_t)cb;
+  ws.xst[f] = (uint16_t)xb;
+  ws.flines[f] = (uint8_t)lines;
+  ws.fvecs[f] = (uint16_t)(dbytes / (K * 4));
+}
+
 template <int KIND, int K, bool RESTORE>
 __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1113,79 +1130,85 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
         more = false;
       } else {
         if (lane < cnt) {
+          const uint32_t f = (s_claimed + lane) % kSeq;
           const uint4* src = reinterpret_cast<const uint4*>(a.work + x + lane);
-          uint4* dst = ws.rec[(s_claimed + lane) % kSeq];
-          dst[0] = __ldg(src);
-          dst[1] = __ldg(src + 1);
-          dst[2] = __ldg(src + 2);
-          dst[3] = __ldg(src + 3);
-          ws.item[(s_claimed + lane) % kSeq] = x + lane;
+          union {
+            uint4 q[4];
+            gc_work w;
+          } u;
+          u.q[0] = __ldg(src);
+          u.q[1] = __ldg(src + 1);
+          u.q[2] = __ldg(src + 2);
+          u.q[3] = __ldg(src + 3);
+          uint4* dst = ws.rec[f];
+          dst[0] = u.q[0];
+          dst[1] = u.q[1];
+          dst[2] = u.q[2];
+          dst[3] = u.q[3];
+          ws.item[f] = x + lane;
+          stage_sizes<KIND, K>(u.w, a, ws, f);
         }
         __syncwarp();
         s_claimed += cnt;
       }
     }
-    // stage claimed tiles while the ring and the mbarriers allow
-    while (s_issued < s_claimed && s_issued - s_done < (uint32_t)kFly) {
-      const gc_work& w = rec_at(ws.rec, s_issued);
-      const uint32_t f = s_issued % kFly;
-      uint32_t dbytes = 0, cb = 0, xb = 0;
-      const bool live = w_live<K>(w, a);
-      if (!live && w.list != 0xffffffffu && lane == 0)
-        report(a.status, w.out_at + w_nint(w.shape) > a.out_pool_len ? GC_ERR_INVALID : GC_ERR_CORRUPT, w.list);
-      if (live) {
-        dbytes = w_vecs(w.shape) * K * 4;
-        const int64_t ws0 = (int64_t)w.ctrl_at + w.win_at;
-        cb = w.win_len < kCtrlCap ? w.win_len : (uint32_t)kCtrlCap;
-        if (ws0 < 0 || (ws0 & 15) || (uint64_t)ws0 + cb > a.ctrl_pool_bytes) cb = 0;
-        if (KIND == GC_PFD) {
-          const uint64_t xs = (w.ctrl_at + w.exc_at) & ~15ull;
-          xb = w.exc_len;
-          if (xb > (uint32_t)kExcCap || xs + xb > a.ctrl_pool_bytes) xb = 0;
+    // stage claimed tiles while the ring and the mbarriers allow: lane p
+    // takes record s_issued + p. A tile never wraps: it starts at offset 0
+    // when it would run past the end, and the bytes skipped there are held
+    // until it is decoded. Every offset follows from one scan of the tiles'
+    // sizes; the tiles that fit are a prefix of the candidates (none when
+    // the first does not fit, the usual case while the ring is full).
+    if (s_issued < s_claimed && s_issued - s_done < (uint32_t)kFly) {
+      const uint32_t r0 = used ? rpos : 0u;  // empty: restart at offset 0
+      const uint32_t need0 = ws.need[s_issued % kFly];
+      const uint32_t pad0 = r0 + need0 > (uint32_t)kRing ? kRing - r0 : 0u;
+      if (used + pad0 + need0 <= (uint32_t)kRing) {
+        const uint32_t cands = min(s_claimed - s_issued, (uint32_t)kFly - (s_issued - s_done));
+        const uint32_t s = s_issued + lane;
+        const uint32_t f = s % kFly;
+        const bool cand = lane < cands;
+        const uint32_t need = cand ? ws.need[f] : 0u;
+        const uint32_t incl = warp_incl_sum(need);
+        const uint32_t excl = incl - need;
+        const uint32_t wrapm = __ballot_sync(kFull, cand && r0 + incl > (uint32_t)kRing);
+        const uint32_t pw = wrapm ? __ffs(wrapm) - 1 : 32u;  // the first tile that would run past the end
+        const uint32_t ew = __shfl_sync(kFull, excl, pw & 31u);
+        const uint32_t pad = wrapm ? kRing - (r0 + ew) : 0u;
+        const bool after = lane >= pw;
+        const uint32_t off = after ? excl - ew : r0 + excl;
+        const uint32_t n =
+            __popc(__ballot_sync(kFull, cand && used + incl + (after ? pad : 0u) <= (uint32_t)kRing));
+        if (lane < n) {
+          const gc_work& w = rec_at(ws.rec, s);
+          const uint32_t dbytes = ws.fvecs[f] * (K * 4u), cb = ws.cst[f], xb = ws.xst[f];
+          ws.at[f] = off;
+          ws.end[f] = need + (lane == pw ? pad : 0u);  // bytes the tile gives back
+          mbar_expect_tx(&ws.mbar[f], dbytes + cb + xb);
+          if (dbytes) bulk_g2s(ws.ring + off, a.data_pool + w.data_at, dbytes, &ws.mbar[f]);
+          if (cb) bulk_g2s(ws.ring + off + dbytes, a.ctrl_pool + (w.ctrl_at + w.win_at), cb, &ws.mbar[f]);
+          if (xb)
+            bulk_g2s(ws.ring + off + dbytes + cb, a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull), xb,
+                     &ws.mbar[f]);
         }
+        rpos = __shfl_sync(kFull, off + need, n - 1);
+        used += __shfl_sync(kFull, incl, n - 1) + (pw < n ? pad : 0u);
+        __syncwarp();
+        s_issued += n;
       }
-      const uint32_t need = (dbytes + cb + xb + 127u) & ~127u;
-      if (used == 0) rpos = 0;  // empty: restart at offset 0
-      // a tile never wraps: it starts at offset 0 when it would run past the
-      // end (the bytes skipped at the end are held until it is decoded)
-      const bool wrap = rpos + need > (uint32_t)kRing;
-      const uint32_t pad = wrap ? kRing - rpos : 0u;
-      if (used + pad + need > (uint32_t)kRing) break;  // the ring is full
-      const uint32_t off = wrap ? 0u : rpos;
-      rpos = off + need;
-      used += pad + need;
-      if (lane == 0) {
-        ws.at[f] = off;
-        ws.end[f] = pad + need;  // bytes the tile gives back
-        ws.cst[f] = (uint16_t)cb;
-        ws.xst[f] = (uint16_t)xb;
-        ws.flines[f] = (uint8_t)(live ? (w_nint(w.shape) + 31) / 32 : 0u);
-        ws.fvecs[f] = (uint8_t)(dbytes / (K * 4));
-        fence_proxy_async();
-        mbar_expect_tx(&ws.mbar[f], dbytes + cb + xb);
-        if (dbytes) bulk_g2s(ws.ring + off, a.data_pool + w.data_at, dbytes, &ws.mbar[f]);
-        if (cb) bulk_g2s(ws.ring + off + dbytes, a.ctrl_pool + (w.ctrl_at + w.win_at), cb, &ws.mbar[f]);
-        if (xb)
-          bulk_g2s(ws.ring + off + dbytes + cb, a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull), xb, &ws.mbar[f]);
-      }
-      __syncwarp();
-      ++s_issued;
     }
     if (s_done == s_issued) {
       if (!more && s_issued == s_claimed) break;
       continue;
     }
-    // a pack: records from s_done on while their lines fit 32
-    uint32_t np = 0, nl = 0, nv = 0;
-    while (s_done + np < s_issued && np < 32) {
-      const uint32_t f = (s_done + np) % kFly;
-      const uint32_t lines = ws.flines[f];
-      const uint32_t vecs = ws.fvecs[f];
-      if (nl + lines > 32 || (K == 32 && nv + vecs > (uint32_t)kPadVec)) break;
-      nl += lines;
-      nv += vecs;
-      ++np;
-    }
+    // a pack: the staged records from s_done on while their lines fit 32
+    // (and, k = 32, their vectors the re-lay buffer); one scan of both
+    const uint32_t staged = s_issued - s_done;
+    const uint32_t fp = (s_done + lane) % kFly;
+    const uint32_t lv = lane < staged ? ws.flines[fp] | (uint32_t)ws.fvecs[fp] << 16 : 0u;
+    const uint32_t lvi = warp_incl_sum(lv);
+    const uint32_t np = __popc(__ballot_sync(
+        kFull, lane < staged && (lvi & 0xffffu) <= 32u && (K != 32 || (lvi >> 16) <= (uint32_t)kPadVec)));
+    const uint32_t nl = __shfl_sync(kFull, lvi & 0xffffu, np - 1);
     // wait for their copies
     for (uint32_t p = 0; p < np && !failed; ++p) {
       const uint32_t s = s_done + p;
@@ -1204,9 +1227,9 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
       if (lane == 0) report(a.status, GC_ERR_TIMEOUT, 0xfffffffeu);
       break;
     }
-    if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, ws, s_done, np, nl);
+    if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, ws, s_done, np, nl, lane < np ? lv : 0u, lvi);
     else decode_pack<KIND, K, RESTORE>(a, ws, s_done, np, nl);
-    for (uint32_t p = 0; p < np; ++p) used -= ws.end[(s_done + p) % kFly];
+    used -= __reduce_add_sync(kFull, lane < np ? ws.end[fp] : 0u);
     s_done += np;
   }
 }
