@@ -169,6 +169,19 @@ struct CtrlView {
   __device__ __forceinline__ uint32_t bits(uint64_t pos, uint32_t width) const {
     return (le(pos >> 3, 4) >> (pos & 7)) & low_mask(width);
   }
+  // whether bytes lo..hi (inclusive) of the list are all in the staged
+  // control window (then s1[off - lo1] reads them)
+  __device__ __forceinline__ bool in_win1(uint64_t lo, uint64_t hi) const {
+    return hi < size && (int64_t)lo >= lo1 && hi - (uint64_t)lo1 < len1;
+  }
+  // 4 little-endian bytes at off (off + 4 <= size)
+  __device__ __forceinline__ uint32_t le4(uint64_t off) const {
+    if (in_win1(off, off + 3)) {
+      const uint8_t* p = s1 + (off - (uint64_t)lo1);
+      return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+    }
+    return le(off, 4);
+  }
   // generic address of bytes [off, off + n) (in a staged window when all
   // of them are there, else in global memory; the caller keeps them inside
   // the list)
@@ -489,6 +502,61 @@ __device__ __forceinline__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64
       ws.xv[line0 + ql] = (unsigned long long)vp;
       ws.xw[line0 + ql] = wb;
     }
+  }
+  return __all_sync(kFull, ok);
+}
+
+// The same for k = 32, where a tile is exactly one frame (32 rows of 32
+// ints): one header, its exception record at exc_at; the values go, as
+// 32-bit words, to xdst when there is room for all of them.
+__device__ __forceinline__ bool parse_pfd32(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows,
+                                            const RowSink<32>& out, WarpSmem<32>& ws, uint32_t line0,
+                                            uint32_t* xdst, uint32_t xroom, uint32_t* xtotal) {
+  const uint32_t lane = lane_id();
+  const uint64_t h = 4 * f0;
+  bool ok = h + 4 <= C.size;
+  const uint32_t hdr = ok ? C.le4(h) : 0u;
+  uint32_t b = hdr & 63u, wcode = (hdr >> 6) & 3u, e = hdr >> 8;
+  if (b > 32 || wcode > 2) {
+    ok = false;
+    b = 0;
+    wcode = 0;
+    e = 0;
+  }
+  const uint32_t lim = rows * 32;  // ints of the frame in this tile
+  if (e > lim) {
+    ok = false;
+    e = 0;
+  }
+  const uint32_t wb = 1u << wcode;
+  if (e && exc_at + (uint64_t)e * (2 + wb) > C.size) {
+    ok = false;
+    e = 0;
+  }
+  const bool expand = xdst != nullptr && e <= xroom;
+  *xtotal = expand ? e : 0xffffffffu;
+  if (lane < rows) out.put(lane, lane * b, b, ok);
+  // the record: e 16-bit positions, then e values of wb bytes
+  const uint8_t* rp = C.addr(exc_at, (uint64_t)e * (2 + wb));
+  const uint8_t* vp = rp + (size_t)e * 2;
+  for (uint32_t x = lane; x < e; x += 32) {
+    const uint32_t pos = (uint32_t)rp[2 * x] | ((uint32_t)rp[2 * x + 1] << 8);
+    if (pos >= lim) {
+      ok = false;
+      continue;
+    }
+    atomicOr(&ws.xm[line0 + (pos >> 5)], 1u << (pos & 31u));
+    if (expand) {
+      const uint8_t* q = vp + (size_t)x * wb;
+      uint32_t v = q[0];
+      if (wb > 1) v |= (uint32_t)q[1] << 8;
+      if (wb > 2) v |= ((uint32_t)q[2] << 16) | ((uint32_t)q[3] << 24);
+      xdst[x] = v;
+    }
+  }
+  if (lane < rows) {
+    ws.xv[line0 + lane] = (unsigned long long)vp;
+    ws.xw[line0 + lane] = wb;
   }
   return __all_sync(kFull, ok);
 }
@@ -951,7 +1019,7 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     } else {
       const uint32_t room = xfast && xfree0 + xused < (uint32_t)Geo<32>::TBW ? Geo<32>::TBW - xfree0 - xused : 0u;
       uint32_t ex = 0;
-      ok = parse_pfd<32>(C, w.tile, w.exc_at, rows, out, ws, line0, rows, ws.tb + xfree0 + xused, room, &ex);
+      ok = parse_pfd32(C, w.tile, w.exc_at, rows, out, ws, line0, ws.tb + xfree0 + xused, room, &ex);
       if (lane == 0) ws.ixb[__popc(live & ((1u << p) - 1u))] = xfree0 + xused;
       if (ex == 0xffffffffu) xfast = false;
       else xused += ex;
