@@ -1272,11 +1272,21 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
     // (and, k = 32, their vectors the re-lay buffer); one scan of both
     const uint32_t staged = s_issued - s_done;
     const uint32_t fp = (s_done + lane) % kFly;
-    const uint32_t lv = lane < staged ? ws.flines[fp] | (uint32_t)ws.fvecs[fp] << 16 : 0u;
-    const uint32_t lvi = warp_incl_sum(lv);
-    const uint32_t np = __popc(__ballot_sync(
-        kFull, lane < staged && (lvi & 0xffffu) <= 32u && (K != 32 || (lvi >> 16) <= (uint32_t)kPadVec)));
-    const uint32_t nl = __shfl_sync(kFull, lvi & 0xffffu, np - 1);
+    const uint32_t lv0 = ws.flines[s_done % kFly] | (uint32_t)ws.fvecs[s_done % kFly] << 16;
+    uint32_t lv, lvi, np, nl;
+    if ((lv0 & 0xffffu) == 32u) {
+      // a whole tile is a pack by itself
+      lv = lane == 0 ? lv0 : 0u;
+      lvi = lv0;
+      np = 1;
+      nl = 32;
+    } else {
+      lv = lane < staged ? ws.flines[fp] | (uint32_t)ws.fvecs[fp] << 16 : 0u;
+      lvi = warp_incl_sum(lv);
+      np = __popc(__ballot_sync(
+          kFull, lane < staged && (lvi & 0xffffu) <= 32u && (K != 32 || (lvi >> 16) <= (uint32_t)kPadVec)));
+      nl = __shfl_sync(kFull, lvi & 0xffffu, np - 1);
+    }
     // wait for their copies
     for (uint32_t p = 0; p < np && !failed; ++p) {
       const uint32_t s = s_done + p;
