@@ -210,7 +210,10 @@ gc_status gc_encode(const gc_codec* codec, const uint32_t* d_gaps, uint64_t n, u
                     uint64_t* d_sizes, void* d_scratch, uint64_t scratch_bytes, void* stream);
 
 /* Encode many lists at once (an index). h_n[i] ints of list i start at
- * h_in_off[i] of d_gaps. The library lays the lists out back to back and
+ * h_in_off[i] of d_gaps; the caller guarantees h_in_off[i] + h_n[i] <= the
+ * length of d_gaps (the library does not know it and reads those ranges as
+ * given). h_in_off[i] is also list i's output offset (gc_list.out_off).
+ * The library lays the lists' encodings out back to back and
  * writes, on the device: d_lists (one gc_list per list), d_ctrl, d_data,
  * d_tiles (tile records of tiles >= 1, with bases), and d_totals = (control
  * bytes, data words, tile records). Capacities are checked on the host from the

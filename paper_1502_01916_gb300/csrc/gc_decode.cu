@@ -897,6 +897,28 @@ __device__ __noinline__ uint32_t exc_value(const uint8_t* p, uint32_t wb) {
   return x;
 }
 
+// A Group-PFD line whose exception values could not be staged: the values
+// are read in place (xwb bytes each at xp, in column order). It runs rarely,
+// so it stays out of line, with its results in memory, and keeps the hot
+// line loop small.
+template <bool RESTORE>
+__device__ __noinline__ uint32_t extract_line_generic(const uint32_t* P, uint32_t sh, uint32_t msk, bool cross,
+                                                      uint32_t xm, const uint8_t* xp, uint32_t xwb, uint32_t* r) {
+  uint32_t R = 0;
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t lo = P[j];
+    const uint32_t hi = cross ? P[kPad + j] : 0u;
+    uint32_t v = __funnelshift_r(lo, hi, sh) & msk;
+    if ((xm >> j) & 1u) {
+      v = exc_value(xp, xwb);
+      xp += xwb;
+    }
+    R += v;
+    r[j] = RESTORE ? R : v;
+  }
+  return R;
+}
+
 // One line (32 ints) of the k = 32 decoder in natural column order: word
 // (P[j], P[33 + j]) >> shift & mask, Group-PFD exceptions over their slots
 // (XMODE 0: none in the pack; 1: values staged as 32-bit words at X, in
@@ -1050,15 +1072,20 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   }
   uint32_t r[32];
   uint32_t R = 0;
-  if (KIND != GC_PFD || !__any_sync(kFull, xm != 0)) {
+  if (KIND != GC_PFD) {
     extract_line<KIND, RESTORE, 0>(P, sh, msk, cross, 0u, nullptr, nullptr, 1u, r, R);
   } else if (xfast) {
+    // (lines without exceptions take the same loop)
     const uint32_t* X = ws.tb + (act ? ws.ixb[rank] : 0u) + xfirst;
     extract_line<KIND, RESTORE, 1>(P, sh, msk, cross, xm, X, nullptr, 1u, r, R);
   } else {
     const uint32_t xwb = xm ? ws.xw[lane] : 1u;
     const uint8_t* xp = xm ? reinterpret_cast<const uint8_t*>(ws.xv[lane]) + (size_t)xfirst * xwb : nullptr;
-    extract_line<KIND, RESTORE, 2>(P, sh, msk, cross, xm, nullptr, xp, xwb, r, R);
+    uint32_t rm[32];
+    const uint32_t Rm = extract_line_generic<RESTORE>(P, sh, msk, cross, xm, xp, xwb, rm);
+    R = RESTORE ? Rm : 0u;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) r[j] = rm[j];
   }
 
   // 3. docIDs: segmented scan of line totals, then each item's base
@@ -1097,37 +1124,48 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     k0 = E + (act ? ws.ibase[rank] : 0u);
   }
 
-  // the re-laid data is read: its buffer takes the results, line l at word
-  // 33 l (no two lanes share a bank)
+  // the re-laid data is read: its buffer takes the results, line l at words
+  // 32 l .. 32 l + 31 with its 16-byte chunk c at chunk c ^ (l & 7), so that
+  // the eight lanes of each quarter-warp touch eight different chunks both
+  // here (a line per lane) and when reading (a chunk per lane, below)
   __syncwarp();
   if (act) {
-    uint32_t* T = ws.tb + lane * kPad;
+    uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
+    const uint32_t sw = lane & 7u;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) T[j] = r[j] + k0;
+    for (int c = 0; c < 8; ++c)
+      T[c ^ sw] = make_uint4(r[4 * c] + k0, r[4 * c + 1] + k0, r[4 * c + 2] + k0, r[4 * c + 3] + k0);
     ws.lout[lane] = ws.iout[rank] + 32ull * (lane - lhead);
     const uint32_t left = ws.inint[rank] - 32u * (lane - lhead);
     ws.lnv[lane] = left < 32u ? left : 32u;
   }
   __syncwarp();
 
-  // 4. 128-byte stores, line by line
+  // 4. stores. Word j of line l sits at word 32 l + 4 ((j / 4) ^ (l & 7)) + j % 4.
+  const uint32_t wsw = 4u * (lane >> 2), wlo = lane & 3u;
   if (heads == 1u) {
     // one tile: its lines are consecutive in the output
-    uint32_t* o = a.out_pool + ws.iout[0] + lane;
+    uint32_t* o = a.out_pool + ws.iout[0];
     const uint32_t n = ws.inint[0];
-    if (n == (uint32_t)kTileInts) {
+    if (n == (uint32_t)kTileInts && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+      // 16-byte stores: lane j takes chunk j % 8 of lines 4 q + j / 8
+      const uint32_t c = lane & 7u;
 #pragma unroll
-      for (int rr = 0; rr < 32; ++rr) o[rr * 32] = ws.tb[rr * kPad + lane];
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t rr = 4u * q + (lane >> 3);
+        const uint4 v = reinterpret_cast<const uint4*>(ws.tb + rr * 32)[c ^ (rr & 7u)];
+        reinterpret_cast<uint4*>(o + rr * 32)[c] = v;
+      }
     } else {
 #pragma unroll
       for (int rr = 0; rr < 32; ++rr)
-        if ((uint32_t)rr * 32u + lane < n) o[rr * 32] = ws.tb[rr * kPad + lane];
+        if ((uint32_t)rr * 32u + lane < n) o[rr * 32 + lane] = ws.tb[rr * 32 + (wsw ^ (4u * (rr & 7))) + wlo];
     }
   } else {
     for (uint32_t ln = 0; ln < nl; ++ln) {
       const uint64_t ob = ws.lout[ln];
       const uint32_t n = ws.lnv[ln];
-      const uint32_t v = ws.tb[ln * kPad + lane];
+      const uint32_t v = ws.tb[ln * 32 + (wsw ^ (4u * (ln & 7u))) + wlo];
       if (lane < n) a.out_pool[ob + lane] = v;
     }
   }

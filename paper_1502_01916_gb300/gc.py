@@ -475,8 +475,11 @@ class Index:
 
 
 def encode_index(codec: gc_codec, d_gaps: torch.Tensor, lengths, out_offsets=None, stream=None) -> Index:
-    """Encode every list of `d_gaps` (lists back to back, `lengths` ints each)
-    in one gc_encode_batch call."""
+    """Encode every list of `d_gaps` in one gc_encode_batch call. List i's
+    `lengths[i]` gaps start at `out_offsets[i]` of `d_gaps` (default: back to
+    back), and its docIDs decode to the same offsets of the output: padding
+    between lists in `d_gaps` places each list's output, e.g. at 16-byte
+    boundaries."""
     dev = d_gaps.device
     h_n = np.ascontiguousarray(lengths, dtype=np.uint32)
     if out_offsets is None:
@@ -484,6 +487,11 @@ def encode_index(codec: gc_codec, d_gaps: torch.Tensor, lengths, out_offsets=Non
         if len(h_n) > 1:
             np.cumsum(h_n[:-1], dtype=np.uint64, out=out_offsets[1:])
     out_offsets = np.ascontiguousarray(out_offsets, dtype=np.uint64)
+    if out_offsets.shape != h_n.shape:
+        raise ValueError("out_offsets needs one offset per list")
+    # the library cannot see the length of d_gaps: check every list lies in it
+    if len(h_n) and int((out_offsets + h_n.astype(np.uint64)).max()) > d_gaps.numel():
+        raise ValueError("a list runs past the end of d_gaps")
     tr = TILE_INTS // codec.k
     rows = (h_n.astype(np.uint64) + codec.k - 1) // codec.k
     nt = (rows + tr - 1) // tr

@@ -118,3 +118,15 @@ def test_scratch_sizes(gc):
     lens = np.array([0, 1, 5000, 70000], np.uint32)
     assert gc.gc_encode_batch_scratch_size(c, lens) > 0
     assert gc.gc_version().startswith("gc ")
+
+
+def test_encode_index_rejects_lists_past_the_gaps(gc):
+    """List offsets are also where the encoder reads each list's gaps; a list
+    that would run past the gaps buffer is refused before any device call."""
+    import torch
+    c = gc.make_codec(gc.SIMPLE, 32)
+    gaps = torch.zeros(100, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        gc.encode_index(c, gaps, [40, 40], out_offsets=np.array([0, 64], np.uint64))
+    with pytest.raises(ValueError):
+        gc.encode_index(c, gaps, [40, 40], out_offsets=np.array([0], np.uint64))

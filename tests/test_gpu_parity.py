@@ -205,6 +205,61 @@ def test_batch_encode_decode(gc, c):
     assert (gc.as_u32(out)[:len(gaps)] == gaps).all()
 
 
+@pytest.mark.parametrize("n", [1024, 5000, 33007])
+def test_pfd_exceptions_beyond_the_staging_room(gc, n):
+    """Group-PFD at k = 32 with wide slots (b = 28) and every fourth row an
+    exception row (8 of 32, under zeta = 0.3's limit of 9): a tile's 256
+    exception values outnumber the 165 free words of the re-lay buffer, so
+    the decoder reads them in place."""
+    rng = np.random.default_rng(n)
+    g = rng.integers(1 << 27, 1 << 28, size=n, dtype=np.uint64)
+    wide = (np.arange(n) // 32) % 4 == 0
+    g[wide] = rng.integers(1 << 30, 1 << 31, size=int(wide.sum()), dtype=np.uint64)
+    g = g.astype(np.uint32)
+    oc, gcc = pair(gc, (O.PFD, 32, 0, 0, 0.3))
+    ctrl, data = O.encode(oc, g)
+    assert (O.decode(oc, ctrl, data, n) == g).all()
+    tiles = O.tile_index(oc, ctrl, n, g)
+    d_data = upload_u32(data)
+    enc = gc.EncodedList(gcc, n, upload_u8(ctrl), d_data[:len(data)], upload_u8(tiles.view(np.uint8)))
+    for use_tiles in (True, False):
+        for restore in (True, False):
+            out = gc.decode(enc, restore_docids=restore, use_tiles=use_tiles)
+            want = O.prefix_sum(g) if restore else g
+            assert (gc.as_u32(out)[:n] == want).all(), (use_tiles, restore)
+
+
+@pytest.mark.parametrize("kind", [O.SIMPLE, O.PFD, O.AFOR])
+@pytest.mark.parametrize("k", [4, 32])
+def test_batch_aligned_outputs(gc, kind, k):
+    """Lists whose outputs start at 16-byte boundaries (gaps laid out with
+    padding, output at the same offsets): whole tiles take 16-byte stores.
+    Every list equals the oracle's docIDs and the padding stays untouched."""
+    oc, gcc = pair(gc, (kind, k, 0, 0, 0.1))
+    lens, gaps, off = small_index(23 + k)
+    L = lens.astype(np.uint64)
+    span = (L + 3) // 4 * 4 + 4 * (np.arange(len(L)) % 3 == 0)  # some gaps wider than the rounding
+    outs = np.zeros(len(L), np.uint64)
+    np.cumsum(span[:-1], out=outs[1:])
+    total = int(outs[-1] + L[-1])
+    padded = np.full(total, 0xDEADBEEF, np.uint32)
+    for i in range(len(L)):
+        padded[int(outs[i]):int(outs[i]) + int(L[i])] = gaps[off[i]:off[i + 1]]
+    idx = gc.encode_index(gcc, upload_u32(padded), lens, out_offsets=outs)
+    for restore in (True, False):
+        out = torch.full((total,), -7, dtype=torch.int32, device="cuda")
+        gc.decode_index(idx, out=out, restore_docids=restore)
+        got = gc.as_u32(out)
+        hole = np.ones(total, bool)
+        for i in range(len(L)):
+            a, n = int(outs[i]), int(L[i])
+            g = gaps[off[i]:off[i + 1]]
+            want = O.prefix_sum(g) if restore else g
+            assert (got[a:a + n] == want).all(), (i, n, restore)
+            hole[a:a + n] = False
+        assert (got[hole] == np.uint32(0xFFFFFFF9)).all()
+
+
 @pytest.mark.parametrize("warps,bps,claim", [(1, 1, 1), (4, 2, 2), (8, 0, 0), (16, 0, 7), (2, 1, 16)])
 @pytest.mark.parametrize("k", [4, 32])
 def test_batch_launch_shapes(gc, warps, bps, claim, k):
