@@ -5,7 +5,8 @@ Workload (default): a synthetic inverted index of 1,000,000 posting lists
 over a 25M-document universe, rank-law (Zipf s = 1.1) lengths clipped to
 [1, 2^22] (1.5e9 docIDs), each list a sorted uniform sample. The index is
 encoded on the GPU with Group-Simple and Group-PFD (zeta = 0.1), both with
-the k = 32 vertical layout. One step decodes the whole index once per codec
+the k = 32 vertical layout. Each list's docIDs go to a 16-byte aligned
+offset of the output (at most 3 ints of padding per list). One step decodes the whole index once per codec
 and restores docIDs (fused prefix sum): one CUDA-graph launch per codec.
 
 Prints one JSON line: decoded ints/s (all codecs, all ranks), the roofline of
@@ -76,8 +77,11 @@ def kernel_hash() -> str:
 
 
 def workload(nlists: int, zipf_c: float = 0.0):
+    """(gaps, starts, lengths): list i is gaps[starts[i]:starts[i] + lengths[i]],
+    every start a multiple of 4 ints, zeros between lists; starts[-1] is the
+    layout's length."""
     import synth
-    gaps, off, lengths = synth.zipf_index(nlists, UNIVERSE, 0, C=zipf_c or synth.ZIPF_C)
+    gaps, off, lengths = synth.zipf_index(nlists, UNIVERSE, 0, C=zipf_c or synth.ZIPF_C, align=4)
     return gaps, off, lengths
 
 
@@ -224,21 +228,22 @@ def main():
     t0 = time.time()
     gaps, off, lengths = workload(a.nlists, a.zipf_c)
     t_gen = time.time() - t0
-    total_ints = int(off[-1])
+    total_ints = int(lengths.sum(dtype=np.uint64))  # decoded ints
+    out_len = int(off[-1])                            # output ints, padding included
     d_gaps = torch.from_numpy(gaps.view(np.int32)).to(dev)
     kinds = [c for c in a.codecs.split(",")]
     idxs = {}
     t0 = time.time()
     for name in kinds:
         codec = gc.make_codec(CODECS[name][0], a.k, zeta=a.zeta)
-        idxs[name] = gc.encode_index(codec, d_gaps, lengths)
+        idxs[name] = gc.encode_index(codec, d_gaps, lengths, out_offsets=off[:-1])
     plans = {n: gc.plan_index(idx) for n, idx in idxs.items()}
     torch.cuda.synchronize()
     t_enc = time.time() - t0
     del d_gaps
     torch.cuda.empty_cache()
 
-    out = torch.empty(total_ints, dtype=torch.int32, device=dev)
+    out = torch.empty(out_len, dtype=torch.int32, device=dev)
     scratch = {n: torch.empty(gc.gc_decode_plan_scratch_size(i.max_tiles), dtype=torch.uint8, device=dev)
                for n, i in idxs.items()}
     status = {n: gc.new_status(dev) for n in idxs}
@@ -257,20 +262,28 @@ def main():
                                   launches_cfg[n].items_per_claim], "ms": info["ms"]}
 
     # correctness at full size: every docID against the host's prefix sums
+    # (the zeros between lists leave the running sum unchanged), and the
+    # padding between lists untouched
     verified = None
     if not a.no_verify:
         cs = np.cumsum(gaps, dtype=np.uint32)
         base = np.where(off[:-1] > 0, cs[np.maximum(off[:-1].astype(np.int64) - 1, 0)], 0).astype(np.uint32)
-        want = cs - np.repeat(base, lengths.astype(np.int64))
+        want = cs - np.repeat(base, np.diff(off).astype(np.int64))
         del cs
+        npad = (off[1:] - off[:-1] - lengths).astype(np.int64)
+        first = (off[:-1] + lengths).astype(np.int64)
+        pad = np.repeat(first - (np.cumsum(npad) - npad), npad) + np.arange(int(npad.sum()), dtype=np.int64)
+        sentinel = np.uint32(0x9E3779B9)
+        want[pad] = sentinel
         verified = True
         for n, idx in idxs.items():
+            out.fill_(int(sentinel.view(np.int32)))
             gc.decode_index(idx, out=out, scratch=scratch[n], status=status[n], launch=launches_cfg[n],
                             plan=plans[n])
             if not np.array_equal(gc.as_u32(out), want):
                 verified = False
                 print(f"VERIFY FAILED for {n}", file=sys.stderr)
-        del want
+        del want, pad
         if not verified:
             raise SystemExit("decoded docIDs differ from the input's prefix sums")
 
@@ -368,8 +381,8 @@ def main():
                 h.copy_(p)
                 h2d += p.numel() * p.element_size()
             host[n] = (hp, pools)
-        h_out = torch.empty(total_ints, dtype=torch.int32, pin_memory=True)
-        d2h = 4 * total_ints * len(idxs)
+        h_out = torch.empty(out_len, dtype=torch.int32, pin_memory=True)
+        d2h = 4 * out_len * len(idxs)
 
         def e2e_step():
             for n in idxs:
@@ -426,6 +439,7 @@ def main():
         "config": {"workload": workload_name(a), "nlists": a.nlists, "ints": total_ints,
                    "codecs": [CODECS[n][1] + (f" zeta={a.zeta}" if n == "pfd" else "") for n in idxs],
                    "k": a.k, "l2": "inputs and outputs larger than L2 (no flush)",
+                   "output": f"each list at a 16-byte aligned offset ({out_len - total_ints} padding ints)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "launch": ({n: {"warps_per_block": l.warps_per_block, "blocks_per_sm": l.blocks_per_sm or "max",
                                    "items_per_claim": l.items_per_claim} if l is not None else "library default"

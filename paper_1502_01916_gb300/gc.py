@@ -466,6 +466,13 @@ class Index:
     def total_ints(self) -> int:
         return int(self.lengths.sum(dtype=np.uint64))
 
+    @property
+    def out_ints(self) -> int:
+        """Length of an output that holds every list at its offset."""
+        if not len(self.lengths):
+            return 0
+        return int((self.out_offsets + self.lengths.astype(np.uint64)).max())
+
     def compressed_bytes(self) -> int:
         return self.ctrl.numel() + 4 * self.data.numel()
 
@@ -550,8 +557,7 @@ def decode_index(index: Index, out: torch.Tensor | None = None, restore_docids: 
     """Decode every list of an index in one call: gc_decode_plan when a plan
     is given, else gc_decode_batch (which plans into its scratch)."""
     dev = index.data.device
-    total = index.total_ints
-    out = torch.empty(max(1, total), dtype=torch.int32, device=dev) if out is None else out
+    out = torch.empty(max(1, index.out_ints), dtype=torch.int32, device=dev) if out is None else out
     if scratch is None:
         size = (gc_decode_plan_scratch_size(index.max_tiles) if plan is not None
                 else gc_decode_batch_scratch_size(index.nlists, index.max_tiles))

@@ -77,7 +77,7 @@ def tune(index, plan=None, restore_docids: bool = True, candidates=None, reps: i
             w, b, c = hit["shape"]
             return _gc.gc_launch(w, b, c), {"key": key, "best_ms": hit["ms"], "ms": {}, "cached": True}
     plan = plan if plan is not None else _gc.plan_index(index)
-    out = torch.empty(max(1, index.total_ints), dtype=torch.int32, device=dev)
+    out = torch.empty(max(1, index.out_ints), dtype=torch.int32, device=dev)
     scratch = torch.empty(_gc.gc_decode_plan_scratch_size(index.max_tiles), dtype=torch.uint8, device=dev)
     st = _gc.new_status(dev)
     times = {}

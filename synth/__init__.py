@@ -136,18 +136,32 @@ def offsets_of(lengths: np.ndarray) -> np.ndarray:
     return off
 
 
+def padded_offsets(lengths: np.ndarray, align: int) -> np.ndarray:
+    """Starts of lists laid out back to back, each at a multiple of `align`
+    ints (len = nlists + 1; the last entry is the layout's length)."""
+    span = (np.asarray(lengths, dtype=np.uint64) + (align - 1)) // align * align
+    off = np.zeros(len(span) + 1, dtype=np.uint64)
+    np.cumsum(span, out=off[1:])
+    if len(span):
+        off[-1] = off[-2] + np.uint64(lengths[-1])
+    return off
+
+
 def uniform_index(seed: int, lengths: np.ndarray, universe: int, out: np.ndarray | None = None,
-                  threads: int | None = None):
+                  threads: int | None = None, align: int = 1):
     """Each list: sorted uniform sample without replacement from [0, universe), as d-gaps.
 
     Returns (gaps, offsets) with offsets[i] the start of list i (len = nlists + 1).
+    With align > 1 every list starts at a multiple of `align` ints and the ints
+    between lists are 0; list i is gaps[offsets[i]:offsets[i] + lengths[i]]
+    (its contents do not depend on the layout).
     ``out`` may be a preallocated uint32 array (for instance pinned host memory).
     """
     lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
-    off = offsets_of(lengths)
+    off = offsets_of(lengths) if align == 1 else padded_offsets(lengths, align)
     total = int(off[-1])
     if out is None:
-        out = np.empty(total, dtype=np.uint32)
+        out = np.empty(total, dtype=np.uint32) if align == 1 else np.zeros(total, dtype=np.uint32)
     assert out.size >= total
     if len(lengths):
         _load().synth_uniform_index(seed, len(lengths), _p32(lengths), _p64(off[:-1].copy()),
@@ -200,9 +214,9 @@ def zipf_index_lengths(nlists: int = 1_000_000, seed: int = 0, C: float = ZIPF_C
 
 
 def zipf_index(nlists: int = 1_000_000, universe: int = 25_000_000, seed: int = 0,
-               C: float = ZIPF_C, out: np.ndarray | None = None):
+               C: float = ZIPF_C, out: np.ndarray | None = None, align: int = 1):
     lengths = zipf_index_lengths(nlists, seed, C)
-    gaps, off = uniform_index(seed + 1, lengths, universe, out=out)
+    gaps, off = uniform_index(seed + 1, lengths, universe, out=out, align=align)
     return gaps, off, lengths
 
 
