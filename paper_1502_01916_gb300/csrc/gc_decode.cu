@@ -1141,32 +1141,42 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   }
   __syncwarp();
 
-  // 4. stores. Word j of line l sits at word 32 l + 4 ((j / 4) ^ (l & 7)) + j % 4.
-  const uint32_t wsw = 4u * (lane >> 2), wlo = lane & 3u;
-  if (heads == 1u) {
-    // one tile: its lines are consecutive in the output
-    uint32_t* o = a.out_pool + ws.iout[0];
-    const uint32_t n = ws.inint[0];
-    if (n == (uint32_t)kTileInts && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
-      // 16-byte stores: lane j takes chunk j % 8 of lines 4 q + j / 8
-      const uint32_t c = lane & 7u;
+  // 4. stores. Lane j takes chunk c = j % 8 of lines 4 q + j / 8 and stores
+  // it with one 16-byte store where the chunk is whole and its output
+  // 16-byte aligned, else word by word. A whole tile whose output is not
+  // aligned goes out line by line instead, lane j storing word j (word j of
+  // line l sits at word 32 l + 4 ((j / 4) ^ (l & 7)) + j % 4).
+  const uint32_t c = lane & 7u;
+  uint32_t* o1 = a.out_pool + ws.iout[0];
+  if (heads == 1u && ws.inint[0] == (uint32_t)kTileInts) {
+    if ((reinterpret_cast<uintptr_t>(o1) & 15u) == 0) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint32_t rr = 4u * q + (lane >> 3);
         const uint4 v = reinterpret_cast<const uint4*>(ws.tb + rr * 32)[c ^ (rr & 7u)];
-        reinterpret_cast<uint4*>(o + rr * 32)[c] = v;
+        reinterpret_cast<uint4*>(o1 + rr * 32)[c] = v;
       }
     } else {
+      const uint32_t wsw = 4u * (lane >> 2), wlo = lane & 3u;
 #pragma unroll
-      for (int rr = 0; rr < 32; ++rr)
-        if ((uint32_t)rr * 32u + lane < n) o[rr * 32 + lane] = ws.tb[rr * 32 + (wsw ^ (4u * (rr & 7))) + wlo];
+      for (int rr = 0; rr < 32; ++rr) o1[rr * 32 + lane] = ws.tb[rr * 32 + (wsw ^ (4u * (rr & 7))) + wlo];
     }
   } else {
-    for (uint32_t ln = 0; ln < nl; ++ln) {
-      const uint64_t ob = ws.lout[ln];
-      const uint32_t n = ws.lnv[ln];
-      const uint32_t v = ws.tb[ln * 32 + (wsw ^ (4u * (ln & 7u))) + wlo];
-      if (lane < n) a.out_pool[ob + lane] = v;
+    for (uint32_t q = 0; 4 * q < nl; ++q) {
+      const uint32_t ln = 4 * q + (lane >> 3);
+      if (ln < nl) {
+        const uint32_t n = ws.lnv[ln];
+        const uint4 v = reinterpret_cast<const uint4*>(ws.tb + ln * 32)[c ^ (ln & 7u)];
+        uint32_t* o = a.out_pool + ws.lout[ln] + 4 * c;
+        if (4 * c + 4 <= n && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+          *reinterpret_cast<uint4*>(o) = v;
+        } else {
+          if (4 * c < n) o[0] = v.x;
+          if (4 * c + 1 < n) o[1] = v.y;
+          if (4 * c + 2 < n) o[2] = v.z;
+          if (4 * c + 3 < n) o[3] = v.w;
+        }
+      }
     }
   }
   __syncwarp();
