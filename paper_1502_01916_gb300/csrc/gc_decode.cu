@@ -1007,10 +1007,21 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     const uint32_t at = ws.at[f];
     const uint32_t vecs = ws.fvecs[f];
     {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(ws.ring + at) + lane;
-      uint32_t* dst = ws.tb + v0 * kPad + lane;
-#pragma unroll 4
-      for (uint32_t v = 0; v < vecs; ++v) dst[v * kPad] = src[v * 32];
+      // lane l moves 16-byte chunk l % 8 of vectors 4 i + l / 8: one 16-byte
+      // load, and four stores that hit 32 different banks across the warp
+      const uint32_t q = lane >> 3;
+      const uint4* src = reinterpret_cast<const uint4*>(ws.ring + at) + lane;
+      uint32_t* dst = ws.tb + (v0 + q) * kPad + 4 * (lane & 7u);
+      for (uint32_t i = 0; 4 * i < vecs; ++i) {
+        if (4 * i + q < vecs) {
+          const uint4 x = src[i * 32];
+          uint32_t* d = dst + i * 4 * kPad;
+          d[0] = x.x;
+          d[1] = x.y;
+          d[2] = x.z;
+          d[3] = x.w;
+        }
+      }
     }
     const uint32_t dbytes = vecs * 32 * 4;
     CtrlView C;
@@ -1268,18 +1279,49 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
         s_claimed += cnt;
       }
     }
-    // stage claimed tiles while the ring and the mbarriers allow: lane p
-    // takes record s_issued + p. A tile never wraps: it starts at offset 0
-    // when it would run past the end, and the bytes skipped there are held
-    // until it is decoded. Every offset follows from one scan of the tiles'
-    // sizes; the tiles that fit are a prefix of the candidates (none when
-    // the first does not fit, the usual case while the ring is full).
+    // stage claimed tiles while the ring and the mbarriers allow. A tile
+    // never wraps: it starts at offset 0 when it would run past the end, and
+    // the bytes skipped there are held until it is decoded. When only the
+    // first candidate fits (whole tiles, mostly) it is placed directly;
+    // when more fit, lane p takes record s_issued + p and every offset
+    // follows from one scan of the sizes (the tiles that fit are a prefix of
+    // the candidates); when none fits (the ring is full) nothing happens.
     if (s_issued < s_claimed && s_issued - s_done < (uint32_t)kFly) {
       const uint32_t r0 = used ? rpos : 0u;  // empty: restart at offset 0
-      const uint32_t need0 = ws.need[s_issued % kFly];
-      const uint32_t pad0 = r0 + need0 > (uint32_t)kRing ? kRing - r0 : 0u;
-      if (used + pad0 + need0 <= (uint32_t)kRing) {
-        const uint32_t cands = min(s_claimed - s_issued, (uint32_t)kFly - (s_issued - s_done));
+      const uint32_t f0 = s_issued % kFly;
+      const uint32_t need0 = ws.need[f0];
+      const bool wrap0 = r0 + need0 > (uint32_t)kRing;  // (the pad is 0 when r0 is the ring's end)
+      const uint32_t pad0 = wrap0 ? kRing - r0 : 0u;
+      const uint32_t off0 = wrap0 ? 0u : r0;
+      const uint32_t cands = min(s_claimed - s_issued, (uint32_t)kFly - (s_issued - s_done));
+      // does a second candidate fit after the first?
+      bool more2 = false;
+      if (cands > 1) {
+        const uint32_t r1 = off0 + need0;
+        const uint32_t need1 = ws.need[(s_issued + 1) % kFly];
+        const uint32_t pad1 = r1 + need1 > (uint32_t)kRing ? kRing - r1 : 0u;
+        more2 = used + pad0 + need0 + pad1 + need1 <= (uint32_t)kRing;
+      }
+      if (used + pad0 + need0 <= (uint32_t)kRing && !more2) {
+        // the first only (the usual case for whole tiles): no scan
+        const uint32_t off = off0;
+        if (lane == 0) {
+          const gc_work& w = rec_at(ws.rec, s_issued);
+          const uint32_t dbytes = ws.fvecs[f0] * (K * 4u), cb = ws.cst[f0], xb = ws.xst[f0];
+          ws.at[f0] = off;
+          ws.end[f0] = need0 + pad0;
+          mbar_expect_tx(&ws.mbar[f0], dbytes + cb + xb);
+          if (dbytes) bulk_g2s(ws.ring + off, a.data_pool + w.data_at, dbytes, &ws.mbar[f0]);
+          if (cb) bulk_g2s(ws.ring + off + dbytes, a.ctrl_pool + (w.ctrl_at + w.win_at), cb, &ws.mbar[f0]);
+          if (xb)
+            bulk_g2s(ws.ring + off + dbytes + cb, a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull), xb,
+                     &ws.mbar[f0]);
+        }
+        rpos = off + need0;
+        used += pad0 + need0;
+        __syncwarp();
+        s_issued += 1;
+      } else if (more2) {
         const uint32_t s = s_issued + lane;
         const uint32_t f = s % kFly;
         const bool cand = lane < cands;
