@@ -167,7 +167,7 @@ enum {
  * memory holds, about 15 KB a warp); blocks_per_sm: resident blocks per SM
  * to launch (0 = as many as fit); the persistent grid is blocks_per_sm *
  * SMs. items_per_claim: 1..16 tiles a warp takes from the shared counter
- * per atomic (0 = default 8). A plan with tiles that take their prefix by
+ * per atomic (0 = default 16). A plan with tiles that take their prefix by
  * look-back is claimed one tile at a time whatever this says, so that the
  * tiles a warp holds never delay the tiles after them for long. */
 typedef struct gc_launch {

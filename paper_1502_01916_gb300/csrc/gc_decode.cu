@@ -1105,34 +1105,41 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     // (a plain scan, less the scan before the item's first line)
     const uint32_t T = act ? R : 0u;
     const uint32_t V = warp_incl_sum(T);
-    const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
-    const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
-    const uint32_t E = v - T;
-    const uint32_t lastl = my_live ? my_line0 + my_lines - 1 : 0u;
-    const uint32_t tot = __shfl_sync(kFull, v, lastl);
-    const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
-    const bool needs_lb = my_live && my_tile > 0 && !has_base;
-    uint32_t base = has_base ? my_base : 0u;
-    if (a.lb) {
-      if (my_live && !needs_lb && (my_shape & GC_WORK_PUBLISH))
-        st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(base + tot));
-      if (my_dead) st_release(a.lb + my_item, kFlagPrefix);  // its error is reported
-      if (needs_lb) st_release(a.lb + my_item, kFlagAgg | tot);
-    }
-    for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
-      const uint32_t p = __ffs(pend) - 1;
-      const uint32_t it = __shfl_sync(kFull, my_item, p);
-      const uint32_t tl = __shfl_sync(kFull, my_tile, p);
-      const uint32_t lst = __shfl_sync(kFull, my_list, p);
-      const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
-      if (lane == p) {
-        base = ex;
-        if (a.lb) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(ex + tot));
+    const uint32_t shape0 = __shfl_sync(kFull, my_shape, 0);
+    if (np == 1 && heads == 1u && (shape0 & (GC_WORK_HAS_BASE | GC_WORK_PUBLISH)) == GC_WORK_HAS_BASE) {
+      // a pack of one live tile with its skip entry, which no other tile
+      // waits for
+      k0 = V - T + __shfl_sync(kFull, my_base, 0);
+    } else {
+      const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
+      const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
+      const uint32_t E = v - T;
+      const uint32_t lastl = my_live ? my_line0 + my_lines - 1 : 0u;
+      const uint32_t tot = __shfl_sync(kFull, v, lastl);
+      const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
+      const bool needs_lb = my_live && my_tile > 0 && !has_base;
+      uint32_t base = has_base ? my_base : 0u;
+      if (a.lb) {
+        if (my_live && !needs_lb && (my_shape & GC_WORK_PUBLISH))
+          st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(base + tot));
+        if (my_dead) st_release(a.lb + my_item, kFlagPrefix);  // its error is reported
+        if (needs_lb) st_release(a.lb + my_item, kFlagAgg | tot);
       }
+      for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
+        const uint32_t p = __ffs(pend) - 1;
+        const uint32_t it = __shfl_sync(kFull, my_item, p);
+        const uint32_t tl = __shfl_sync(kFull, my_tile, p);
+        const uint32_t lst = __shfl_sync(kFull, my_list, p);
+        const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
+        if (lane == p) {
+          base = ex;
+          if (a.lb) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(ex + tot));
+        }
+      }
+      if (my_live) ws.ibase[my_rank] = base;
+      __syncwarp();
+      k0 = E + (act ? ws.ibase[rank] : 0u);
     }
-    if (my_live) ws.ibase[my_rank] = base;
-    __syncwarp();
-    k0 = E + (act ? ws.ibase[rank] : 0u);
   }
 
   // the re-laid data is read: its buffer takes the results, line l at words
@@ -1615,7 +1622,7 @@ namespace {
 constexpr uint32_t kMaxWarps = 16;     // warps per block (launch bounds: 512 threads)
 constexpr uint32_t kDefaultWarps = 4;
 constexpr uint32_t kMaxClaim = kSeq;   // records per claim
-constexpr uint32_t kDefaultClaim = 8;
+constexpr uint32_t kDefaultClaim = 16;
 constexpr uint64_t kHdr = 256;         // scratch header: claim counter, record counts
 
 template <int KIND, int K, bool RESTORE>
