@@ -969,7 +969,7 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   const uint32_t my_vec0 = (lvi >> 16) - my_vecs;
   const bool my_live = my_lines > 0;
   const uint32_t live = __ballot_sync(kFull, my_live);
-  const uint32_t heads = __reduce_or_sync(kFull, my_live ? 1u << my_line0 : 0u);
+  const uint32_t heads = np == 1 ? (live & 1u) : __reduce_or_sync(kFull, my_live ? 1u << my_line0 : 0u);
   uint32_t my_item = 0, my_tile = 0, my_base = 0, my_shape = 0, my_list = 0xffffffffu;
   uint64_t my_out = 0;
   if (lane < np) {
@@ -999,9 +999,10 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   // its control patterns into one (word, shift, width) entry per row
   for (uint32_t lm = live; lm; lm &= lm - 1) {
     const uint32_t p = __ffs(lm) - 1;
-    const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
-    const uint32_t rows = __shfl_sync(kFull, my_lines, p);
-    const uint32_t v0 = __shfl_sync(kFull, my_vec0, p);
+    // (a pack of one: line 0, its nl lines, vector 0)
+    const uint32_t line0 = np == 1 ? 0u : __shfl_sync(kFull, my_line0, p);
+    const uint32_t rows = np == 1 ? nl : __shfl_sync(kFull, my_lines, p);
+    const uint32_t v0 = np == 1 ? 0u : __shfl_sync(kFull, my_vec0, p);
     const gc_work& w = rec_at(ws.rec, s0 + p);
     const uint32_t f = (s0 + p) % kFly;
     const uint32_t at = ws.at[f];
@@ -1147,15 +1148,18 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   // the eight lanes of each quarter-warp touch eight different chunks both
   // here (a line per lane) and when reading (a chunk per lane, below)
   __syncwarp();
+  const bool whole = heads == 1u && ws.inint[0] == (uint32_t)kTileInts;  // one whole tile
   if (act) {
     uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
     const uint32_t sw = lane & 7u;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
       T[c ^ sw] = make_uint4(r[4 * c] + k0, r[4 * c + 1] + k0, r[4 * c + 2] + k0, r[4 * c + 3] + k0);
-    ws.lout[lane] = ws.iout[rank] + 32ull * (lane - lhead);
-    const uint32_t left = ws.inint[rank] - 32u * (lane - lhead);
-    ws.lnv[lane] = left < 32u ? left : 32u;
+    if (!whole) {
+      ws.lout[lane] = ws.iout[rank] + 32ull * (lane - lhead);
+      const uint32_t left = ws.inint[rank] - 32u * (lane - lhead);
+      ws.lnv[lane] = left < 32u ? left : 32u;
+    }
   }
   __syncwarp();
 
@@ -1166,7 +1170,7 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   // line l sits at word 32 l + 4 ((j / 4) ^ (l & 7)) + j % 4).
   const uint32_t c = lane & 7u;
   uint32_t* o1 = a.out_pool + ws.iout[0];
-  if (heads == 1u && ws.inint[0] == (uint32_t)kTileInts) {
+  if (whole) {
     if ((reinterpret_cast<uintptr_t>(o1) & 15u) == 0) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -1404,7 +1408,7 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
     }
     if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, ws, s_done, np, nl, lane < np ? lv : 0u, lvi);
     else decode_pack<KIND, K, RESTORE>(a, ws, s_done, np, nl);
-    used -= __reduce_add_sync(kFull, lane < np ? ws.end[fp] : 0u);
+    used -= np == 1 ? ws.end[s_done % kFly] : __reduce_add_sync(kFull, lane < np ? ws.end[fp] : 0u);
     s_done += np;
   }
 }
