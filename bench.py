@@ -36,10 +36,9 @@ CODECS = {"simple": (0, "Group-Simple"), "pfd": (3, "Group-PFD")}
 # ncu capture (profiles/k_decode_zipf_index_dram.md), with the hash of the
 # kernel sources they were taken on; once the sources change, null.
 NCU_TRAFFIC = {
-    "simple": {"bytes": 2929310720 + 5942661632, "hash": "d0dd3f2f5321decc"},
-    "pfd": {"bytes": 2406914560 + 5939302400, "hash": "d0dd3f2f5321decc"},
+    "simple": {"bytes": 2954974720 + 5950713344, "hash": "67146018e4d11008"},
+    "pfd": {"bytes": 2432178944 + 5945080576, "hash": "67146018e4d11008"},
 }
-
 
 def parse():
     p = argparse.ArgumentParser()
