@@ -80,6 +80,7 @@ struct __align__(128) WarpSmem {
   unsigned long long iout[32];           // pack item (by rank among decoded ones): first output int
   uint32_t inint[32];                    // its ints
   uint32_t ibase[32];                    // its docID base
+  uint32_t irec[32];                     // its record slot | first re-laid vector << 8
   uint32_t ixb[32];                      // Group-PFD: its first exception value in the buffer's free tail
   uint32_t rw[Geo<K>::PROWS];            // row: ring word of its first word (lane 0)
   uint32_t rs[Geo<K>::PROWS];            // row: shift | width << 8
@@ -89,6 +90,10 @@ struct __align__(128) WarpSmem {
   unsigned long long lout[32];           // line: output index of its first int
   uint32_t lnv[32];                      // line: ints it holds
 };
+
+// k = 32: four blocks of four warps fit an SM's 228 KB (with 1 KB reserved
+// per block)
+static_assert(sizeof(WarpSmem<32>) * 4 + 1024 <= 233472 / 4, "per-warp shared memory outgrew 16 warps per SM");
 
 struct DecodeArgs {
   const gc_work* work;
@@ -951,6 +956,64 @@ __device__ __forceinline__ void extract_line(const uint32_t* P, uint32_t sh, uin
   }
 }
 
+// Group-Simple, k = 32: the rows of all of a pack's tiles at once. Line l of
+// the pack is row q = l - lhead of its tile, and lane l also reads its
+// tile's selector q (a tile of R rows needs at most R selectors: each
+// covers at least one of its rows, the first one too, since fewer than
+// its own rows lie in the tile before). One scan of the selectors' row
+// counts (less the scan before the tile's first lane) gives each
+// selector's first row; a line then takes the last of its tile's
+// selectors that starts at or before it. Returns the line's row entry in
+// registers (re-laid word of the row's first word, shift | width << 8) and
+// reports a tile whose selectors are malformed or do not cover its rows.
+__device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, WarpSmem<32>& ws, bool act, uint32_t lane,
+                                                    uint32_t heads, uint32_t nl, uint32_t rank, uint32_t lhead,
+                                                    uint32_t& ent, uint32_t& sw) {
+  // this line's tile (its record slot is also its staging slot)
+  const uint32_t im = act ? ws.irec[rank] : 0u;
+  const uint32_t f = im & 255u, v0 = im >> 8;
+  const gc_work& w = *reinterpret_cast<const gc_work*>(ws.rec[f]);
+  const uint32_t after = heads & ~(0xffffffffu >> (31u - lane));  // heads of later tiles
+  const uint32_t rows = (after ? __ffs(after) - 1 : nl) - lhead;
+  const uint32_t q = lane - lhead;
+  const uint32_t vecs = ws.fvecs[f];
+  CtrlView C;
+  C.g = a.ctrl_pool + w.ctrl_at;
+  C.size = w.ctrl_bytes;
+  C.s1 = ws.ring + ws.at[f] + vecs * 128u;
+  C.lo1 = w.win_at;
+  C.len1 = ws.cst[f];
+  C.s2 = nullptr;
+  C.lo2 = 0;
+  C.len2 = 0;
+  // selector q of the tile (Table III; 4 bits each, low nibble first)
+  const uint64_t u = (w.ctrl_bit >> 2) + q;
+  const uint32_t sel = act ? (C.byte(u >> 1, 0xffu) >> ((u & 1) * 4)) & 15u : 0u;
+  const bool bad = sel > 9;
+  const uint32_t num = !act ? 0u : bad ? 32u : sel_num(sel);
+  const uint32_t bw = bad ? 0u : sel_bw(sel);
+  const uint32_t V = warp_incl_sum(num);
+  const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
+  const int32_t start = (int32_t)(V - (lhead ? Vb : 0u) - num) - (int32_t)w_skip(w.shape);  // its first row
+  const bool valid = act && start < (int32_t)rows;
+  bool ok = !(valid && bad);
+  const uint32_t M = __reduce_or_sync(kFull, valid ? 1u << (lhead + (start > 0 ? (uint32_t)start : 0u)) : 0u);
+  // this line's selector: the k-th of its tile's (the valid ones are a prefix of the tile's lanes)
+  const uint32_t k = __popc(M & (0xffffffffu >> (31u - lane)) & ~((1u << lhead) - 1u));
+  const uint32_t us = (lhead + k - 1u) & 31u;
+  const int32_t st = __shfl_sync(kFull, start, us);
+  const uint32_t wu = __shfl_sync(kFull, bw, us);
+  const uint32_t nu = __shfl_sync(kFull, num, us);
+  const uint32_t b = w_bit0(w.shape) + 32u * (us - lhead) + (uint32_t)((int32_t)q - st) * wu;
+  // (a row past its selector's rows means the tile's skip entry and its
+  // selectors disagree)
+  const bool out_of_range = k == 0 || (uint32_t)((int32_t)q - st) >= nu || b + wu > 32u * vecs;
+  if (act && out_of_range) ok = false;
+  ent = act && !out_of_range ? v0 * kPad + (b >> 5) * kPad : v0 * kPad;
+  sw = act && !out_of_range ? (b & 31u) | (wu << 8) : 0u;
+  if (!ok) report(a.status, GC_ERR_CORRUPT, w.list);
+}
+
 // The k = 32 pack decoder. Each staged tile's data vectors are first re-laid
 // at 33 words per vector, so that the rows of a pack, one per lane, sit in
 // different banks whichever vectors they start in; lane l then reads line l
@@ -986,6 +1049,7 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   if (my_live) {
     ws.iout[my_rank] = my_out;
     ws.inint[my_rank] = w_nint(my_shape);
+    if (KIND == GC_SIMPLE) ws.irec[my_rank] = (s0 + lane) % kSeq | my_vec0 << 8;
   }
   if (KIND == GC_PFD) ws.xm[lane] = 0;
 
@@ -1041,9 +1105,9 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     out.stride = kPad;
     out.bit0 = w_bit0(w.shape);
     out.vec_bits = 32 * vecs;
-    bool ok;
+    bool ok = true;
     if (KIND == GC_SIMPLE) {
-      ok = parse_simple<32>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
+      // parsed below, all of the pack's tiles at once
     } else if (KIND == GC_SCHEME) {
       const uint64_t row0 = (uint64_t)w.tile * Geo<32>::TR;
       if (a.ld == GC_LD_BINARY) ok = parse_scheme_binary<32>(C, row0, rows, a.cg, out);
@@ -1067,8 +1131,13 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   const uint32_t upto = heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
   const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;  // its item among the decoded ones
   const uint32_t lhead = act ? 31u - __clz(upto) : 0u;          // the item's first line
-  const uint32_t ent = act ? ws.rw[lane] : 0u;
-  const uint32_t sw = act ? ws.rs[lane] : 0u;
+  uint32_t ent, sw;
+  if (KIND == GC_SIMPLE) {
+    parse_simple_pack32(a, ws, act, lane, heads, nl, rank, lhead, ent, sw);
+  } else {
+    ent = act ? ws.rw[lane] : 0u;
+    sw = act ? ws.rs[lane] : 0u;
+  }
   const uint32_t sh = sw & 31u, wd = sw >> 8;
   const uint32_t msk = low_mask(wd);
   const bool cross = sh + wd > 32;
