@@ -81,7 +81,6 @@ struct __align__(128) WarpSmem {
   uint32_t inint[32];                    // its ints
   uint32_t ibase[32];                    // its docID base
   uint32_t irec[32];                     // its record slot | first re-laid vector << 8
-  uint32_t ixb[32];                      // Group-PFD: its first exception value in the buffer's free tail
   uint32_t rw[Geo<K>::PROWS];            // row: ring word of its first word (lane 0)
   uint32_t rs[Geo<K>::PROWS];            // row: shift | width << 8
   uint32_t xm[32];                       // line: Group-PFD exception slots
@@ -507,61 +506,6 @@ __device__ __forceinline__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64
       ws.xv[line0 + ql] = (unsigned long long)vp;
       ws.xw[line0 + ql] = wb;
     }
-  }
-  return __all_sync(kFull, ok);
-}
-
-// The same for k = 32, where a tile is exactly one frame (32 rows of 32
-// ints): one header, its exception record at exc_at; the values go, as
-// 32-bit words, to xdst when there is room for all of them.
-__device__ __forceinline__ bool parse_pfd32(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows,
-                                            const RowSink<32>& out, WarpSmem<32>& ws, uint32_t line0,
-                                            uint32_t* xdst, uint32_t xroom, uint32_t* xtotal) {
-  const uint32_t lane = lane_id();
-  const uint64_t h = 4 * f0;
-  bool ok = h + 4 <= C.size;
-  const uint32_t hdr = ok ? C.le4(h) : 0u;
-  uint32_t b = hdr & 63u, wcode = (hdr >> 6) & 3u, e = hdr >> 8;
-  if (b > 32 || wcode > 2) {
-    ok = false;
-    b = 0;
-    wcode = 0;
-    e = 0;
-  }
-  const uint32_t lim = rows * 32;  // ints of the frame in this tile
-  if (e > lim) {
-    ok = false;
-    e = 0;
-  }
-  const uint32_t wb = 1u << wcode;
-  if (e && exc_at + (uint64_t)e * (2 + wb) > C.size) {
-    ok = false;
-    e = 0;
-  }
-  const bool expand = xdst != nullptr && e <= xroom;
-  *xtotal = expand ? e : 0xffffffffu;
-  if (lane < rows) out.put(lane, lane * b, b, ok);
-  // the record: e 16-bit positions, then e values of wb bytes
-  const uint8_t* rp = C.addr(exc_at, (uint64_t)e * (2 + wb));
-  const uint8_t* vp = rp + (size_t)e * 2;
-  for (uint32_t x = lane; x < e; x += 32) {
-    const uint32_t pos = (uint32_t)rp[2 * x] | ((uint32_t)rp[2 * x + 1] << 8);
-    if (pos >= lim) {
-      ok = false;
-      continue;
-    }
-    atomicOr(&ws.xm[line0 + (pos >> 5)], 1u << (pos & 31u));
-    if (expand) {
-      const uint8_t* q = vp + (size_t)x * wb;
-      uint32_t v = q[0];
-      if (wb > 1) v |= (uint32_t)q[1] << 8;
-      if (wb > 2) v |= ((uint32_t)q[2] << 16) | ((uint32_t)q[3] << 24);
-      xdst[x] = v;
-    }
-  }
-  if (lane < rows) {
-    ws.xv[line0 + lane] = (unsigned long long)vp;
-    ws.xw[line0 + lane] = wb;
   }
   return __all_sync(kFull, ok);
 }
@@ -1014,6 +958,120 @@ __device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, WarpSme
   if (!ok) report(a.status, GC_ERR_CORRUPT, w.list);
 }
 
+// Group-PFD: one tile's exceptions: every one sets its slot's bit in its
+// line's mask and, with `stage`, its value goes as a 32-bit word to the
+// re-lay buffer at word xb + its index (e 16-bit positions at rp, then e
+// values of wb bytes; the tile's first line is hl, its frame holds lim ints).
+__device__ __forceinline__ void pfd_exceptions(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t lane, uint32_t hl,
+                                               uint32_t e, uint32_t lim, uint32_t wb, const uint8_t* rp, uint32_t xb,
+                                               bool stage, uint32_t list) {
+  const uint8_t* vp = rp + (size_t)e * 2;
+  for (uint32_t x = lane; x < e; x += 32) {
+    const uint32_t pos = (uint32_t)rp[2 * x] | ((uint32_t)rp[2 * x + 1] << 8);
+    if (pos >= lim) {
+      report(a.status, GC_ERR_CORRUPT, list);
+      continue;
+    }
+    atomicOr(&ws.xm[hl + (pos >> 5)], 1u << (pos & 31u));
+    if (stage) {
+      const uint8_t* v8 = vp + (size_t)x * wb;
+      uint32_t v = v8[0];
+      if (wb > 1) v |= (uint32_t)v8[1] << 8;
+      if (wb > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
+      ws.tb[xb + x] = v;
+    }
+  }
+}
+
+// Group-PFD, k = 32: the headers, rows and exceptions of all of a pack's
+// tiles at once (a tile is one frame, Sec 6). Line l is row q = l - lhead
+// of its tile: every line reads its tile's header (b, exception width code,
+// exception count e) and takes row q at q * b bits (lanes past the pack's
+// lines read the first tile's). The pack's exception values go, as 32-bit
+// words and tile after tile, to the re-lay buffer from word xfree0 on when
+// all of them fit (xfast), else the lines read them in place (xv, xw);
+// every exception sets its slot's bit in its line's mask (xm, zeroed
+// beforehand). Returns the line's row entry in registers and the buffer
+// word of its tile's first exception value (xbase); reports a tile whose
+// header, row widths or exception record are malformed.
+__device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, WarpSmem<32>& ws, bool act, uint32_t lane,
+                                                 uint32_t heads, uint32_t nl, uint32_t rank, uint32_t lhead,
+                                                 uint32_t xfree0, uint32_t& ent, uint32_t& sw, uint32_t& xbase,
+                                                 bool& xfast) {
+  // this line's tile (its record slot is also its staging slot)
+  const uint32_t im = heads ? ws.irec[rank] : 0u;
+  const uint32_t f = im % kSeq, v0 = im >> 8;
+  const gc_work& w = *reinterpret_cast<const gc_work*>(ws.rec[f]);
+  const uint32_t after = heads & ~(0xffffffffu >> (31u - lane));  // heads of later tiles
+  const uint32_t rows = (after ? __ffs(after) - 1 : nl) - lhead;
+  const uint32_t q = lane - lhead;
+  const uint32_t vecs = ws.fvecs[f];
+  CtrlView C;
+  C.g = a.ctrl_pool + w.ctrl_at;
+  C.size = w.ctrl_bytes;
+  C.s1 = ws.ring + ws.at[f] + vecs * 128u;
+  C.lo1 = w.win_at;
+  C.len1 = ws.cst[f];
+  C.s2 = C.s1 + ws.cst[f];
+  C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
+  C.len2 = ws.xst[f];
+  // the header
+  const uint64_t h = 4ull * w.tile;
+  bool ok = h + 4 <= C.size;
+  const uint32_t hdr = heads && ok ? C.le4(h) : 0u;
+  uint32_t b = hdr & 63u, wcode = (hdr >> 6) & 3u, e = hdr >> 8;
+  if (b > 32 || wcode > 2) {
+    ok = false;
+    b = 0;
+    wcode = 0;
+    e = 0;
+  }
+  const uint32_t lim = rows * 32;  // ints of the frame in this tile
+  if (e > lim) {
+    ok = false;
+    e = 0;
+  }
+  const uint32_t wb = 1u << wcode;
+  if (e && w.exc_at + (uint64_t)e * (2 + wb) > C.size) {
+    ok = false;
+    e = 0;
+  }
+  // this line's row
+  const uint32_t rb = w_bit0(w.shape) + q * b;
+  const bool oor = rb + b > 32u * vecs;
+  if (oor) ok = false;
+  ent = !act ? 0u : oor ? v0 * kPad : v0 * kPad + (rb >> 5) * kPad;
+  sw = act && !oor ? (rb & 31u) | (b << 8) : 0u;
+  if (act && !ok) report(a.status, GC_ERR_CORRUPT, w.list);
+  // the record: e 16-bit positions, then e values of wb bytes
+  const uint8_t* rp = C.addr(w.exc_at, (uint64_t)e * (2 + wb));
+  if (heads == 1u) {
+    // one tile: every lane holds its facts
+    xbase = xfree0;
+    xfast = xfree0 + e <= (uint32_t)Geo<32>::TBW;
+    pfd_exceptions(a, ws, lane, 0, e, lim, wb, rp, xbase, xfast, w.list);
+  } else {
+    // the tiles' values one after another; then tile by tile
+    const uint32_t E = warp_incl_sum(act && lane == lhead ? e : 0u);
+    xfast = xfree0 + __shfl_sync(kFull, E, 31) <= (uint32_t)Geo<32>::TBW;
+    xbase = xfree0 + E - (act ? e : 0u);
+    for (uint32_t hm = heads; hm; hm &= hm - 1) {
+      const uint32_t hl = __ffs(hm) - 1;  // the tile's first line
+      const uint32_t ef = __shfl_sync(kFull, e, hl);
+      const uint32_t limf = __shfl_sync(kFull, lim, hl);
+      const uint32_t wbf = __shfl_sync(kFull, wb, hl);
+      const uint32_t xb = __shfl_sync(kFull, xbase, hl);
+      const uint32_t lf = __shfl_sync(kFull, w.list, hl);
+      const uint8_t* rpf = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, (unsigned long long)rp, hl));
+      pfd_exceptions(a, ws, lane, hl, ef, limf, wbf, rpf, xb, xfast, lf);
+    }
+  }
+  if (!xfast && act) {
+    ws.xv[lane] = (unsigned long long)(rp + (size_t)e * 2);
+    ws.xw[lane] = wb;
+  }
+}
+
 // The k = 32 pack decoder. Each staged tile's data vectors are first re-laid
 // at 33 words per vector, so that the rows of a pack, one per lane, sit in
 // different banks whichever vectors they start in; lane l then reads line l
@@ -1049,15 +1107,13 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   if (my_live) {
     ws.iout[my_rank] = my_out;
     ws.inint[my_rank] = w_nint(my_shape);
-    if (KIND == GC_SIMPLE) ws.irec[my_rank] = (s0 + lane) % kSeq | my_vec0 << 8;
+    if (KIND == GC_SIMPLE || KIND == GC_PFD) ws.irec[my_rank] = (s0 + lane) % kSeq | my_vec0 << 8;
   }
   if (KIND == GC_PFD) ws.xm[lane] = 0;
 
   // Group-PFD: the exception values of the pack go, as 32-bit words, to the
   // part of the buffer past the re-laid vectors (when they all fit)
   const uint32_t xfree0 = __shfl_sync(kFull, lvi >> 16, np - 1) * kPad;
-  uint32_t xused = 0;
-  bool xfast = true;
 
   // 1. per tile: re-lay its data vectors at 33 words per vector, and turn
   // its control patterns into one (word, shift, width) entry per row
@@ -1115,12 +1171,7 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     } else if (KIND == GC_AFOR) {
       ok = parse_afor<32>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
     } else {
-      const uint32_t room = xfast && xfree0 + xused < (uint32_t)Geo<32>::TBW ? Geo<32>::TBW - xfree0 - xused : 0u;
-      uint32_t ex = 0;
-      ok = parse_pfd32(C, w.tile, w.exc_at, rows, out, ws, line0, ws.tb + xfree0 + xused, room, &ex);
-      if (lane == 0) ws.ixb[__popc(live & ((1u << p) - 1u))] = xfree0 + xused;
-      if (ex == 0xffffffffu) xfast = false;
-      else xused += ex;
+      // parsed below, all of the pack's tiles at once
     }
     if (!ok && lane == 0) report(a.status, GC_ERR_CORRUPT, w.list);
   }
@@ -1131,9 +1182,13 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   const uint32_t upto = heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
   const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;  // its item among the decoded ones
   const uint32_t lhead = act ? 31u - __clz(upto) : 0u;          // the item's first line
-  uint32_t ent, sw;
+  uint32_t ent, sw, xbase = 0;
+  bool xfast = true;
   if (KIND == GC_SIMPLE) {
     parse_simple_pack32(a, ws, act, lane, heads, nl, rank, lhead, ent, sw);
+  } else if (KIND == GC_PFD) {
+    parse_pfd_pack32(a, ws, act, lane, heads, nl, rank, lhead, xfree0, ent, sw, xbase, xfast);
+    __syncwarp();
   } else {
     ent = act ? ws.rw[lane] : 0u;
     sw = act ? ws.rs[lane] : 0u;
@@ -1157,7 +1212,7 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     extract_line<KIND, RESTORE, 0>(P, sh, msk, cross, 0u, nullptr, nullptr, 1u, r, R);
   } else if (xfast) {
     // (lines without exceptions take the same loop)
-    const uint32_t* X = ws.tb + (act ? ws.ixb[rank] : 0u) + xfirst;
+    const uint32_t* X = ws.tb + (act ? xbase : 0u) + xfirst;
     extract_line<KIND, RESTORE, 1>(P, sh, msk, cross, xm, X, nullptr, 1u, r, R);
   } else {
     const uint32_t xwb = xm ? ws.xw[lane] : 1u;
