@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--no-per-list", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the TF-stream and zeta = 0 decodes")
     p.add_argument("--serve-seconds", type=float, default=0.5, help="trace length per request rate")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work budget per codec")
     return p.parse_args()
@@ -424,6 +425,12 @@ def main():
         sn = "pfd" if "pfd" in idxs else next(iter(idxs))
         serving = serving_rates(gc, idxs[sn], a.serve_seconds, launch=launches_cfg[sn])
 
+    # TF streams and Group-PFD without exceptions (BP128's fixed-width frames),
+    # after the timed region
+    extras = None
+    if not a.no_extras:
+        extras = extra_rates(gc, lengths, off, gaps, dev, peak)
+
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
         kinds_id = [CODECS[n][0] for n in idxs]
@@ -446,6 +453,7 @@ def main():
                    "autotuned": tuned or None,
                    "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},
         "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list, "serving": serving,
+        "extras": extras,
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(sum(launches.values()) * a.steps),
         "verified_full_output": verified, "setup_s": {"generate": t_gen, "encode": t_enc},
@@ -454,6 +462,64 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def extra_rates(gc, lengths, off, gaps, dev, peak, reps=5, nsample=300, seed=5):
+    """Decode rates beyond the main workload, each on the same lists and
+    output layout, timed like the main decode (CUDA events, library default
+    launch shape) and checked on a random sample of lists:
+    - tf_<codec>: term-frequency streams (values >= 1, geometric with mean 2),
+      decoded without the prefix sum (restore_docids = 0);
+    - bp_k<k>: Group-PFD with no exception rows (zeta = 0), i.e. SIMD-BP128's
+      fixed-width frames (Sec 6.3), on the d-gaps, docIDs restored; k = 4 is
+      the paper's 128-int frame, k = 32 the GPU layout."""
+    import torch
+    import synth
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(len(lengths), min(nsample, len(lengths)), replace=False)
+    total = int(lengths.sum(dtype=np.uint64))
+
+    def run(idx, restore, want):
+        plan = gc.plan_index(idx)
+        out = torch.empty(max(1, idx.out_ints), dtype=torch.int32, device=dev)
+        scratch = torch.empty(gc.gc_decode_plan_scratch_size(idx.max_tiles), dtype=torch.uint8, device=dev)
+        st = gc.new_status(dev)
+        for _ in range(3):
+            gc.decode_index(idx, out=out, restore_docids=restore, scratch=scratch, status=st, plan=plan, check=False)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gc.decode_index(idx, out=out, restore_docids=restore, scratch=scratch, status=st, plan=plan, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        gc.check_status(st, "extra decode")
+        got = gc.as_u32(out)
+        ok = all(np.array_equal(got[int(off[i]):int(off[i]) + int(lengths[i])], want(i)) for i in ids)
+        ms = float(np.median(ts))
+        alg = idx.compressed_bytes() + plan.nbytes() + 4 * total
+        return {"ms_per_launch": ms, "ints_per_s": total / (ms / 1e3), "bits_per_int": 8.0 * idx.compressed_bytes() / total,
+                "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac": alg / (ms / 1e3) / 1e9 / peak, "sample_verified": ok}
+
+    res = {"lists_verified": len(ids)}
+    tfs, _ = synth.tf_index(21, lengths, 2.0, align=4)
+    d = torch.from_numpy(tfs.view(np.int32)).to(dev)
+    for name, kind in (("simple", CODECS["simple"][0]), ("pfd", CODECS["pfd"][0])):
+        idx = gc.encode_index(gc.make_codec(kind, 32, zeta=0.10), d, lengths, out_offsets=off[:-1])
+        res[f"tf_{name}"] = run(idx, False, lambda i: tfs[int(off[i]):int(off[i]) + int(lengths[i])])
+        del idx
+    del d, tfs
+    d = torch.from_numpy(gaps.view(np.int32)).to(dev)
+    for k in (4, 32):
+        idx = gc.encode_index(gc.make_codec(CODECS["pfd"][0], k, zeta=0.0), d, lengths, out_offsets=off[:-1])
+        res[f"bp_k{k}"] = run(idx, True, lambda i: np.cumsum(gaps[int(off[i]):int(off[i]) + int(lengths[i])],
+                                                              dtype=np.uint32))
+        del idx
+    del d
+    torch.cuda.empty_cache()
+    return res
 
 
 def serving_rates(gc, idx, seconds, rates=(1e4, 5e4, 2e5), launch=None):

@@ -57,6 +57,8 @@ def _load():
             lib.synth_clustered_index.argtypes = [ctypes.c_uint64, ctypes.c_uint64, U32P, U64P,
                                                   ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
                                                   U32P, U32P, ctypes.c_int]
+            lib.synth_tf_index.argtypes = [ctypes.c_uint64, ctypes.c_uint64, U32P, U64P, ctypes.c_double,
+                                           U32P, ctypes.c_int]
             lib.synth_uniform_u32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                               ctypes.c_uint32, U32P]
             lib.synth_width_mix.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
@@ -167,6 +169,21 @@ def uniform_index(seed: int, lengths: np.ndarray, universe: int, out: np.ndarray
         _load().synth_uniform_index(seed, len(lengths), _p32(lengths), _p64(off[:-1].copy()),
                                     universe, _p32(out), threads or _threads())
     return out[:total], off
+
+
+def tf_index(seed: int, lengths: np.ndarray, mean: float = 2.0, align: int = 1, threads: int | None = None):
+    """Term frequencies for lists of the given lengths: values >= 1, geometric
+    with mean `mean`, one seeded stream per list. Returns (tfs, offsets) laid
+    out as uniform_index lays out gaps (align > 1: each list at a multiple of
+    `align` ints, zeros between lists)."""
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
+    off = offsets_of(lengths) if align == 1 else padded_offsets(lengths, align)
+    total = int(off[-1])
+    out = np.empty(total, dtype=np.uint32) if align == 1 else np.zeros(total, dtype=np.uint32)
+    if len(lengths):
+        _load().synth_tf_index(seed, len(lengths), _p32(lengths), _p64(off[:-1].copy()), float(mean), _p32(out),
+                               threads or _threads())
+    return out, off
 
 
 def clustered_index(seed: int, max_lengths: np.ndarray, universe: int, run_mean: float = 16.0,

@@ -312,4 +312,16 @@ void synth_width_mix(uint64_t seed, uint64_t n, uint32_t wlo, uint32_t whi, uint
   }
 }
 
+// Term frequencies of an index: list i's lengths[i] values, each >= 1 and
+// geometric with the given mean, at out + offsets[i] (one stream per list,
+// so the values do not depend on the layout or the thread count).
+void synth_tf_index(uint64_t seed, uint64_t nlists, const uint32_t* lengths, const uint64_t* offsets,
+                    double mean, uint32_t* out, int nthreads) {
+  parallel_for(nlists, nthreads, 256, [&](uint64_t i) {
+    Rng rng(list_seed(seed, i) ^ 0x2545f491ull);
+    uint32_t* dst = out + offsets[i];
+    for (uint32_t t = 0; t < lengths[i]; ++t) dst[t] = rng.geometric(mean);
+  });
+}
+
 }  // extern "C"

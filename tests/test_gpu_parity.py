@@ -19,7 +19,7 @@ K_GSC = [(1, 0), (2, 0), (4, 0), (8, 0), (1, 1), (2, 1), (4, 1), (8, 1), (4, 2),
 CODECS = ([(O.SIMPLE, k, 0, 0, 0.1) for k in (4, 32)]
           + [(O.SCHEME, k, cg, ld, 0.1) for k in (4, 32) for cg, ld in K_GSC]
           + [(O.AFOR, k, 0, 0, 0.1) for k in (4, 32)]
-          + [(O.PFD, k, 0, 0, z) for k in (4, 32) for z in (0.01, 0.1, 0.3)])
+          + [(O.PFD, k, 0, 0, z) for k in (4, 32) for z in (0.0, 0.01, 0.1, 0.3)])
 
 
 def cid(c):

@@ -392,7 +392,7 @@ CODECS = ([O.Codec(O.SIMPLE, k) for k in (4, 32)]
              for cg, ld in [(1, 0), (2, 0), (4, 0), (8, 0), (1, 1), (2, 1), (4, 1), (8, 1),
                             (4, 2), (8, 2)]]
           + [O.Codec(O.AFOR, k) for k in (4, 32)]
-          + [O.Codec(O.PFD, k, zeta=z) for k in (4, 32) for z in (0.01, 0.1, 0.3)])
+          + [O.Codec(O.PFD, k, zeta=z) for k in (4, 32) for z in (0.0, 0.01, 0.1, 0.3)])
 
 
 @pytest.mark.parametrize("codec", CODECS, ids=repr)
