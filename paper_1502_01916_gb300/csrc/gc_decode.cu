@@ -835,62 +835,19 @@ __device__ void decode_pack(const DecodeArgs& a, WarpSmem<K>& ws, uint32_t s0, u
   __syncwarp();
 }
 
-// One Group-PFD exception value of `wb` bytes (little-endian), wherever its
-// frame's values are (staged window or global memory). Out of line: it runs
-// once per exception, and keeping it out of the unrolled loop keeps that
-// loop small.
-__device__ __noinline__ uint32_t exc_value(const uint8_t* p, uint32_t wb) {
-  uint32_t x = p[0];
-  if (wb > 1) x |= (uint32_t)p[1] << 8;
-  if (wb > 2) x |= ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-  return x;
-}
-
-// A Group-PFD line whose exception values could not be staged: the values
-// are read in place (xwb bytes each at xp, in column order). It runs rarely,
-// so it stays out of line, with its results in memory, and keeps the hot
-// line loop small.
-template <bool RESTORE>
-__device__ __noinline__ uint32_t extract_line_generic(const uint32_t* P, uint32_t sh, uint32_t msk, bool cross,
-                                                      uint32_t xm, const uint8_t* xp, uint32_t xwb, uint32_t* r) {
-  uint32_t R = 0;
-  for (int j = 0; j < 32; ++j) {
-    const uint32_t lo = P[j];
-    const uint32_t hi = cross ? P[kPad + j] : 0u;
-    uint32_t v = __funnelshift_r(lo, hi, sh) & msk;
-    if ((xm >> j) & 1u) {
-      v = exc_value(xp, xwb);
-      xp += xwb;
-    }
-    R += v;
-    r[j] = RESTORE ? R : v;
-  }
-  return R;
-}
-
 // One line (32 ints) of the k = 32 decoder in natural column order: word
-// (P[j], P[33 + j]) >> shift & mask, Group-PFD exceptions over their slots
-// (XMODE 0: none in the pack; 1: values staged as 32-bit words at X, in
-// column order; 2: values of xwb bytes at xp), and the running sum.
-template <int KIND, bool RESTORE, int XMODE>
-__device__ __forceinline__ void extract_line(const uint32_t* P, uint32_t sh, uint32_t msk, bool cross, uint32_t xm,
-                                             const uint32_t* X, const uint8_t* xp, uint32_t xwb, uint32_t (&r)[32],
-                                             uint32_t& R) {
+// (P[j], P[33 + j]) >> shift & mask, and the running sum (the prefix within
+// the line) when restoring docIDs.
+template <int KIND, bool RESTORE>
+__device__ __forceinline__ void extract_line(const uint32_t* P, uint32_t sh, uint32_t msk, bool cross,
+                                             uint32_t (&r)[32], uint32_t& R) {
   R = 0;
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const uint32_t lo = P[j];
     uint32_t hi = 0;
     if (KIND != GC_SIMPLE && cross) hi = P[kPad + j];  // Group-Simple values never cross a word
-    uint32_t v = __funnelshift_r(lo, hi, sh) & msk;
-    if (XMODE == 1) {
-      if ((xm >> j) & 1u) v = *X++;
-    } else if (XMODE == 2) {
-      if ((xm >> j) & 1u) {
-        v = exc_value(xp, xwb);
-        xp += xwb;
-      }
-    }
+    const uint32_t v = __funnelshift_r(lo, hi, sh) & msk;
     if (RESTORE) {
       R += v;
       r[j] = R;
@@ -958,13 +915,13 @@ __device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, WarpSme
   if (!ok) report(a.status, GC_ERR_CORRUPT, w.list);
 }
 
-// Group-PFD: one tile's exceptions: every one sets its slot's bit in its
-// line's mask and, with `stage`, its value goes as a 32-bit word to the
-// re-lay buffer at word xb + its index (e 16-bit positions at rp, then e
-// values of wb bytes; the tile's first line is hl, its frame holds lim ints).
-__device__ __forceinline__ void pfd_exceptions(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t lane, uint32_t hl,
-                                               uint32_t e, uint32_t lim, uint32_t wb, const uint8_t* rp, uint32_t xb,
-                                               bool stage, uint32_t list) {
+// Group-PFD, k = 32: one tile's exceptions overwrite their slots in the
+// pack's line-major buffer (line l at words 32 l .. 32 l + 31, its 16-byte
+// chunk c at chunk c ^ (l & 7)): e 16-bit positions at rp, then e values of
+// wb bytes (Sec 6.2, decoding Step 3); the tile's first line is hl, its
+// frame holds lim ints. A position outside the frame is reported.
+__device__ __forceinline__ void pfd_patch(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t lane, uint32_t hl, uint32_t e,
+                                          uint32_t lim, uint32_t wb, const uint8_t* rp, uint32_t list) {
   const uint8_t* vp = rp + (size_t)e * 2;
   for (uint32_t x = lane; x < e; x += 32) {
     const uint32_t pos = (uint32_t)rp[2 * x] | ((uint32_t)rp[2 * x + 1] << 8);
@@ -972,32 +929,31 @@ __device__ __forceinline__ void pfd_exceptions(const DecodeArgs& a, WarpSmem<32>
       report(a.status, GC_ERR_CORRUPT, list);
       continue;
     }
-    atomicOr(&ws.xm[hl + (pos >> 5)], 1u << (pos & 31u));
-    if (stage) {
-      const uint8_t* v8 = vp + (size_t)x * wb;
-      uint32_t v = v8[0];
-      if (wb > 1) v |= (uint32_t)v8[1] << 8;
-      if (wb > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
-      ws.tb[xb + x] = v;
-    }
+    const uint8_t* v8 = vp + (size_t)x * wb;
+    uint32_t v = v8[0];
+    if (wb > 1) v |= (uint32_t)v8[1] << 8;
+    if (wb > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
+    const uint32_t line = hl + (pos >> 5), col = pos & 31u;
+    ws.tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
   }
 }
 
-// Group-PFD, k = 32: the headers, rows and exceptions of all of a pack's
-// tiles at once (a tile is one frame, Sec 6). Line l is row q = l - lhead
-// of its tile: every line reads its tile's header (b, exception width code,
-// exception count e) and takes row q at q * b bits (lanes past the pack's
-// lines read the first tile's). The pack's exception values go, as 32-bit
-// words and tile after tile, to the re-lay buffer from word xfree0 on when
-// all of them fit (xfast), else the lines read them in place (xv, xw);
-// every exception sets its slot's bit in its line's mask (xm, zeroed
-// beforehand). Returns the line's row entry in registers and the buffer
-// word of its tile's first exception value (xbase); reports a tile whose
-// header, row widths or exception record are malformed.
+// The facts of a Group-PFD tile's exceptions that the patch step needs.
+struct PfdExc {
+  const uint8_t* rp;  // the exception record (positions, then values)
+  uint32_t e, wb, lim, list;
+};
+
+// Group-PFD, k = 32: the headers and rows of all of a pack's tiles at once
+// (a tile is one frame, Sec 6). Line l is row q = l - lhead of its tile:
+// every line reads its tile's header (b, exception width code, exception
+// count e) and takes row q at q * b bits (lanes past the pack's lines read
+// the first tile's). Returns the line's row entry in registers and its
+// tile's exception record; reports a tile whose header, row widths or
+// exception record are malformed.
 __device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, WarpSmem<32>& ws, bool act, uint32_t lane,
                                                  uint32_t heads, uint32_t nl, uint32_t rank, uint32_t lhead,
-                                                 uint32_t xfree0, uint32_t& ent, uint32_t& sw, uint32_t& xbase,
-                                                 bool& xfast) {
+                                                 uint32_t& ent, uint32_t& sw, PfdExc& x) {
   // this line's tile (its record slot is also its staging slot)
   const uint32_t im = heads ? ws.irec[rank] : 0u;
   const uint32_t f = im % kSeq, v0 = im >> 8;
@@ -1043,32 +999,29 @@ __device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, WarpSmem<3
   ent = !act ? 0u : oor ? v0 * kPad : v0 * kPad + (rb >> 5) * kPad;
   sw = act && !oor ? (rb & 31u) | (b << 8) : 0u;
   if (act && !ok) report(a.status, GC_ERR_CORRUPT, w.list);
-  // the record: e 16-bit positions, then e values of wb bytes
-  const uint8_t* rp = C.addr(w.exc_at, (uint64_t)e * (2 + wb));
+  x.rp = C.addr(w.exc_at, (uint64_t)e * (2 + wb));
+  x.e = e;
+  x.wb = wb;
+  x.lim = lim;
+  x.list = w.list;
+}
+
+// Group-PFD, k = 32: the exceptions of every tile of the pack over their
+// slots (a pack of one tile: every lane already holds its facts).
+__device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t lane, uint32_t heads,
+                                                 const PfdExc& x) {
   if (heads == 1u) {
-    // one tile: every lane holds its facts
-    xbase = xfree0;
-    xfast = xfree0 + e <= (uint32_t)Geo<32>::TBW;
-    pfd_exceptions(a, ws, lane, 0, e, lim, wb, rp, xbase, xfast, w.list);
-  } else {
-    // the tiles' values one after another; then tile by tile
-    const uint32_t E = warp_incl_sum(act && lane == lhead ? e : 0u);
-    xfast = xfree0 + __shfl_sync(kFull, E, 31) <= (uint32_t)Geo<32>::TBW;
-    xbase = xfree0 + E - (act ? e : 0u);
-    for (uint32_t hm = heads; hm; hm &= hm - 1) {
-      const uint32_t hl = __ffs(hm) - 1;  // the tile's first line
-      const uint32_t ef = __shfl_sync(kFull, e, hl);
-      const uint32_t limf = __shfl_sync(kFull, lim, hl);
-      const uint32_t wbf = __shfl_sync(kFull, wb, hl);
-      const uint32_t xb = __shfl_sync(kFull, xbase, hl);
-      const uint32_t lf = __shfl_sync(kFull, w.list, hl);
-      const uint8_t* rpf = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, (unsigned long long)rp, hl));
-      pfd_exceptions(a, ws, lane, hl, ef, limf, wbf, rpf, xb, xfast, lf);
-    }
+    pfd_patch(a, ws, lane, 0, x.e, x.lim, x.wb, x.rp, x.list);
+    return;
   }
-  if (!xfast && act) {
-    ws.xv[lane] = (unsigned long long)(rp + (size_t)e * 2);
-    ws.xw[lane] = wb;
+  for (uint32_t hm = heads; hm; hm &= hm - 1) {
+    const uint32_t hl = __ffs(hm) - 1;  // the tile's first line
+    const uint32_t e = __shfl_sync(kFull, x.e, hl);
+    const uint32_t lim = __shfl_sync(kFull, x.lim, hl);
+    const uint32_t wb = __shfl_sync(kFull, x.wb, hl);
+    const uint32_t list = __shfl_sync(kFull, x.list, hl);
+    const uint8_t* rp = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, (unsigned long long)x.rp, hl));
+    pfd_patch(a, ws, lane, hl, e, lim, wb, rp, list);
   }
 }
 
@@ -1109,11 +1062,6 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
     ws.inint[my_rank] = w_nint(my_shape);
     if (KIND == GC_SIMPLE || KIND == GC_PFD) ws.irec[my_rank] = (s0 + lane) % kSeq | my_vec0 << 8;
   }
-  if (KIND == GC_PFD) ws.xm[lane] = 0;
-
-  // Group-PFD: the exception values of the pack go, as 32-bit words, to the
-  // part of the buffer past the re-laid vectors (when they all fit)
-  const uint32_t xfree0 = __shfl_sync(kFull, lvi >> 16, np - 1) * kPad;
 
   // 1. per tile: re-lay its data vectors at 33 words per vector, and turn
   // its control patterns into one (word, shift, width) entry per row
@@ -1182,13 +1130,12 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   const uint32_t upto = heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
   const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;  // its item among the decoded ones
   const uint32_t lhead = act ? 31u - __clz(upto) : 0u;          // the item's first line
-  uint32_t ent, sw, xbase = 0;
-  bool xfast = true;
+  uint32_t ent, sw;
+  PfdExc px;
   if (KIND == GC_SIMPLE) {
     parse_simple_pack32(a, ws, act, lane, heads, nl, rank, lhead, ent, sw);
   } else if (KIND == GC_PFD) {
-    parse_pfd_pack32(a, ws, act, lane, heads, nl, rank, lhead, xfree0, ent, sw, xbase, xfast);
-    __syncwarp();
+    parse_pfd_pack32(a, ws, act, lane, heads, nl, rank, lhead, ent, sw, px);
   } else {
     ent = act ? ws.rw[lane] : 0u;
     sw = act ? ws.rs[lane] : 0u;
@@ -1197,31 +1144,43 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   const uint32_t msk = low_mask(wd);
   const bool cross = sh + wd > 32;
   const uint32_t* P = ws.tb + ent;
-  uint32_t xm = 0, xfirst = 0;
-  if (KIND == GC_PFD) {
-    // the tile is one frame: exceptions before this line in it
-    xm = act ? ws.xm[lane] : 0u;
-    const uint32_t cnt = __popc(xm);
-    const uint32_t V = warp_incl_sum(cnt);
-    const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
-    xfirst = V - cnt - (lhead ? Vb : 0u);
-  }
   uint32_t r[32];
   uint32_t R = 0;
   if (KIND != GC_PFD) {
-    extract_line<KIND, RESTORE, 0>(P, sh, msk, cross, 0u, nullptr, nullptr, 1u, r, R);
-  } else if (xfast) {
-    // (lines without exceptions take the same loop)
-    const uint32_t* X = ws.tb + (act ? xbase : 0u) + xfirst;
-    extract_line<KIND, RESTORE, 1>(P, sh, msk, cross, xm, X, nullptr, 1u, r, R);
+    extract_line<KIND, RESTORE>(P, sh, msk, cross, r, R);
   } else {
-    const uint32_t xwb = xm ? ws.xw[lane] : 1u;
-    const uint8_t* xp = xm ? reinterpret_cast<const uint8_t*>(ws.xv[lane]) + (size_t)xfirst * xwb : nullptr;
-    uint32_t rm[32];
-    const uint32_t Rm = extract_line_generic<RESTORE>(P, sh, msk, cross, xm, xp, xwb, rm);
-    R = RESTORE ? Rm : 0u;
+    // Group-PFD: the slots' values, then the exceptions over their slots in
+    // the line-major buffer (line l at words 32 l .., 16-byte chunk c at
+    // chunk c ^ (l & 7)), then the running sum over the patched line
+    extract_line<KIND, false>(P, sh, msk, cross, r, R);
+    uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
+    const uint32_t swz = lane & 7u;
+    __syncwarp();  // (the re-laid data is read)
+    if (act) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) r[j] = rm[j];
+      for (int c = 0; c < 8; ++c) T[c ^ swz] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+    }
+    __syncwarp();
+    pfd_patch_pack32(a, ws, lane, heads, px);
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint4 v = T[c ^ swz];
+        r[4 * c] = v.x;
+        r[4 * c + 1] = v.y;
+        r[4 * c + 2] = v.z;
+        r[4 * c + 3] = v.w;
+      }
+    }
+    R = 0;
+    if (RESTORE) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        R += r[j];
+        r[j] = R;
+      }
+    }
   }
 
   // 3. docIDs: segmented scan of line totals, then each item's base
