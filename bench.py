@@ -36,9 +36,10 @@ CODECS = {"simple": (0, "Group-Simple"), "pfd": (3, "Group-PFD")}
 # ncu capture (profiles/k_decode_zipf_index_dram.md), with the hash of the
 # kernel sources they were taken on; once the sources change, null.
 NCU_TRAFFIC = {
-    "simple": {"bytes": 2954974720 + 5950713344, "hash": "67146018e4d11008"},
-    "pfd": {"bytes": 2432178944 + 5945080576, "hash": "67146018e4d11008"},
+    "simple": {"bytes": 2955285504 + 5949318400, "hash": "f0fbb070363a342c"},
+    "pfd": {"bytes": 2433082880 + 5944994304, "hash": "f0fbb070363a342c"},
 }
+
 
 def parse():
     p = argparse.ArgumentParser()
