@@ -367,6 +367,49 @@ gc_status gc_decode_static(const gc_codec* codec, const uint8_t* d_ctrl, uint64_
                            const uint32_t* d_data, uint64_t data_words, uint64_t n, const gc_tile* d_tiles,
                            uint32_t* d_out, int restore_docids, uint32_t* d_status, void* stream);
 
+/* ------------------------------------------------------ AND queries */
+
+/* Scratch bytes gc_intersect needs: a_ints = the sum of the a lists'
+ * lengths, a_tiles and b_tiles = the sums of the a and b lists' tiles
+ * (ceil(n / k) rows in tiles of 1024 / k rows). */
+gc_status gc_intersect_scratch_size(uint64_t a_ints, uint64_t a_tiles, uint64_t b_tiles, uint64_t* bytes);
+
+/* AND queries over a batch index (Sec 7.4: the lists of a query are decoded
+ * and intersected, skip pointers letting the intersection pass over blocks
+ * that cannot match). Query q returns the docIDs of list d_a[q] that are
+ * also in list d_b[q], in increasing order. List a is decoded whole; of
+ * list b only the tiles that can hold one of a's docIDs are decoded: tile
+ * t >= 1 holds the docIDs above its skip entry (gc_tile.base, the docID
+ * before the tile), so a docID x can only be in the last tile whose entry
+ * is below x. Put the shorter list of a query in d_a.
+ *   d_lists / nlists, d_tile_pool / tile_pool_len, d_ctrl_pool /
+ *     ctrl_pool_bytes, d_data_pool / data_pool_words: the index, as for
+ *     gc_decode_batch; every tile record of a b list must carry its skip
+ *     entry (GC_TILE_BASE, which gc_encode_batch writes), else
+ *     GC_ERR_UNSUPPORTED in d_status.
+ *   d_a, d_b: nqueries list indices each, on the device.
+ *   d_a_offs: nqueries uint64, exclusive prefix sums of the a lists'
+ *     lengths: a's docIDs, and query q's results, start there.
+ *   d_b_tile_offs: nqueries uint64, exclusive prefix sums of the b lists'
+ *     tiles.
+ *   a_ints, a_tiles, b_tiles: the totals gc_intersect_scratch_size takes.
+ *   d_out: a_ints uint32, receives query q's results from d_a_offs[q] on.
+ *   d_counts: nqueries uint32, receives each query's result count.
+ *   d_scratch: gc_intersect_scratch_size bytes, 256-byte aligned. After
+ *     the call its first 32 bytes hold four uint64: the a tiles decoded,
+ *     those of them that took their prefix by look-back, the b tiles
+ *     decoded, and those of them that took it by look-back.
+ * A list index >= nlists gives GC_ERR_INVALID in d_status (and no results
+ * for that query). Asynchronous on `stream`; no host synchronisation, so it
+ * is graph-capturable. The paper's queries also rank; this call returns the
+ * matching docIDs only. */
+gc_status gc_intersect(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists, const gc_tile* d_tile_pool,
+                       uint64_t tile_pool_len, const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
+                       const uint32_t* d_data_pool, uint64_t data_pool_words, const uint32_t* d_a,
+                       const uint32_t* d_b, const uint64_t* d_a_offs, const uint64_t* d_b_tile_offs, uint64_t nqueries,
+                       uint64_t a_ints, uint64_t a_tiles, uint64_t b_tiles, uint32_t* d_out, uint32_t* d_counts,
+                       void* d_scratch, uint64_t scratch_bytes, uint32_t* d_status, void* stream);
+
 /* Number of kernels the last gc_* call on this host thread launched (for
  * launch accounting). */
 uint32_t gc_last_launch_count(void);

@@ -1827,6 +1827,38 @@ gc_status plan_impl(const gc_codec& c, const gc_list* lists, const gc_list* one,
   return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;
 }
 
+}  // namespace
+
+gc_status gc_host::plan_fill(const gc_codec& c, const gc_list* d_lists, uint64_t nlists, const uint32_t* d_sel,
+                             const uint64_t* d_outs, uint64_t nsel, const gc_tile* d_tiles, uint64_t ntiles,
+                             const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes, gc_work* d_work, uint64_t cap,
+                             uint64_t* d_count, uint32_t* d_status, cudaStream_t s) {
+  if (cap == 0) return GC_OK;
+  PlanArgs a = {};
+  a.kind = c.kind;
+  a.k = c.k;
+  a.cg = c.cg;
+  a.ld = c.ld;
+  a.lists = d_lists;
+  a.nlists = nsel;
+  a.sel = d_sel;
+  a.outs = d_outs;
+  a.nall = nlists;
+  a.tiles = d_tiles;
+  a.ntiles = d_tiles ? ntiles : 0;
+  a.ctrl_pool = d_ctrl_pool;
+  a.ctrl_pool_bytes = d_ctrl_pool ? ctrl_pool_bytes : 0;
+  a.work = d_work;
+  a.cap = cap;
+  a.count = reinterpret_cast<unsigned long long*>(d_count);
+  a.status = d_status;
+  k_plan_fill<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(a);
+  gc_host::count_launch();
+  return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+}
+
+namespace {
+
 gc_status decode_plan_impl(const gc_codec& c, const gc_work* work, const uint64_t* count, uint64_t work_cap,
                            const uint8_t* ctrl_pool, uint64_t ctrl_pool_bytes, const uint32_t* data_pool,
                            uint64_t data_pool_words, uint32_t* out_pool, uint64_t out_pool_len, int restore,

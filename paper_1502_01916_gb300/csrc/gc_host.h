@@ -31,4 +31,13 @@ uint64_t index_sums_bytes(const gc_codec& c, uint64_t n);
 gc_status build_tiles(const gc_codec& c, const uint8_t* d_ctrl, uint64_t ctrl_bytes, uint64_t n, gc_tile* d_tiles,
                       void* d_sums, uint32_t* d_status, cudaStream_t s);
 
+// The rest of a work plan whose records the caller has written, (list,
+// tile) each, `list` an index into d_sel / d_outs: fills every record
+// below count[0] as gc_plan_select fills its own (list d_lists[d_sel[list]],
+// output at d_outs[list] + 1024 * tile; records past count[0] are left).
+gc_status plan_fill(const gc_codec& c, const gc_list* d_lists, uint64_t nlists, const uint32_t* d_sel,
+                    const uint64_t* d_outs, uint64_t nsel, const gc_tile* d_tiles, uint64_t ntiles,
+                    const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes, gc_work* d_work, uint64_t cap,
+                    uint64_t* d_count, uint32_t* d_status, cudaStream_t s);
+
 }  // namespace gc_host

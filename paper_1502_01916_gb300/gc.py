@@ -25,7 +25,7 @@ __all__ = [
     "TILE_BASE", "WORK_VEC_SHIFT", "WORK_BIT_SHIFT", "WORK_SKIP_SHIFT", "WORK_HAS_BASE", "WORK_PUBLISH",
     "TILE_DTYPE", "LIST_DTYPE", "WORK_DTYPE",
     "WORK_BYTES", "GcError", "gc_work", "gc_plan_batch", "gc_plan_select", "gc_decode_plan_scratch_size",
-    "gc_decode_plan", "Plan",
+    "gc_decode_plan", "Plan", "gc_intersect_scratch_size", "gc_intersect", "intersect",
     "plan_index",
     "gc_codec", "gc_tile", "gc_list", "gc_launch", "library_path", "load", "make_codec",
     "gc_pfd_rows_for_zeta", "gc_max_encoded_size", "gc_encode_scratch_size", "gc_encode",
@@ -147,6 +147,9 @@ def load():
             "gc_decode_plan_scratch_size": (_I, [_U64, _U64P]),
             "gc_decode_plan": (_I, [_CP, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I,
                                     ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
+            "gc_intersect_scratch_size": (_I, [_U64, _U64, _U64, _U64P]),
+            "gc_intersect": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V, _V, _U64, _U64, _U64,
+                                  _U64, _V, _V, _V, _U64, _V, _V]),
             "gc_last_launch_count": (_U32, []),
             "gc_version": (ctypes.c_char_p, []),
         }
@@ -572,3 +575,58 @@ def decode_index(index: Index, out: torch.Tensor | None = None, restore_docids: 
     if check:
         check_status(st, "gc_decode_plan" if plan is not None else "gc_decode_batch")
     return out
+
+
+def gc_intersect_scratch_size(a_ints: int, a_tiles: int, b_tiles: int) -> int:
+    b = _U64()
+    _check(load().gc_intersect_scratch_size(a_ints, a_tiles, b_tiles, ctypes.byref(b)), "gc_intersect_scratch_size")
+    return b.value
+
+
+def gc_intersect(index, d_a, d_b, d_a_offs, d_b_tile_offs, nqueries, a_ints, a_tiles, b_tiles, d_out, d_counts,
+                 d_scratch, d_status, stream=None):
+    tile_len = index.tiles.numel() // TILE_BYTES
+    _check(load().gc_intersect(ctypes.byref(index.codec), _ptr(index.lists), index.nlists, _ptr(index.tiles), tile_len,
+                               _ptr(index.ctrl), index.ctrl.numel(), _ptr(index.data), index.data.numel(), _ptr(d_a),
+                               _ptr(d_b), _ptr(d_a_offs), _ptr(d_b_tile_offs), nqueries, a_ints, a_tiles, b_tiles,
+                               _ptr(d_out), _ptr(d_counts), _ptr(d_scratch), d_scratch.numel(), _ptr(d_status),
+                               _stream(stream)),
+           "gc_intersect")
+
+
+def intersect(index: Index, pairs, status=None, stream=None, check: bool = True):
+    """AND queries over a resident index: for each (i, j) in `pairs`, the
+    docIDs in both list i and list j (gc_intersect; each query's shorter list
+    is decoded whole, the other only where its skip entries allow a match).
+    Returns (results, counts, offsets): query q's docIDs are
+    results[offsets[q]:offsets[q] + counts[q]] (uint32 numpy)."""
+    dev = index.data.device
+    P = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    nq = len(P)
+    L = index.lengths.astype(np.int64)
+    li, lj = P[:, 0], P[:, 1]
+    swap = L[lj] < L[li]
+    qa = np.where(swap, lj, li).astype(np.uint32)
+    qb = np.where(swap, li, lj).astype(np.uint32)
+    tr = TILE_INTS // index.codec.k
+    tiles = lambda n: ((n + index.codec.k - 1) // index.codec.k + tr - 1) // tr
+    na = L[qa]
+    tb = tiles(L[qb])
+    aoff = np.zeros(nq, np.uint64)
+    boff = np.zeros(nq, np.uint64)
+    if nq > 1:
+        np.cumsum(na[:-1], out=aoff[1:])
+        np.cumsum(tb[:-1], out=boff[1:])
+    a_ints, a_tiles, b_tiles = int(na.sum()), int(tiles(na).sum()), int(tb.sum())
+    up = lambda x, dt: torch.from_numpy(np.ascontiguousarray(x).view(dt)).to(dev)
+    d_a, d_b = up(qa, np.int32), up(qb, np.int32)
+    d_aoff, d_boff = up(aoff, np.int64), up(boff, np.int64)
+    d_out = torch.empty(max(1, a_ints), dtype=torch.int32, device=dev)
+    d_counts = torch.zeros(max(1, nq), dtype=torch.int32, device=dev)
+    scratch = torch.empty(gc_intersect_scratch_size(a_ints, a_tiles, b_tiles), dtype=torch.uint8, device=dev)
+    st = new_status(dev) if status is None else status
+    gc_intersect(index, d_a, d_b, d_aoff, d_boff, nq, a_ints, a_tiles, b_tiles, d_out, d_counts, scratch, st, stream)
+    if check:
+        check_status(st, "gc_intersect")
+    return as_u32(d_out), as_u32(d_counts[:nq]), aoff
+

@@ -130,3 +130,16 @@ def test_encode_index_rejects_lists_past_the_gaps(gc):
         gc.encode_index(c, gaps, [40, 40], out_offsets=np.array([0, 64], np.uint64))
     with pytest.raises(ValueError):
         gc.encode_index(c, gaps, [40, 40], out_offsets=np.array([0], np.uint64))
+
+
+def test_intersect_validates_on_the_host(gc):
+    """gc_intersect: no queries is a no-op, missing buffers are refused,
+    scratch grows with the work, all before any device call."""
+    lib = gc.load()
+    c = gc.make_codec(gc.SIMPLE, 32)
+    args = [None, 1, None, 0, None, 0, None, 0, None, None, None, None]
+    assert lib.gc_intersect(ctypes.byref(c), *args, 0, 0, 0, 0, None, None, None, 0, None, None) == 0
+    assert lib.gc_intersect(ctypes.byref(c), *args, 1, 0, 0, 0, None, None, None, 0, None, None) == 1
+    s1 = gc.gc_intersect_scratch_size(1000, 2, 10)
+    s2 = gc.gc_intersect_scratch_size(100000, 200, 1000)
+    assert 0 < s1 < s2
