@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the TF-stream and zeta = 0 decodes")
+    p.add_argument("--no-and", action="store_true", help="skip the AND-query measurement")
+    p.add_argument("--and-queries", type=int, default=4000, help="two-list AND queries in the timed batch")
     p.add_argument("--serve-seconds", type=float, default=0.5, help="trace length per request rate")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work budget per codec")
     return p.parse_args()
@@ -474,6 +476,12 @@ def main():
         sn = "pfd" if "pfd" in idxs else next(iter(idxs))
         serving = serving_rates(gc, idxs[sn], a.serve_seconds, launch=launches_cfg[sn])
 
+    # AND queries over the resident index (skip entries bound what is decoded)
+    and_q = None
+    if not a.no_and:
+        sn = "pfd" if "pfd" in idxs else next(iter(idxs))
+        and_q = and_query_rates(gc, idxs[sn], lengths, off, gaps, dev, a.and_queries)
+
     # TF streams and Group-PFD without exceptions (BP128's fixed-width frames),
     # after the timed region
     extras = None
@@ -505,7 +513,7 @@ def main():
                    "autotuned": tuned or None,
                    "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},
         "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list, "serving": serving,
-        "extras": extras,
+        "extras": extras, "and_queries": and_q,
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(sum(launches.values()) * a.steps),
         "verified_full_output": verified, "setup_s": {"generate": t_gen, "encode": t_enc},
@@ -572,6 +580,54 @@ def extra_rates(gc, lengths, off, gaps, dev, peak, reps=5, nsample=300, seed=5):
     del d
     torch.cuda.empty_cache()
     return res
+
+
+def and_query_rates(gc, idx, lengths, off, gaps, dev, nq=4000, reps=5, nverify=200, seed=13):
+    """Two-list AND queries over the resident index (gc_intersect), each
+    list drawn with probability proportional to length^0.5 (as the serving
+    trace draws them), answered as one batch: timed with CUDA events, checked
+    on a sample of queries against numpy's intersection of the host's prefix
+    sums. Reports how many tiles of the longer lists the skip entries let
+    the call leave undecoded."""
+    import torch
+    rng = np.random.default_rng(seed)
+    w = np.sqrt(lengths.astype(np.float64))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    pairs = np.minimum(np.searchsorted(cdf, rng.random((nq, 2)), side="right"), len(lengths) - 1)
+    b = gc.and_batch(idx, pairs)
+    st = gc.new_status(dev)
+    for _ in range(3):
+        gc.run_and_batch(idx, b, st)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gc.run_and_batch(idx, b, st)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    gc.check_status(st, "and queries")
+    res, counts = gc.as_u32(b.d_out), gc.as_u32(b.d_counts[:nq])
+    a_tiles, b_tiles_decoded = gc.and_batch_tiles(b)
+
+    def ids(i):
+        return np.cumsum(gaps[int(off[i]):int(off[i]) + int(lengths[i])], dtype=np.uint32)
+
+    ok = True
+    for q in rng.choice(nq, min(nverify, nq), replace=False):
+        want = np.intersect1d(ids(b.qa[q]), ids(b.qb[q]))
+        got = res[int(b.aoff[q]):int(b.aoff[q]) + int(counts[q])]
+        ok = ok and np.array_equal(got, want)
+    ms = float(np.median(ts))
+    return {"queries": nq, "ms_per_batch": ms, "queries_per_s": nq / (ms / 1e3),
+            "codec": gc.codec_name(idx.codec), "results": int(counts.sum()),
+            "shorter_list_ints": b.a_ints, "longer_list_ints": b.b_ints,
+            "longer_list_tiles": b.b_tiles, "longer_list_tiles_decoded": b_tiles_decoded,
+            "decoded_ints_vs_both_whole": (b.a_ints + 1024 * b_tiles_decoded) / max(1, b.a_ints + b.b_ints),
+            "sample_verified": bool(ok), "sample": int(min(nverify, nq)),
+            "launches_per_batch": gc.gc_last_launch_count()}
 
 
 def serving_rates(gc, idx, seconds, rates=(1e4, 5e4, 2e5), launch=None):

@@ -25,7 +25,8 @@ __all__ = [
     "TILE_BASE", "WORK_VEC_SHIFT", "WORK_BIT_SHIFT", "WORK_SKIP_SHIFT", "WORK_HAS_BASE", "WORK_PUBLISH",
     "TILE_DTYPE", "LIST_DTYPE", "WORK_DTYPE",
     "WORK_BYTES", "GcError", "gc_work", "gc_plan_batch", "gc_plan_select", "gc_decode_plan_scratch_size",
-    "gc_decode_plan", "Plan", "gc_intersect_scratch_size", "gc_intersect", "intersect",
+    "gc_decode_plan", "Plan", "gc_intersect_scratch_size", "gc_intersect", "intersect", "AndBatch", "and_batch",
+    "run_and_batch", "and_batch_tiles",
     "plan_index",
     "gc_codec", "gc_tile", "gc_list", "gc_launch", "library_path", "load", "make_codec",
     "gc_pfd_rows_for_zeta", "gc_max_encoded_size", "gc_encode_scratch_size", "gc_encode",
@@ -594,12 +595,33 @@ def gc_intersect(index, d_a, d_b, d_a_offs, d_b_tile_offs, nqueries, a_ints, a_t
            "gc_intersect")
 
 
-def intersect(index: Index, pairs, status=None, stream=None, check: bool = True):
-    """AND queries over a resident index: for each (i, j) in `pairs`, the
-    docIDs in both list i and list j (gc_intersect; each query's shorter list
-    is decoded whole, the other only where its skip entries allow a match).
-    Returns (results, counts, offsets): query q's docIDs are
-    results[offsets[q]:offsets[q] + counts[q]] (uint32 numpy)."""
+@dataclasses.dataclass
+class AndBatch:
+    """A batch of AND queries laid out for gc_intersect (device arrays and
+    the totals that size its scratch)."""
+    qa: np.ndarray         # per query: list decoded whole (the shorter)
+    qb: np.ndarray         # per query: list decoded by tile
+    aoff: np.ndarray       # per query: first int of its a docIDs and results
+    d_a: torch.Tensor
+    d_b: torch.Tensor
+    d_aoff: torch.Tensor
+    d_boff: torch.Tensor
+    a_ints: int
+    a_tiles: int
+    b_tiles: int
+    b_ints: int
+    d_out: torch.Tensor
+    d_counts: torch.Tensor
+    scratch: torch.Tensor
+
+    @property
+    def nqueries(self) -> int:
+        return len(self.qa)
+
+
+def and_batch(index: Index, pairs) -> AndBatch:
+    """Lay out the queries (i, j) of `pairs` for gc_intersect: each query's
+    shorter list first, offsets, tile totals, output and scratch buffers."""
     dev = index.data.device
     P = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
     nq = len(P)
@@ -609,7 +631,10 @@ def intersect(index: Index, pairs, status=None, stream=None, check: bool = True)
     qa = np.where(swap, lj, li).astype(np.uint32)
     qb = np.where(swap, li, lj).astype(np.uint32)
     tr = TILE_INTS // index.codec.k
-    tiles = lambda n: ((n + index.codec.k - 1) // index.codec.k + tr - 1) // tr
+
+    def tiles(n):
+        return ((n + index.codec.k - 1) // index.codec.k + tr - 1) // tr
+
     na = L[qa]
     tb = tiles(L[qb])
     aoff = np.zeros(nq, np.uint64)
@@ -618,15 +643,39 @@ def intersect(index: Index, pairs, status=None, stream=None, check: bool = True)
         np.cumsum(na[:-1], out=aoff[1:])
         np.cumsum(tb[:-1], out=boff[1:])
     a_ints, a_tiles, b_tiles = int(na.sum()), int(tiles(na).sum()), int(tb.sum())
-    up = lambda x, dt: torch.from_numpy(np.ascontiguousarray(x).view(dt)).to(dev)
-    d_a, d_b = up(qa, np.int32), up(qb, np.int32)
-    d_aoff, d_boff = up(aoff, np.int64), up(boff, np.int64)
-    d_out = torch.empty(max(1, a_ints), dtype=torch.int32, device=dev)
-    d_counts = torch.zeros(max(1, nq), dtype=torch.int32, device=dev)
-    scratch = torch.empty(gc_intersect_scratch_size(a_ints, a_tiles, b_tiles), dtype=torch.uint8, device=dev)
-    st = new_status(dev) if status is None else status
-    gc_intersect(index, d_a, d_b, d_aoff, d_boff, nq, a_ints, a_tiles, b_tiles, d_out, d_counts, scratch, st, stream)
+
+    def up(x, dt):
+        return torch.from_numpy(np.ascontiguousarray(x).view(dt)).to(dev)
+
+    return AndBatch(qa, qb, aoff, up(qa, np.int32), up(qb, np.int32), up(aoff, np.int64), up(boff, np.int64),
+                    a_ints, a_tiles, b_tiles, int(L[qb].sum()),
+                    torch.empty(max(1, a_ints), dtype=torch.int32, device=dev),
+                    torch.zeros(max(1, nq), dtype=torch.int32, device=dev),
+                    torch.empty(gc_intersect_scratch_size(a_ints, a_tiles, b_tiles), dtype=torch.uint8, device=dev))
+
+
+def run_and_batch(index: Index, b: AndBatch, status, stream=None):
+    """gc_intersect on a prepared batch (asynchronous)."""
+    gc_intersect(index, b.d_a, b.d_b, b.d_aoff, b.d_boff, b.nqueries, b.a_ints, b.a_tiles, b.b_tiles, b.d_out,
+                 b.d_counts, b.scratch, status, stream)
+
+
+def and_batch_tiles(b: AndBatch):
+    """(a tiles decoded, b tiles decoded) of the last run (the scratch
+    header gc_intersect fills)."""
+    h = b.scratch[:32].view(torch.int64).cpu().numpy()
+    return int(h[0]), int(h[2])
+
+
+def intersect(index: Index, pairs, status=None, stream=None, check: bool = True):
+    """AND queries over a resident index: for each (i, j) in `pairs`, the
+    docIDs in both list i and list j (gc_intersect; each query's shorter list
+    is decoded whole, the other only where its skip entries allow a match).
+    Returns (results, counts, offsets): query q's docIDs are
+    results[offsets[q]:offsets[q] + counts[q]] (uint32 numpy)."""
+    b = and_batch(index, pairs)
+    st = new_status(index.data.device) if status is None else status
+    run_and_batch(index, b, st, stream)
     if check:
         check_status(st, "gc_intersect")
-    return as_u32(d_out), as_u32(d_counts[:nq]), aoff
-
+    return as_u32(b.d_out), as_u32(b.d_counts[:b.nqueries]), b.aoff
