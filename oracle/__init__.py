@@ -9,7 +9,8 @@ CUDA library.
 Every oracle function here is pinned by ``tests/test_oracle_*.py`` against
 facts that the paper or the mathematics fix (Table III, Algorithm 1 by
 brute force, Eq. 1/2 bounds, the worked examples of Sections 4.2, 5.1 and
-5.3.1, exhaustive partitions for AFOR, minimality of the PFD width).
+5.3.1, exhaustive partitions for AFOR, minimality of the PFD width, Variable
+Byte's encodings worked by hand).
 """
 from __future__ import annotations
 
@@ -85,6 +86,11 @@ def _load():
             lib.orc_tile_index.argtypes = [_U32, _U32, _U32, _U32, _u8p, _U64, _U64, ctypes.c_void_p]
             lib.orc_tile_bases.argtypes = [_u32p, _U64, _U32, ctypes.c_void_p]
             lib.orc_tile_bases.restype = None
+            lib.orc_vb_size.argtypes = [_U32]
+            lib.orc_vb_size.restype = _U32
+            lib.orc_vb_encode.argtypes = [_u32p, _U64, _u8p, _U64]
+            lib.orc_vb_encode.restype = _U64
+            lib.orc_vb_decode.argtypes = [_u8p, _U64, _U64, _u32p]
             _lib = lib
     return _lib
 
@@ -253,6 +259,35 @@ def decode(codec: Codec, ctrl, data, n: int) -> np.ndarray:
                             _p(d1, _u32p), len(d), n, _p(out, _u32p))
     if st:
         raise OracleError(st, "decode")
+    return out[:n].copy()
+
+
+def vb_size(x: int) -> int:
+    """Bytes Variable Byte takes for x (Section 2.3)."""
+    return int(_load().orc_vb_size(int(x)))
+
+
+def vb_encode(gaps) -> np.ndarray:
+    """Variable Byte (Section 2.3; lists shorter than 64, Section 7.5):
+    7-bit groups most significant first, the high bit set on each number's
+    last byte. Returns the bytes (uint8)."""
+    g = _u32(gaps)
+    out = np.zeros(max(1, 5 * len(g)), np.uint8)
+    g1 = g if len(g) else np.zeros(1, np.uint32)
+    nb = _load().orc_vb_encode(_p(g1, _u32p), len(g), _p(out, _u8p), len(out))
+    if nb == 2**64 - 1:
+        raise OracleError(ERR_NOSPACE, "vb_encode")
+    return out[:nb].copy()
+
+
+def vb_decode(data, n: int) -> np.ndarray:
+    """n ints from Variable Byte bytes (all of them used)."""
+    b = np.ascontiguousarray(data, dtype=np.uint8)
+    b1 = b if len(b) else np.zeros(1, np.uint8)
+    out = np.zeros(max(1, n), np.uint32)
+    st = _load().orc_vb_decode(_p(b1, _u8p), len(b), n, _p(out, _u32p))
+    if st:
+        raise OracleError(st, "vb_decode")
     return out[:n].copy()
 
 

@@ -21,6 +21,10 @@
  *     (Sec 6.1)
  *   - Group-PFD: per-frame b from the exception-ratio rule, exceptions stored
  *     apart at 8/16/32 bits (Sec 6.2, Steps 1-4 of encoding, 1-3 of decoding)
+ *   - Variable Byte, the code the paper keeps for posting lists shorter than
+ *     64 (Sec 2.3, Sec 7.5), in the form of the book the paper cites for it:
+ *     7-bit groups, most significant first, the high bit set on a number's
+ *     last byte
  *
  * Byte-level conventions where the paper's figures are missing (Figs 1-5):
  *   - every bit stream is LSB-first: control bit t is bit t%8 of byte t/8;
@@ -826,3 +830,61 @@ void orc_tile_bases(const uint32_t* gaps, uint64_t n, uint32_t k, orc_tile* tile
     tiles[t].flags = 1u;
   }
 }
+
+/* ------------------------------------------------------------ Variable Byte
+ * Sec 2.3: a non-negative integer in whole bytes, 7 bits of its binary
+ * representation per byte, the remaining (most significant) bit of each
+ * byte telling whether it is the number's last byte. Groups go most
+ * significant first and the last byte carries the set bit (the form of the
+ * book the paper cites). Sec 7.5 codes posting lists shorter than 64 so. */
+
+/* bytes Variable Byte takes for x: one per started group of 7 bits, at
+ * least one */
+uint32_t orc_vb_size(uint32_t x) {
+  uint32_t bytes = 1;
+  while (x >= 128u) {
+    x /= 128u;
+    bytes += 1;
+  }
+  return bytes;
+}
+
+/* encode n ints to out (capacity cap bytes); returns the bytes written, or
+ * (uint64_t)-1 when they do not fit */
+uint64_t orc_vb_encode(const uint32_t* g, uint64_t n, uint8_t* out, uint64_t cap) {
+  uint64_t pos = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint32_t x = g[i];
+    const uint32_t bytes = orc_vb_size(x);
+    if (pos + bytes > cap) return (uint64_t)-1;
+    /* group j (0 = least significant) goes to byte pos + bytes - 1 - j */
+    uint32_t v = x;
+    for (uint32_t j = 0; j < bytes; ++j) {
+      out[pos + bytes - 1 - j] = (uint8_t)(v % 128u);
+      v /= 128u;
+    }
+    out[pos + bytes - 1] |= 0x80u; /* the last byte */
+    pos += bytes;
+  }
+  return pos;
+}
+
+/* decode n ints from the first nbytes bytes of in; returns 0, or
+ * ORC_ERR_CORRUPT when the bytes end before n numbers do, a number needs
+ * more than 32 bits, or bytes are left over */
+int orc_vb_decode(const uint8_t* in, uint64_t nbytes, uint64_t n, uint32_t* out) {
+  uint64_t pos = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t v = 0;
+    for (;;) {
+      if (pos >= nbytes) return ORC_ERR_CORRUPT;
+      const uint8_t b = in[pos++];
+      v = v * 128u + (b & 0x7fu);
+      if (v > 0xffffffffull) return ORC_ERR_CORRUPT;
+      if (b & 0x80u) break;
+    }
+    out[i] = (uint32_t)v;
+  }
+  return pos == nbytes ? ORC_OK : ORC_ERR_CORRUPT;
+}
+

@@ -573,3 +573,52 @@ def test_generators_shapes():
     for i in range(500):
         d = O.prefix_sum(gaps[off[i]:off[i + 1]])
         assert (np.diff(d.astype(np.int64)) > 0).all() and (len(d) == 0 or d[-1] < 50_000_000)
+
+
+# ---------------------------------------------------------- Variable Byte
+
+def test_vb_hand_worked_encodings():
+    """Section 2.3, values worked by hand: 7-bit groups most significant
+    first, the high bit set on the last byte."""
+    cases = {
+        0: [0x80],
+        1: [0x81],
+        127: [0xFF],
+        128: [0x01, 0x80],
+        300: [0x02, 0xAC],
+        16383: [0x7F, 0xFF],
+        16384: [0x01, 0x00, 0x80],
+        2**21: [0x01, 0x00, 0x00, 0x80],
+        2**28: [0x01, 0x00, 0x00, 0x00, 0x80],
+        2**32 - 1: [0x0F, 0x7F, 0x7F, 0x7F, 0xFF],
+    }
+    for x, want in cases.items():
+        assert list(O.vb_encode([x])) == want, x
+        assert O.vb_size(x) == len(want)
+        assert O.vb_decode(np.array(want, np.uint8), 1)[0] == x
+
+
+def test_vb_stream_properties():
+    """Every number has exactly one byte with the high bit set, its last;
+    a number takes ceil(bits / 7) bytes (at least one); decoding restores
+    the sequence."""
+    g = synth.width_mix(5, 5000, 0, 32)
+    b = O.vb_encode(g)
+    last = (b & 0x80) != 0
+    assert last.sum() == len(g) and last[-1]
+    sizes = np.diff(np.concatenate(([-1], np.flatnonzero(last))))
+    want = np.maximum(1, -(-np.array([int(x).bit_length() for x in g]) // 7))
+    assert (sizes == want).all()
+    assert (O.vb_decode(b, len(g)) == g).all()
+
+
+def test_vb_rejects_malformed_streams():
+    """Bytes that end inside a number, numbers wider than 32 bits and
+    left-over bytes are reported."""
+    b = O.vb_encode([5, 300])
+    with pytest.raises(O.OracleError):
+        O.vb_decode(b[:-1], 2)
+    with pytest.raises(O.OracleError):
+        O.vb_decode(np.array([0x10, 0x00, 0x00, 0x00, 0x80], np.uint8), 1)
+    with pytest.raises(O.OracleError):
+        O.vb_decode(np.concatenate((b, [0x81])).astype(np.uint8), 2)
