@@ -367,6 +367,46 @@ gc_status gc_decode_static(const gc_codec* codec, const uint8_t* d_ctrl, uint64_
                            const uint32_t* d_data, uint64_t data_words, uint64_t n, const gc_tile* d_tiles,
                            uint32_t* d_out, int restore_docids, uint32_t* d_status, void* stream);
 
+/* ----------------------------------------------- Variable Byte lists */
+
+/* One list of Variable Byte bytes in a batch: its bytes at byte_off of the
+ * byte pool (nbytes of them), its n numbers decoding to out_off of the
+ * output. 24 bytes. */
+typedef struct {
+  uint64_t byte_off;
+  uint64_t out_off;
+  uint32_t n;
+  uint32_t nbytes;
+} gc_vb_list;
+
+/* Scratch bytes gc_vb_encode_batch needs for nlists lists. */
+gc_status gc_vb_encode_batch_scratch_size(uint64_t nlists, uint64_t* bytes);
+
+/* Variable Byte (Sec 2.3), which the paper keeps for posting lists shorter
+ * than 64 (Sec 7.5): each number in whole bytes, 7 bits per byte, most
+ * significant group first, the high bit set on the number's last byte.
+ * Encodes nlists lists at once: list i's d_n[i] gaps start at d_in_off[i]
+ * of d_gaps (the caller guarantees they lie inside it); the lists' bytes go
+ * back to back to d_bytes (bytes_cap bytes; at most 5 per number), their
+ * records to d_lists (out_off = d_in_off[i]), and the total byte count to
+ * *d_total (device). A batch larger than bytes_cap writes no list and
+ * reports GC_ERR_NOSPACE in d_status. All arguments but the sizes are
+ * device pointers; asynchronous on `stream`; the paper has no batch form. */
+gc_status gc_vb_encode_batch(const uint32_t* d_gaps, const uint64_t* d_in_off, const uint32_t* d_n, uint64_t nlists,
+                             gc_vb_list* d_lists, uint8_t* d_bytes, uint64_t bytes_cap, uint64_t* d_total,
+                             void* d_scratch, uint64_t scratch_bytes, uint32_t* d_status, void* stream);
+
+/* Decodes the nlists lists of d_lists from the byte pool d_bytes
+ * (bytes_len bytes) into d_out (out_len uint32): raw numbers, or each
+ * list's docIDs (its own prefix sum, modulo 2^32) when restore_docids. A
+ * record that points outside the pools reports GC_ERR_INVALID, a list whose
+ * bytes end inside a number, hold a number wider than 32 bits or are left
+ * over reports GC_ERR_CORRUPT (the list's list index in d_status[1]).
+ * Asynchronous on `stream`. */
+gc_status gc_vb_decode_batch(const gc_vb_list* d_lists, uint64_t nlists, const uint8_t* d_bytes, uint64_t bytes_len,
+                             uint32_t* d_out, uint64_t out_len, int restore_docids, uint32_t* d_status,
+                             void* stream);
+
 /* ------------------------------------------------------ AND queries */
 
 /* Scratch bytes gc_intersect needs: a_ints = the sum of the a lists'

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_build", "libgc.so")
 
-SOURCES = ["gc_api.cpp", "gc_decode.cu", "gc_encode.cu", "gc_index.cu", "gc_intersect.cu"]
+SOURCES = ["gc_api.cpp", "gc_decode.cu", "gc_encode.cu", "gc_index.cu", "gc_intersect.cu", "gc_vb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

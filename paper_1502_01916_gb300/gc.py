@@ -26,7 +26,8 @@ __all__ = [
     "TILE_DTYPE", "LIST_DTYPE", "WORK_DTYPE",
     "WORK_BYTES", "GcError", "gc_work", "gc_plan_batch", "gc_plan_select", "gc_decode_plan_scratch_size",
     "gc_decode_plan", "Plan", "gc_intersect_scratch_size", "gc_intersect", "intersect", "AndBatch", "and_batch",
-    "run_and_batch", "and_batch_tiles",
+    "run_and_batch", "and_batch_tiles", "VB_LIST_BYTES", "VB_LIST_DTYPE", "gc_vb_encode_batch",
+    "gc_vb_decode_batch", "MixedIndex", "encode_mixed_index", "decode_mixed",
     "plan_index",
     "gc_codec", "gc_tile", "gc_list", "gc_launch", "library_path", "load", "make_codec",
     "gc_pfd_rows_for_zeta", "gc_max_encoded_size", "gc_encode_scratch_size", "gc_encode",
@@ -148,6 +149,9 @@ def load():
             "gc_decode_plan_scratch_size": (_I, [_U64, _U64P]),
             "gc_decode_plan": (_I, [_CP, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I,
                                     ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
+            "gc_vb_encode_batch_scratch_size": (_I, [_U64, _U64P]),
+            "gc_vb_encode_batch": (_I, [_V, _V, _V, _U64, _V, _V, _U64, _V, _V, _U64, _V, _V]),
+            "gc_vb_decode_batch": (_I, [_V, _U64, _V, _U64, _V, _U64, _I, _V, _V]),
             "gc_intersect_scratch_size": (_I, [_U64, _U64, _U64, _U64P]),
             "gc_intersect": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V, _V, _U64, _U64, _U64,
                                   _U64, _V, _V, _V, _U64, _V, _V]),
@@ -679,3 +683,105 @@ def intersect(index: Index, pairs, status=None, stream=None, check: bool = True)
     if check:
         check_status(st, "gc_intersect")
     return as_u32(b.d_out), as_u32(b.d_counts[:b.nqueries]), b.aoff
+
+
+# ------------------------------------------------ Variable Byte short lists
+
+VB_LIST_BYTES = 24
+VB_LIST_DTYPE = np.dtype([("byte_off", "<u8"), ("out_off", "<u8"), ("n", "<u4"), ("nbytes", "<u4")])
+
+
+def gc_vb_encode_batch(d_gaps, d_in_off, d_n, nlists, d_lists, d_bytes, d_total, stream=None, status=None):
+    dev = d_gaps.device
+    b = _U64()
+    _check(load().gc_vb_encode_batch_scratch_size(nlists, ctypes.byref(b)), "gc_vb_encode_batch_scratch_size")
+    scratch = torch.empty(max(256, b.value), dtype=torch.uint8, device=dev)
+    st = new_status(dev) if status is None else status
+    _check(load().gc_vb_encode_batch(_ptr(d_gaps), _ptr(d_in_off), _ptr(d_n), nlists, _ptr(d_lists), _ptr(d_bytes),
+                                     d_bytes.numel(), _ptr(d_total), _ptr(scratch), scratch.numel(), _ptr(st),
+                                     _stream(stream)),
+           "gc_vb_encode_batch")
+    if status is None:
+        check_status(st, "gc_vb_encode_batch")
+
+
+def gc_vb_decode_batch(d_lists, nlists, d_bytes, d_out, restore_docids, d_status, stream=None):
+    _check(load().gc_vb_decode_batch(_ptr(d_lists), nlists, _ptr(d_bytes), d_bytes.numel(), _ptr(d_out), d_out.numel(),
+                                     int(bool(restore_docids)), _ptr(d_status), _stream(stream)),
+           "gc_vb_decode_batch")
+
+
+@dataclasses.dataclass
+class MixedIndex:
+    """An index whose lists shorter than `vb_below` are Variable Byte (the
+    paper's rule for short lists, Section 7.5) and the others a Group codec:
+    `group` holds the long lists (None when there are none), the Variable
+    Byte pools the short ones; every list decodes to its offset of one
+    output."""
+    lengths: np.ndarray       # all lists
+    out_offsets: np.ndarray   # all lists
+    vb_below: int
+    group: Index | None
+    vb_lists: torch.Tensor    # gc_vb_list records of the short lists
+    vb_bytes: torch.Tensor
+    n_short: int
+
+    @property
+    def out_ints(self) -> int:
+        if not len(self.lengths):
+            return 0
+        return int((self.out_offsets + self.lengths.astype(np.uint64)).max())
+
+    @property
+    def total_ints(self) -> int:
+        return int(self.lengths.sum(dtype=np.uint64))
+
+    def compressed_bytes(self) -> int:
+        g = self.group.compressed_bytes() if self.group is not None else 0
+        return g + self.vb_bytes.numel()
+
+
+def encode_mixed_index(codec: gc_codec, d_gaps: torch.Tensor, lengths, out_offsets=None, vb_below: int = 64,
+                       stream=None) -> MixedIndex:
+    """Encode lists shorter than vb_below with Variable Byte and the rest
+    with `codec` (encode_index); offsets as for encode_index."""
+    dev = d_gaps.device
+    L = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if out_offsets is None:
+        out_offsets = np.zeros(len(L), np.uint64)
+        if len(L) > 1:
+            np.cumsum(L[:-1], dtype=np.uint64, out=out_offsets[1:])
+    offs = np.ascontiguousarray(out_offsets, dtype=np.uint64)
+    if len(L) and int((offs + L.astype(np.uint64)).max()) > d_gaps.numel():
+        raise ValueError("a list runs past the end of d_gaps")
+    short = L < vb_below
+    group = encode_index(codec, d_gaps, L[~short], out_offsets=offs[~short], stream=stream) if (~short).any() else None
+    ns = int(short.sum())
+    d_lists = torch.empty(max(1, ns) * VB_LIST_BYTES, dtype=torch.uint8, device=dev)
+    cap = 5 * int(L[short].sum(dtype=np.uint64))
+    d_bytes = torch.empty(max(16, cap), dtype=torch.uint8, device=dev)
+    d_total = torch.zeros(1, dtype=torch.int64, device=dev)
+    if ns:
+        up = lambda x, dt: torch.from_numpy(np.ascontiguousarray(x).view(dt)).to(dev)
+        gc_vb_encode_batch(d_gaps, up(offs[short], np.int64), up(L[short], np.int32), ns, d_lists, d_bytes, d_total,
+                           stream)
+    nb = int(d_total.item())
+    return MixedIndex(L, offs, vb_below, group, d_lists, d_bytes[:max(1, nb)] if ns else d_bytes[:0], ns)
+
+
+def decode_mixed(mi: MixedIndex, out: torch.Tensor | None = None, restore_docids: bool = True, plan=None,
+                 status=None, check: bool = True, stream=None, launch=None) -> torch.Tensor:
+    """Decode every list of a mixed index into one output (two launches
+    after the plan: the Group decoder and the Variable Byte decoder)."""
+    dev = mi.vb_bytes.device
+    out = torch.empty(max(1, mi.out_ints), dtype=torch.int32, device=dev) if out is None else out
+    st = new_status(dev) if status is None else status
+    if mi.group is not None:
+        decode_index(mi.group, out=out, restore_docids=restore_docids, status=st, check=False, stream=stream,
+                     plan=plan, launch=launch)
+    if mi.n_short:
+        gc_vb_decode_batch(mi.vb_lists, mi.n_short, mi.vb_bytes, out, restore_docids, st, stream)
+    if check:
+        check_status(st, "decode_mixed")
+    return out
+

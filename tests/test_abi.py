@@ -143,3 +143,14 @@ def test_intersect_validates_on_the_host(gc):
     s1 = gc.gc_intersect_scratch_size(1000, 2, 10)
     s2 = gc.gc_intersect_scratch_size(100000, 200, 1000)
     assert 0 < s1 < s2
+
+
+def test_vb_batch_validates_on_the_host(gc):
+    """gc_vb_decode_batch / gc_vb_encode_batch: empty batches are no-ops,
+    missing buffers are refused, before any device call."""
+    lib = gc.load()
+    assert lib.gc_vb_decode_batch(None, 0, None, 0, None, 0, 1, None, None) == 0
+    assert lib.gc_vb_decode_batch(None, 3, None, 0, None, 0, 1, None, None) == 1
+    assert lib.gc_vb_encode_batch(None, None, None, 3, None, None, 0, None, None, 0, None, None) == 1
+    b = ctypes.c_uint64()
+    assert lib.gc_vb_encode_batch_scratch_size(5000, ctypes.byref(b)) == 0 and b.value >= 5000 * 8

@@ -1,0 +1,95 @@
+"""Variable Byte for short lists (Sec 2.3, Sec 7.5) on the GPU against the
+oracle: the batch encoder's bytes equal the oracle's, list by list; the
+batch decoder restores gaps and docIDs; an index whose short lists are
+Variable Byte decodes every list to its prefix sums and is smaller than the
+same index with Group codecs alone in the short-list regime."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_1502_01916_gb300 import build
+    build.build()
+    import paper_1502_01916_gb300 as gc
+    return gc
+
+
+def short_lists(seed, nlists=3000):
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, 64, size=nlists).astype(np.uint32)
+    lens[:4] = [0, 1, 63, 2]
+    g = synth.width_mix(seed, int(lens.sum()), 0, 32)
+    off = np.zeros(nlists + 1, np.uint64)
+    np.cumsum(lens, out=off[1:])
+    return lens, g, off
+
+
+def test_vb_batch_matches_oracle(gc):
+    lens, g, off = short_lists(3)
+    dev = torch.device("cuda")
+    d_gaps = torch.from_numpy(g.view(np.int32)).to(dev)
+    d_lists = torch.empty(len(lens) * gc.VB_LIST_BYTES, dtype=torch.uint8, device=dev)
+    d_bytes = torch.empty(5 * len(g), dtype=torch.uint8, device=dev)
+    d_total = torch.zeros(1, dtype=torch.int64, device=dev)
+    d_off = torch.from_numpy(off[:-1].view(np.int64)).to(dev)
+    d_n = torch.from_numpy(lens.view(np.int32)).to(dev)
+    gc.gc_vb_encode_batch(d_gaps, d_off, d_n, len(lens), d_lists, d_bytes, d_total)
+    recs = d_lists.cpu().numpy().view(gc.VB_LIST_DTYPE)
+    pool = d_bytes.cpu().numpy()
+    total = int(d_total.item())
+    want_total = 0
+    for i in range(len(lens)):
+        want = O.vb_encode(g[off[i]:off[i + 1]])
+        r = recs[i]
+        assert int(r["n"]) == lens[i] and int(r["out_off"]) == int(off[i]) and int(r["nbytes"]) == len(want)
+        assert (pool[int(r["byte_off"]):int(r["byte_off"]) + len(want)] == want).all(), i
+        want_total += len(want)
+    assert total == want_total
+    for restore in (False, True):
+        out = torch.full((len(g) + 1,), -1, dtype=torch.int32, device=dev)
+        st = gc.new_status(dev)
+        gc.gc_vb_decode_batch(d_lists, len(lens), d_bytes[:total], out, restore, st)
+        gc.check_status(st, "vb decode")
+        got = gc.as_u32(out)
+        for i in range(len(lens)):
+            seg = g[off[i]:off[i + 1]]
+            want = O.prefix_sum(seg) if restore else seg
+            assert (got[int(off[i]):int(off[i + 1])] == want).all(), (i, restore)
+
+
+@pytest.mark.parametrize("kind", [O.SIMPLE, O.PFD])
+def test_mixed_index_short_lists(gc, kind):
+    """Clustered short lists (config 4's recipe at 60,000 lists): lists under
+    64 as Variable Byte, the rest with a Group codec at k = 32."""
+    maxlen = synth.lognormal_lengths(9, 60_000, 12.0, 1.5, 1 << 16)
+    gaps, off, lens = synth.clustered_index(10, maxlen, 50_000_000, 16.0, 5000.0)
+    dev = torch.device("cuda")
+    d_gaps = torch.from_numpy(gaps.view(np.int32)).to(dev)
+    codec = gc.make_codec(kind, 32, zeta=0.1)
+    mi = gc.encode_mixed_index(codec, d_gaps, lens, vb_below=64)
+    assert mi.n_short == int((lens < 64).sum()) > 0
+    out = gc.as_u32(gc.decode_mixed(mi))
+    for i in range(len(lens)):
+        a, b = int(off[i]), int(off[i + 1])
+        assert (out[a:b] == O.prefix_sum(gaps[a:b])).all(), i
+    whole = gc.encode_index(codec, d_gaps, lens)
+    assert mi.compressed_bytes() < whole.compressed_bytes()
+
+
+def test_vb_corrupt_list_reported(gc):
+    lens, g, off = short_lists(5, 50)
+    dev = torch.device("cuda")
+    mi = gc.encode_mixed_index(gc.make_codec(O.SIMPLE, 32), torch.from_numpy(g.view(np.int32)).to(dev), lens)
+    b = mi.vb_bytes.clone()
+    b[:] = b & 0x7F  # no number ends: every list runs out of bytes
+    mi.vb_bytes = b
+    with pytest.raises(gc.GcError) as ei:
+        gc.decode_mixed(mi)
+    assert ei.value.code == 3
