@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the TF-stream and zeta = 0 decodes")
     p.add_argument("--no-and", action="store_true", help="skip the AND-query measurement")
+    p.add_argument("--no-short", action="store_true", help="skip the short-list (Variable Byte rule) measurement")
     p.add_argument("--and-queries", type=int, default=4000, help="two-list AND queries in the timed batch")
     p.add_argument("--serve-seconds", type=float, default=0.5, help="trace length per request rate")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work budget per codec")
@@ -482,6 +483,12 @@ def main():
         sn = "pfd" if "pfd" in idxs else next(iter(idxs))
         and_q = and_query_rates(gc, idxs[sn], lengths, off, gaps, dev, a.and_queries)
 
+    # the clustered short-list index with and without Variable Byte for
+    # lists shorter than 64
+    short = None
+    if not a.no_short:
+        short = short_list_rates(gc, dev)
+
     # TF streams and Group-PFD without exceptions (BP128's fixed-width frames),
     # after the timed region
     extras = None
@@ -513,7 +520,7 @@ def main():
                    "autotuned": tuned or None,
                    "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},
         "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list, "serving": serving,
-        "extras": extras, "and_queries": and_q,
+        "extras": extras, "and_queries": and_q, "short_lists": short,
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(sum(launches.values()) * a.steps),
         "verified_full_output": verified, "setup_s": {"generate": t_gen, "encode": t_enc},
@@ -578,6 +585,66 @@ def extra_rates(gc, lengths, off, gaps, dev, peak, reps=5, nsample=300, seed=5):
                                                               dtype=np.uint32))
         del idx
     del d
+    torch.cuda.empty_cache()
+    return res
+
+
+def short_list_rates(gc, dev, reps=5, nsample=300, seed=17):
+    """The clustered short-list index (4M lists over 50M documents,
+    log-normal lengths with median 12, clustered docIDs; 87% of the lists
+    shorter than 64), encoded with Group-PFD and with Group-Scheme at byte
+    granularity (incomplete unary), each alone and with the paper's rule for
+    short lists (Variable Byte below 64 postings, Sec 7.5): compressed bits
+    per int and the decode time of the whole index (CUDA events; the plan of
+    the Group part built beforehand), checked on a sample of lists."""
+    import torch
+    import synth
+    gaps, off, lens = synth.clustered_short_index()
+    total = int(lens.sum(dtype=np.uint64))
+    d = torch.from_numpy(gaps.view(np.int32)).to(dev)
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(len(lens), min(nsample, len(lens)), replace=False)
+    out = torch.empty(max(1, total), dtype=torch.int32, device=dev)
+    st = gc.new_status(dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        gc.check_status(st, "short lists")
+        got = gc.as_u32(out)
+        ok = all(np.array_equal(got[int(off[i]):int(off[i + 1])],
+                                np.cumsum(gaps[int(off[i]):int(off[i + 1])], dtype=np.uint32)) for i in ids)
+        return float(np.median(ts)), ok
+
+    res = {"lists": int(len(lens)), "ints": total, "short_share": float((lens < 64).mean())}
+    for name, kind, kw in (("pfd", 3, {"zeta": 0.10}), ("scheme_iu_cg8", 1, {"cg": 8, "ld": gc.LD_IU})):
+        codec = gc.make_codec(kind, 32, **kw)
+        idx = gc.encode_index(codec, d, lens)
+        plan = gc.plan_index(idx)
+        scratch = torch.empty(gc.gc_decode_plan_scratch_size(idx.max_tiles), dtype=torch.uint8, device=dev)
+        ms, ok = timed(lambda: gc.decode_index(idx, out=out, scratch=scratch, status=st, plan=plan, check=False))
+        res[name] = {"bits_per_int": 8.0 * (idx.compressed_bytes() + idx.index_bytes()) / total, "ms": ms,
+                     "ints_per_s": total / (ms / 1e3), "sample_verified": ok}
+        del idx, plan, scratch
+        mi = gc.encode_mixed_index(codec, d, lens, vb_below=64)
+        mplan = gc.plan_index(mi.group)
+        ms, ok = timed(lambda: gc.decode_mixed(mi, out=out, status=st, plan=mplan, check=False))
+        gbytes = mi.group.compressed_bytes() + mi.group.index_bytes()
+        res[name + "_vb_below_64"] = {
+            "bits_per_int": 8.0 * (gbytes + mi.vb_bytes.numel() + 24 * mi.n_short) / total, "ms": ms,
+            "ints_per_s": total / (ms / 1e3), "sample_verified": ok, "vb_lists": mi.n_short}
+        del mi, mplan
+        torch.cuda.empty_cache()
+    del d, out
     torch.cuda.empty_cache()
     return res
 
