@@ -420,8 +420,13 @@ def main():
                 "frac": per_codec[dom]["frac"], "traffic": traffic, "peak_source": peak_src,
                 "timed_as": "graph launch (memset of the queue counter and look-back words + decode kernel)"}
 
-    # end to end through the C ABI with host buffers: pinned index pools in,
-    # docIDs out, every step
+    # end to end through the C ABI with host buffers: every step copies each
+    # codec's plan and pools in from pinned host memory, decodes, and copies
+    # its docIDs out to pinned host memory. The steps are pipelined as a
+    # caller would: one stream copies in, one decodes, one copies out (the
+    # host link carries both directions at once); a codec's pools are copied
+    # again only after the kernel that read them, and its output is decoded
+    # into again only after it was copied out.
     e2e = None
     if not a.no_e2e:
         host = {}
@@ -433,16 +438,48 @@ def main():
                 h.copy_(p)
                 h2d += p.numel() * p.element_size()
             host[n] = (hp, pools)
-        h_out = torch.empty(out_len, dtype=torch.int32, pin_memory=True)
         d2h = 4 * out_len * len(idxs)
+        dout = {n: torch.empty(out_len, dtype=torch.int32, device=dev) for n in idxs}
+        hout = {n: torch.empty(out_len, dtype=torch.int32, pin_memory=True) for n in idxs}
+        s_in, s_dec, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
+        g_e2e = {}
+        for n, idx in idxs.items():
+            with torch.cuda.stream(s_dec):
+                gc.decode_index(idx, out=dout[n], scratch=scratch[n], status=status[n], launch=launches_cfg[n],
+                                check=False, plan=plans[n])
+            s_dec.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s_dec, capture_error_mode="relaxed"):
+                gc.decode_index(idx, out=dout[n], scratch=scratch[n], status=status[n], launch=launches_cfg[n],
+                                check=False, plan=plans[n])
+            g_e2e[n] = g
+        torch.cuda.synchronize()
+        k_done, o_done = {n: None for n in idxs}, {n: None for n in idxs}
 
         def e2e_step():
             for n in idxs:
                 hp, pools = host[n]
-                for h, p in zip(hp, pools):
-                    p.copy_(h, non_blocking=True)
-                graphs[n].replay()
-                h_out.copy_(out, non_blocking=True)
+                if k_done[n] is not None:
+                    s_in.wait_event(k_done[n])
+                with torch.cuda.stream(s_in):
+                    for h, p in zip(hp, pools):
+                        p.copy_(h, non_blocking=True)
+                e_in = torch.cuda.Event()
+                e_in.record(s_in)
+                s_dec.wait_event(e_in)
+                if o_done[n] is not None:
+                    s_dec.wait_event(o_done[n])
+                with torch.cuda.stream(s_dec):
+                    g_e2e[n].replay()
+                e_k = torch.cuda.Event()
+                e_k.record(s_dec)
+                k_done[n] = e_k
+                s_out.wait_event(e_k)
+                with torch.cuda.stream(s_out):
+                    hout[n].copy_(dout[n], non_blocking=True)
+                e_o = torch.cuda.Event()
+                e_o.record(s_out)
+                o_done[n] = e_o
 
         for _ in range(max(1, a.warmup)):
             e2e_step()
@@ -450,9 +487,15 @@ def main():
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(cur)
+        for st_ in (s_in, s_dec, s_out):
+            st_.wait_event(f0)
         ksteps = max(1, min(a.steps, 5))
         for _ in range(ksteps):
             e2e_step()
+        for st_ in (s_in, s_dec, s_out):
+            e = torch.cuda.Event()
+            e.record(st_)
+            cur.wait_event(e)
         f1.record(cur)
         torch.cuda.synchronize()
         barrier()
@@ -461,10 +504,26 @@ def main():
             t = torch.tensor([ems], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
-        e2e = {"value": ints_per_step * ksteps * world / (ems / 1e3), "unit": "ints/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ksteps}
         for n in idxs:
             gc.check_status(status[n], f"e2e decode {n}")
+        # each direction alone, for context: one codec's pools in, one output out
+        n0 = next(iter(idxs))
+        c0, c1, c2, c3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        c0.record(cur)
+        for h, p in zip(*host[n0]):
+            p.copy_(h, non_blocking=True)
+        c1.record(cur)
+        c2.record(cur)
+        hout[n0].copy_(dout[n0], non_blocking=True)
+        c3.record(cur)
+        torch.cuda.synchronize()
+        in_b = sum(p.numel() * p.element_size() for p in host[n0][1])
+        e2e = {"value": ints_per_step * ksteps * world / (ems / 1e3), "unit": "ints/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ksteps,
+               "pipelined": "copy-in, decode and copy-out streams",
+               "h2d_gbs_alone": in_b / (c0.elapsed_time(c1) / 1e3) / 1e9,
+               "d2h_gbs_alone": 4 * out_len / (c2.elapsed_time(c3) / 1e3) / 1e9}
+        del dout, hout, host, g_e2e
 
     # one launch per list (gc_decode on each list of a sample)
     per_list = None
