@@ -50,6 +50,7 @@ constexpr int kExcCap = 1024;   // exception bytes staged per tile (all or none)
 static_assert(kFly == kSeq, "a claimed record's staging slot is its record slot");
 
 constexpr int kPadVec = 34;     // k = 32: data vectors of a pack, re-laid at 33 words each
+constexpr int kPadVec4 = 272;   // k = 4: data vectors of a pack, re-laid at 4 words each plus one per 8
 constexpr int kPad = 33;        // words per re-laid vector (one bank apart per vector)
 
 template <int K>
@@ -60,7 +61,7 @@ struct Geo {
   static constexpr int MAXVEC = TR + 1;      // data vectors a tile spans at most
   // k = 32: the pack's data re-laid at 33 words per vector; k = 4: a 32 x 32
   // transpose buffer
-  static constexpr int TBW = K == 32 ? kPadVec * kPad : 32 * 32;
+  static constexpr int TBW = K == 32 ? kPadVec * kPad : 4 * kPadVec4 + kPadVec4 / 8;
 
 };
 
@@ -83,9 +84,6 @@ struct __align__(128) WarpSmem {
   uint32_t irec[32];                     // its record slot | first re-laid vector << 8
   uint32_t rw[Geo<K>::PROWS];            // row: ring word of its first word (lane 0)
   uint32_t rs[Geo<K>::PROWS];            // row: shift | width << 8
-  uint32_t xm[32];                       // line: Group-PFD exception slots
-  uint32_t xw[32];                       // line: exception value bytes
-  unsigned long long xv[32];             // line: generic address of its frame's values
   unsigned long long lout[32];           // line: output index of its first int
   uint32_t lnv[32];                      // line: ints it holds
 };
@@ -423,91 +421,96 @@ __device__ __forceinline__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit,
   return __all_sync(kFull, ok);
 }
 
-// Group-PFD decoding Step 1: per 32-row frame the header (b, exception
-// width code, exception count e); the frames' exception records follow the
-// headers of the whole list, frame after frame, and the tile's first one is
-// at exc_at. Rows go to the sink; every exception sets its slot's bit in the
-// mask of its line, and each line gets the address of its frame's values.
-template <int K>
-__device__ __forceinline__ bool parse_pfd(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows, const RowSink<K>& out,
-                          WarpSmem<K>& ws, uint32_t line0, uint32_t nlines, uint32_t* xdst = nullptr,
-                          uint32_t xroom = 0, uint32_t* xtotal = nullptr) {
-  constexpr uint32_t pb = (kPfdFrameRows * K) <= 256 ? 1u : 2u;
-  constexpr uint32_t LPF = K;  // lines per frame (32 rows of K ints)
+// Group-PFD at k = 4, decoding Step 1: per 32-row frame (128 ints) the
+// header (b, exception width code, exception count e); the tile's frames'
+// exception records follow one another from exc_at (e 8-bit positions, then
+// e values of wb bytes). Rows go to the sink; every header and record is
+// checked to lie inside the list (the exceptions themselves are patched in
+// after the rows are decoded, pfd_patch4).
+__device__ __forceinline__ bool parse_pfd4(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows,
+                                           const RowSink<4>& out) {
   const uint32_t lane = lane_id();
   const uint32_t nfr = (rows + kPfdFrameRows - 1) / kPfdFrameRows;
   bool ok = true;
-  uint32_t b = 0, wcode = 0, e = 0, xb = 0, frows = 0;
+  uint32_t b = 0, xb = 0;
   if (lane < nfr) {
     const uint64_t f = f0 + lane;
     if (4 * f + 4 > C.size) ok = false;
-    const uint32_t hdr = C.le(4 * f, 4);
+    const uint32_t hdr = ok ? C.le(4 * f, 4) : 0u;
     b = hdr & 63u;
-    wcode = (hdr >> 6) & 3u;
-    e = hdr >> 8;
+    const uint32_t wcode = (hdr >> 6) & 3u;
+    uint32_t e = hdr >> 8;
     if (b > 32 || wcode > 2) {
       ok = false;
       b = 0;
       e = 0;
-      wcode = 0;
     }
-    frows = rows - 32 * lane < 32 ? rows - 32 * lane : 32;
-    if (e > frows * K) {
+    const uint32_t frows = rows - 32 * lane < 32 ? rows - 32 * lane : 32;
+    if (e > frows * 4) {
       ok = false;
       e = 0;
     }
-    xb = e * (pb + (1u << wcode));
+    xb = e * (1u + (1u << wcode));
   }
   const uint64_t xrec0 = exc_at + (warp_incl_sum(xb) - xb);
-  if (lane < nfr && e && xrec0 + xb > C.size) {
-    ok = false;
-    e = 0;
-    xb = 0;
-  }
+  if (lane < nfr && xb && xrec0 + xb > C.size) ok = false;
   const uint32_t inclL = warp_incl_sum(32u * b);
   const uint32_t lstart = inclL - 32u * b;
-  const uint32_t inclE = warp_incl_sum(e);
-  const uint32_t etot = __shfl_sync(kFull, inclE, 31);
-  const bool expand = xdst != nullptr && etot <= xroom;
-  if (xtotal) *xtotal = expand ? etot : 0xffffffffu;
   for (uint32_t fl = 0; fl < nfr; ++fl) {
     const uint32_t bf = __shfl_sync(kFull, b, fl);
     const uint32_t ls = __shfl_sync(kFull, lstart, fl);
     const uint32_t q = fl * 32 + lane;
     if (q < rows) out.put(q, ls + lane * bf, bf, ok);
   }
+  return __all_sync(kFull, ok);
+}
+
+// Group-PFD at k = 4, decoding Step 3: every exception of a tile's frames
+// overwrites its slot in the pack's line-major buffer (line l at words
+// 32 l .., 16-byte chunk c at chunk c ^ (l & 7)); the tile's first line is
+// line0. Headers and records were checked by parse_pfd4; a position
+// outside its frame is reported.
+__device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, WarpSmem<4>& ws, const CtrlView& C, uint64_t f0,
+                                           uint64_t exc_at, uint32_t rows, uint32_t line0, uint32_t list) {
+  const uint32_t lane = lane_id();
+  const uint32_t nfr = (rows + kPfdFrameRows - 1) / kPfdFrameRows;
+  uint32_t e = 0, wb = 1, xb = 0, lim = 0;
+  if (lane < nfr) {
+    const uint64_t f = f0 + lane;
+    const uint32_t hdr = 4 * f + 4 <= C.size ? C.le(4 * f, 4) : 0u;
+    const uint32_t wcode = (hdr >> 6) & 3u;
+    const uint32_t frows = rows - 32 * lane < 32 ? rows - 32 * lane : 32;
+    lim = frows * 4;
+    e = hdr >> 8;
+    if ((hdr & 63u) > 32 || wcode > 2 || e > lim) e = 0;
+    wb = 1u << wcode;
+    xb = e * (1u + wb);
+  }
+  const uint64_t rec = exc_at + (warp_incl_sum(xb) - xb);
+  if (lane < nfr && xb && rec + xb > C.size) e = 0;
   for (uint32_t fl = 0; fl < nfr; ++fl) {
     const uint32_t ef = __shfl_sync(kFull, e, fl);
-    const uint32_t lim = __shfl_sync(kFull, frows, fl) * K;
-    const uint64_t rec = __shfl_sync(kFull, xrec0, fl);
-    const uint32_t wb = 1u << __shfl_sync(kFull, wcode, fl);
-    const uint32_t xs = __shfl_sync(kFull, inclE - e, fl);  // exceptions of the tile before this frame
-    // the frame's record: ef positions, then ef values (all inside the list)
-    const uint8_t* rp = C.addr(rec, (uint64_t)ef * (pb + wb));
-    const uint8_t* vp = rp + (size_t)ef * pb;
+    if (ef == 0) continue;
+    const uint32_t wbf = __shfl_sync(kFull, wb, fl);
+    const uint32_t limf = __shfl_sync(kFull, lim, fl);
+    const uint64_t rf = __shfl_sync(kFull, rec, fl);
+    const uint8_t* rp = C.addr(rf, (uint64_t)ef * (1 + wbf));
+    const uint8_t* vp = rp + ef;
     for (uint32_t x = lane; x < ef; x += 32) {
-      const uint32_t pos = pb == 1 ? (uint32_t)rp[x] : ((uint32_t)rp[2 * x] | ((uint32_t)rp[2 * x + 1] << 8));
-      if (pos >= lim) {
-        ok = false;
+      const uint32_t pos = rp[x];
+      if (pos >= limf) {
+        report(a.status, GC_ERR_CORRUPT, list);
         continue;
       }
-      const uint32_t i = fl * kPfdFrameRows * K + pos;  // tile-relative int
-      atomicOr(&ws.xm[line0 + (i >> 5)], 1u << (i & 31u));
-      if (expand) {
-        const uint8_t* q = vp + (size_t)x * wb;
-        uint32_t v = q[0];
-        if (wb > 1) v |= (uint32_t)q[1] << 8;
-        if (wb > 2) v |= ((uint32_t)q[2] << 16) | ((uint32_t)q[3] << 24);
-        xdst[xs + x] = v;
-      }
-    }
-    const uint32_t ql = fl * LPF + lane;
-    if (lane < LPF && ql < nlines) {
-      ws.xv[line0 + ql] = (unsigned long long)vp;
-      ws.xw[line0 + ql] = wb;
+      const uint8_t* v8 = vp + (size_t)x * wbf;
+      uint32_t v = v8[0];
+      if (wbf > 1) v |= (uint32_t)v8[1] << 8;
+      if (wbf > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
+      const uint32_t i = fl * 128 + pos;  // int of the tile
+      const uint32_t line = line0 + (i >> 5), col = i & 31u;
+      ws.tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
     }
   }
-  return __all_sync(kFull, ok);
 }
 
 // ------------------------------------------------------------ look-back
@@ -578,52 +581,74 @@ __device__ __forceinline__ bool w_live(const gc_work& w, const DecodeArgs& a) {
          w.data_at % K == 0 && w.data_at + (uint64_t)vecs * K <= a.data_pool_words;
 }
 
-// Decode the pack of records s0 .. s0 + np - 1 of this warp's sequence
-// (staged, their mbarriers complete), `nl` lines in all.
-template <int KIND, int K, bool RESTORE>
-__device__ void decode_pack(const DecodeArgs& a, WarpSmem<K>& ws, uint32_t s0, uint32_t np, uint32_t nl) {
-  constexpr uint32_t RPL = Geo<K>::RPL;
+// The k = 4 pack decoder (the paper's own layout): records s0 .. s0 + np - 1
+// of this warp's sequence (staged, their mbarriers complete), `nl` lines
+// in all. Each staged tile's 16-byte vectors are re-laid in shared memory,
+// vector v of the pack at word 4 v + v / 8 (one spare word per 8 vectors,
+// so that lanes reading different rows mostly hit different banks); every
+// tile's control patterns become one (vector, shift, width) entry per row;
+// lane l then reads line l (32 ints: rows 8 l .. 8 l + 7 of the pack, 4
+// components each) in natural order. Group-PFD exceptions are patched into
+// the line-major buffer before the running sum.
+template <int KIND, bool RESTORE>
+__device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, uint32_t np, uint32_t nl,
+                             uint32_t lv, uint32_t lvi) {
+  constexpr uint32_t RPL = Geo<4>::RPL;  // rows per line (8)
   const uint32_t lane = lane_id();
 
-  // per-item facts, item p in lane p
-  uint32_t my_line0 = 0, my_lines = 0, my_nint = 0, my_item = 0, my_tile = 0, my_base = 0, my_shape = 0;
-  uint32_t my_list = 0xffffffffu;
-  bool my_dead = false;  // a non-empty record that cannot be decoded
-  {
-    uint32_t l0 = 0;
-    for (uint32_t p = 0; p < np; ++p) {
-      const gc_work& w = rec_at(ws.rec, s0 + p);
-      const bool live = w_live<K>(w, a);
-      const uint32_t lines = live ? (w_nint(w.shape) + 31) / 32 : 0;
-      if (lane == p) {
-        my_line0 = l0;
-        my_lines = lines;
-        my_nint = live ? w_nint(w.shape) : 0;
-        my_item = ws.item[(s0 + p) % kSeq];
-        my_tile = w.tile;
-        my_base = w.base;
-        my_shape = w.shape;
-        my_list = live ? w.list : 0xffffffffu;
-        my_dead = !live && w.list != 0xffffffffu;
-      }
-      l0 += lines;
-    }
+  // items: lane p < np holds item p, its lines and vectors (lv: lines |
+  // vectors << 16) and their inclusive sums over the pack (lvi)
+  const uint32_t my_lines = lv & 0xffffu;
+  const uint32_t my_vecs = lv >> 16;
+  const uint32_t my_line0 = (lvi & 0xffffu) - my_lines;
+  const uint32_t my_vec0 = (lvi >> 16) - my_vecs;
+  const bool my_live = my_lines > 0;
+  const uint32_t live = __ballot_sync(kFull, my_live);
+  const uint32_t heads = np == 1 ? (live & 1u) : __reduce_or_sync(kFull, my_live ? 1u << my_line0 : 0u);
+  uint32_t my_item = 0, my_tile = 0, my_base = 0, my_shape = 0, my_list = 0xffffffffu;
+  uint64_t my_out = 0;
+  if (lane < np) {
+    const gc_work& w = rec_at(ws.rec, s0 + lane);
+    my_item = ws.item[(s0 + lane) % kSeq];
+    my_tile = w.tile;
+    my_base = w.base;
+    my_shape = w.shape;
+    my_list = w.list;
+    my_out = w.out_at;
   }
-  if (KIND == GC_PFD) ws.xm[lane] = 0;
-  __syncwarp();
+  const bool my_dead = lane < np && !my_live && my_list != 0xffffffffu;
+  const uint32_t my_rank = __popc(live & ((1u << lane) - 1u));
+  if (my_live) {
+    ws.iout[my_rank] = my_out;
+    ws.inint[my_rank] = w_nint(my_shape);
+  }
 
-  // 1. control patterns -> row entries
-  bool all_ok = true;
-  for (uint32_t p = 0; p < np; ++p) {
-    const uint32_t lines = __shfl_sync(kFull, my_lines, p);
-    if (lines == 0) continue;
+  // 1. per tile: re-lay its vectors, and turn its control patterns into one
+  // (vector, shift, width) entry per row
+  for (uint32_t lm = live; lm; lm &= lm - 1) {
+    const uint32_t p = __ffs(lm) - 1;
     const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
-    const uint32_t nint = __shfl_sync(kFull, my_nint, p);
+    const uint32_t lines = __shfl_sync(kFull, my_lines, p);
+    const uint32_t v0 = __shfl_sync(kFull, my_vec0, p);
     const gc_work& w = rec_at(ws.rec, s0 + p);
     const uint32_t f = (s0 + p) % kFly;
     const uint32_t at = ws.at[f];
-    const uint32_t vecs = w_vecs(w.shape);
-    const uint32_t dbytes = vecs * K * 4;
+    const uint32_t vecs = ws.fvecs[f];
+    {
+      // lane l moves vector 32 i + l (one 16-byte load, four stores; the
+      // stores of a step hit 32 different banks)
+      const uint4* src = reinterpret_cast<const uint4*>(ws.ring + at);
+      for (uint32_t v = lane; v < vecs; v += 32) {
+        const uint4 x = src[v];
+        const uint32_t g = v0 + v;
+        uint32_t* d = ws.tb + 4 * g + (g >> 3);
+        d[0] = x.x;
+        d[1] = x.y;
+        d[2] = x.z;
+        d[3] = x.w;
+      }
+    }
+    const uint32_t dbytes = vecs * 16;
     CtrlView C;
     C.g = a.ctrl_pool + w.ctrl_at;
     C.size = w.ctrl_bytes;
@@ -633,204 +658,209 @@ __device__ void decode_pack(const DecodeArgs& a, WarpSmem<K>& ws, uint32_t s0, u
     C.s2 = ws.ring + at + dbytes + ws.cst[f];
     C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
     C.len2 = ws.xst[f];
-    RowSink<K> out;
+    RowSink<4> out;
     out.rw = ws.rw + line0 * RPL;
     out.rs = ws.rs + line0 * RPL;
-    out.word0 = at / 4;
-    out.stride = K;
+    out.word0 = v0;  // entries hold the row's first vector
+    out.stride = 1;
     out.bit0 = w_bit0(w.shape);
     out.vec_bits = 32 * vecs;
-    const uint32_t rows = (nint + K - 1) / K;
-    const uint64_t row0 = (uint64_t)w.tile * Geo<K>::TR;
+    const uint32_t rows = (w_nint(w.shape) + 3) / 4;
+    const uint64_t row0 = (uint64_t)w.tile * Geo<4>::TR;
     bool ok;
     if (KIND == GC_SIMPLE) {
-      ok = parse_simple<K>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
+      ok = parse_simple<4>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
     } else if (KIND == GC_SCHEME) {
-      if (a.ld == GC_LD_BINARY) ok = parse_scheme_binary<K>(C, row0, rows, a.cg, out);
-      else ok = parse_scheme_unary<K>(C, w.ctrl_bit, rows, a.cg, a.ld == GC_LD_IU, out);
+      if (a.ld == GC_LD_BINARY) ok = parse_scheme_binary<4>(C, row0, rows, a.cg, out);
+      else ok = parse_scheme_unary<4>(C, w.ctrl_bit, rows, a.cg, a.ld == GC_LD_IU, out);
     } else if (KIND == GC_AFOR) {
-      ok = parse_afor<K>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
+      ok = parse_afor<4>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
     } else {
-      ok = parse_pfd<K>(C, row0 / kPfdFrameRows, w.exc_at, rows, out, ws, line0, lines);
+      ok = parse_pfd4(C, row0 / kPfdFrameRows, w.exc_at, rows, out);
     }
     // rows of the last line past the tile's end read nothing
-    if (lane < lines * RPL - rows && RPL > 1) {
-      ws.rw[line0 * RPL + rows + lane] = at / 4;
+    if (lane < lines * RPL - rows) {
+      ws.rw[line0 * RPL + rows + lane] = v0;
       ws.rs[line0 * RPL + rows + lane] = 0;
     }
-    if (!ok) {
-      if (lane == 0) report(a.status, GC_ERR_CORRUPT, w.list);
-      all_ok = false;
-    }
+    if (!ok && lane == 0) report(a.status, GC_ERR_CORRUPT, w.list);
   }
-  (void)all_ok;
   __syncwarp();
 
-  // 2. lane l decodes line l: its item p_l (the last live item whose first
-  // line is at or before l) and q, the line within that item
+  // 2. lane l reads line l: rows 8 l .. 8 l + 7, four components each
   const bool act = lane < nl;
-  uint32_t p_l = 0, lhead = 0;
-  for (uint32_t p = 0; p < np; ++p) {
-    const uint32_t lines = __shfl_sync(kFull, my_lines, p);
-    const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
-    if (lines && line0 <= lane) {
-      p_l = p;
-      lhead = line0;
-    }
-  }
-  const uint32_t q = lane - lhead;  // line of the item
-  const uint32_t nint_l = __shfl_sync(kFull, my_nint, p_l);
-  uint32_t nv = 0;
-  if (act) nv = nint_l - 32 * q < 32 ? nint_l - 32 * q : 32;
-
-  uint32_t xmask = 0, xfirst = 0, xwb = 1;
-  const uint8_t* xvals = nullptr;
-  if (KIND == GC_PFD) {
-    xmask = act ? ws.xm[lane] : 0;
-    // exceptions before this line in its frame (K lines per frame)
-    const bool fhead = (q % K) == 0;
-    uint32_t cnt = __popc(xmask);
-    uint32_t v = cnt;
-    bool f = fhead || !act;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, v, o);
-      const bool g = __shfl_up_sync(kFull, f, o);
-      if (lane >= (uint32_t)o && !f) {
-        v += y;
-        f = g;
-      }
-    }
-    xfirst = v - cnt;
-    if (xmask) {
-      xvals = reinterpret_cast<const uint8_t*>(ws.xv[lane]);
-      xwb = ws.xw[lane];
-    }
-  }
-
-  // 3. extract in rotated column order: step c reads column (c + l) % 32
+  const uint32_t upto = heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
+  const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;  // its item among the decoded ones
+  const uint32_t lhead = act ? 31u - __clz(upto) : 0u;          // the item's first line
   uint32_t r[32];
-  uint32_t R = 0, Rw = 0;
-  const uint32_t* ringw = reinterpret_cast<const uint32_t*>(ws.ring);
-  uint32_t rw0 = 0, sh0 = 0, wd0 = 0;
-  if (K == 32 && act) {
-    rw0 = ws.rw[lane];
-    sh0 = ws.rs[lane] & 31u;
-    wd0 = ws.rs[lane] >> 8;
-  }
+  uint32_t R = 0;
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    const uint32_t m = (uint32_t)(c + lane) & 31u;  // int of the line
-    uint32_t wi, sh, wd, comp;
-    if (K == 32) {
-      wi = rw0;
-      sh = sh0;
-      wd = wd0;
-      comp = m;
-    } else {
-      const uint32_t row = lane * RPL + (m / K);
-      wi = act ? ws.rw[row] : 0;
-      const uint32_t s = act ? ws.rs[row] : 0;
-      sh = s & 31u;
-      wd = s >> 8;
-      comp = m % K;
-    }
-    const uint32_t lo = ringw[wi + comp];
-    const uint32_t hi = (sh + wd > 32) ? ringw[wi + K + comp] : 0u;
-    uint32_t v = __funnelshift_r(lo, hi, sh) & low_mask(wd);
-    if (KIND == GC_PFD) {
-      if ((xmask >> m) & 1u) {
-        const uint32_t idx = xfirst + __popc(xmask & ((1u << m) - 1u));
-        const uint8_t* p = xvals + (size_t)idx * xwb;
-        uint32_t x = p[0];
-        if (xwb > 1) x |= (uint32_t)p[1] << 8;
-        if (xwb > 2) x |= ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-        v = x;
-      }
-    }
-    if (m >= nv) v = 0;
-    if (RESTORE) {
-      R += v;
-      r[c] = R;
-      if ((uint32_t)c == 31u - lane) Rw = R;
-    } else {
-      r[c] = v;
-    }
-  }
-
-  // 4. docIDs: segmented scan of line totals, then each item's base
-  uint32_t base_l = 0, E = 0;
-  const uint32_t T = R;
-  if (RESTORE) {
-    const bool head = act && q == 0;
-    uint32_t v = act ? T : 0;
-    bool f = head || !act;
+  for (int rr = 0; rr < (int)RPL; ++rr) {
+    const uint32_t row = act ? lane * RPL + rr : 0u;
+    const uint32_t vi = act ? ws.rw[row] : 0u;
+    const uint32_t sw = act ? ws.rs[row] : 0u;
+    const uint32_t sh = sw & 31u, wd = sw >> 8;
+    const uint32_t msk = low_mask(wd);
+    const bool cross = sh + wd > 32;
+    const uint32_t* P0 = ws.tb + 4 * vi + (vi >> 3);
+    const uint32_t* P1 = ws.tb + 4 * (vi + 1) + ((vi + 1) >> 3);
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, v, o);
-      const bool g = __shfl_up_sync(kFull, f, o);
-      if (lane >= (uint32_t)o && !f) {
-        v += y;
-        f = g;
-      }
-    }
-    E = v - (act ? T : 0);
-    // item totals: inclusive value at each item's last line
-    const uint32_t lastl = my_lines ? my_line0 + my_lines - 1 : 0;
-    const uint32_t tot = __shfl_sync(kFull, v, lastl);
-    const bool live = lane < np && my_lines > 0;
-    const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
-    const bool needs_lb = live && my_tile > 0 && !has_base;
-    uint32_t base = has_base ? my_base : 0;
-    if (a.lb) {
-      if (live && !needs_lb && (my_shape & GC_WORK_PUBLISH)) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(base + tot));
-      if (lane < np && my_dead) st_release(a.lb + my_item, kFlagPrefix);  // its error is reported
-      if (needs_lb) st_release(a.lb + my_item, kFlagAgg | tot);
-    }
-    uint32_t pend = __ballot_sync(kFull, needs_lb);
-    while (pend) {
-      const uint32_t p = __ffs(pend) - 1;
-      pend &= pend - 1;
-      const uint32_t it = __shfl_sync(kFull, my_item, p);
-      const uint32_t tl = __shfl_sync(kFull, my_tile, p);
-      const uint32_t lst = __shfl_sync(kFull, my_list, p);
-      const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
-      if (lane == p) {
-        base = ex;
-        if (a.lb) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(ex + tot));
-      }
-    }
-    base_l = __shfl_sync(kFull, base, p_l);
-  }
-
-  // 5. final values, transposed to line-major order
-  if (act) {
-    const uint32_t k0 = E + base_l - Rw;
-    const uint32_t k1 = k0 + T;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const uint32_t m = (uint32_t)(c + lane) & 31u;
-      uint32_t v = r[c];
-      if (RESTORE) v += ((uint32_t)c + lane < 32u) ? k1 : k0;
-      ws.tb[lane * 32 + m] = v;
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t lo = P0[c];
+      uint32_t hi = 0;
+      if (KIND != GC_SIMPLE && cross) hi = P1[c];  // Group-Simple values never cross a word
+      r[4 * rr + c] = __funnelshift_r(lo, hi, sh) & msk;
     }
   }
-  __syncwarp();
-  // output bases of the lines
-  {
-    const uint64_t oat = (lane < np) ? rec_at(ws.rec, s0 + lane).out_at : 0ull;
-    const uint64_t ob = __shfl_sync(kFull, oat, p_l);
+  if (KIND == GC_PFD) {
+    // the values over the exception slots, in the line-major buffer
+    uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
+    const uint32_t swz = lane & 7u;
+    __syncwarp();  // (the re-laid data is read)
     if (act) {
-      ws.lout[lane] = ob + 32ull * q;
-      ws.lnv[lane] = nv;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) T[c ^ swz] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+    }
+    __syncwarp();
+    for (uint32_t lm = live; lm; lm &= lm - 1) {
+      const uint32_t p = __ffs(lm) - 1;
+      const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
+      const gc_work& w = rec_at(ws.rec, s0 + p);
+      const uint32_t f = (s0 + p) % kFly;
+      const uint32_t at = ws.at[f];
+      const uint32_t dbytes = ws.fvecs[f] * 16;
+      CtrlView C;
+      C.g = a.ctrl_pool + w.ctrl_at;
+      C.size = w.ctrl_bytes;
+      C.s1 = ws.ring + at + dbytes;
+      C.lo1 = w.win_at;
+      C.len1 = ws.cst[f];
+      C.s2 = ws.ring + at + dbytes + ws.cst[f];
+      C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
+      C.len2 = ws.xst[f];
+      const uint64_t row0 = (uint64_t)w.tile * Geo<4>::TR;
+      pfd_patch4(a, ws, C, row0 / kPfdFrameRows, w.exc_at, (w_nint(w.shape) + 3) / 4, line0, w.list);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint4 v = T[c ^ swz];
+        r[4 * c] = v.x;
+        r[4 * c + 1] = v.y;
+        r[4 * c + 2] = v.z;
+        r[4 * c + 3] = v.w;
+      }
+    }
+  }
+  if (RESTORE) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      R += r[j];
+      r[j] = R;
+    }
+  }
+
+  // 3. docIDs: segmented scan of line totals, then each item's base
+  uint32_t k0 = 0;
+  if (RESTORE) {
+    // (a plain scan, less the scan before the item's first line)
+    const uint32_t T = act ? R : 0u;
+    const uint32_t V = warp_incl_sum(T);
+    const uint32_t shape0 = __shfl_sync(kFull, my_shape, 0);
+    if (np == 1 && heads == 1u && (shape0 & (GC_WORK_HAS_BASE | GC_WORK_PUBLISH)) == GC_WORK_HAS_BASE) {
+      // a pack of one live tile with its skip entry, which no other tile
+      // waits for
+      k0 = V - T + __shfl_sync(kFull, my_base, 0);
+    } else {
+      const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
+      const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
+      const uint32_t E = v - T;
+      const uint32_t lastl = my_live ? my_line0 + my_lines - 1 : 0u;
+      const uint32_t tot = __shfl_sync(kFull, v, lastl);
+      const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
+      const bool needs_lb = my_live && my_tile > 0 && !has_base;
+      uint32_t base = has_base ? my_base : 0u;
+      if (a.lb) {
+        if (my_live && !needs_lb && (my_shape & GC_WORK_PUBLISH))
+          st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(base + tot));
+        if (my_dead) st_release(a.lb + my_item, kFlagPrefix);  // its error is reported
+        if (needs_lb) st_release(a.lb + my_item, kFlagAgg | tot);
+      }
+      for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
+        const uint32_t p = __ffs(pend) - 1;
+        const uint32_t it = __shfl_sync(kFull, my_item, p);
+        const uint32_t tl = __shfl_sync(kFull, my_tile, p);
+        const uint32_t lst = __shfl_sync(kFull, my_list, p);
+        const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
+        if (lane == p) {
+          base = ex;
+          if (a.lb) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(ex + tot));
+        }
+      }
+      if (my_live) ws.ibase[my_rank] = base;
+      __syncwarp();
+      k0 = E + (act ? ws.ibase[rank] : 0u);
+    }
+  }
+
+  // the re-laid data is read: its buffer takes the results, line l at words
+  // 32 l .. 32 l + 31 with its 16-byte chunk c at chunk c ^ (l & 7), so that
+  // the eight lanes of each quarter-warp touch eight different chunks both
+  // here (a line per lane) and when reading (a chunk per lane, below)
+  __syncwarp();
+  const bool whole = heads == 1u && ws.inint[0] == (uint32_t)kTileInts;  // one whole tile
+  if (act) {
+    uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
+    const uint32_t sw = lane & 7u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      T[c ^ sw] = make_uint4(r[4 * c] + k0, r[4 * c + 1] + k0, r[4 * c + 2] + k0, r[4 * c + 3] + k0);
+    if (!whole) {
+      ws.lout[lane] = ws.iout[rank] + 32ull * (lane - lhead);
+      const uint32_t left = ws.inint[rank] - 32u * (lane - lhead);
+      ws.lnv[lane] = left < 32u ? left : 32u;
     }
   }
   __syncwarp();
-  for (uint32_t ln = 0; ln < nl; ++ln) {
-    const uint64_t ob = ws.lout[ln];
-    const uint32_t n = ws.lnv[ln];
-    const uint32_t v = ws.tb[ln * 32 + lane];
-    if (lane < n) a.out_pool[ob + lane] = v;
+
+  // 4. stores. Lane j takes chunk c = j % 8 of lines 4 q + j / 8 and stores
+  // it with one 16-byte store where the chunk is whole and its output
+  // 16-byte aligned, else word by word. A whole tile whose output is not
+  // aligned goes out line by line instead, lane j storing word j (word j of
+  // line l sits at word 32 l + 4 ((j / 4) ^ (l & 7)) + j % 4).
+  const uint32_t c = lane & 7u;
+  uint32_t* o1 = a.out_pool + ws.iout[0];
+  if (whole) {
+    if ((reinterpret_cast<uintptr_t>(o1) & 15u) == 0) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t rr = 4u * q + (lane >> 3);
+        const uint4 v = reinterpret_cast<const uint4*>(ws.tb + rr * 32)[c ^ (rr & 7u)];
+        reinterpret_cast<uint4*>(o1 + rr * 32)[c] = v;
+      }
+    } else {
+      const uint32_t wsw = 4u * (lane >> 2), wlo = lane & 3u;
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) o1[rr * 32 + lane] = ws.tb[rr * 32 + (wsw ^ (4u * (rr & 7))) + wlo];
+    }
+  } else {
+    for (uint32_t q = 0; 4 * q < nl; ++q) {
+      const uint32_t ln = 4 * q + (lane >> 3);
+      if (ln < nl) {
+        const uint32_t n = ws.lnv[ln];
+        const uint4 v = reinterpret_cast<const uint4*>(ws.tb + ln * 32)[c ^ (ln & 7u)];
+        uint32_t* o = a.out_pool + ws.lout[ln] + 4 * c;
+        if (4 * c + 4 <= n && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+          *reinterpret_cast<uint4*>(o) = v;
+        } else {
+          if (4 * c < n) o[0] = v.x;
+          if (4 * c + 1 < n) o[1] = v.y;
+          if (4 * c + 2 < n) o[2] = v.z;
+          if (4 * c + 3 < n) o[3] = v.w;
+        }
+      }
+    }
   }
   __syncwarp();
 }
@@ -1468,7 +1498,8 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
       lv = lane < staged ? ws.flines[fp] | (uint32_t)ws.fvecs[fp] << 16 : 0u;
       lvi = warp_incl_sum(lv);
       np = __popc(__ballot_sync(
-          kFull, lane < staged && (lvi & 0xffffu) <= 32u && (K != 32 || (lvi >> 16) <= (uint32_t)kPadVec)));
+          kFull, lane < staged && (lvi & 0xffffu) <= 32u &&
+                     (lvi >> 16) <= (uint32_t)(K == 32 ? kPadVec : kPadVec4)));
       nl = __shfl_sync(kFull, lvi & 0xffffu, np - 1);
     }
     // wait for their copies
@@ -1490,7 +1521,7 @@ __global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
       break;
     }
     if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, ws, s_done, np, nl, lane < np ? lv : 0u, lvi);
-    else decode_pack<KIND, K, RESTORE>(a, ws, s_done, np, nl);
+    else decode_pack4<KIND, RESTORE>(a, ws, s_done, np, nl, lane < np ? lv : 0u, lvi);
     used -= np == 1 ? ws.end[s_done % kFly] : __reduce_add_sync(kFull, lane < np ? ws.end[fp] : 0u);
     s_done += np;
   }
