@@ -15,7 +15,10 @@
 // base (the docID before tile t) is below x; mark it; (3) one plan record
 // per marked tile, its 1024 ints to their own slot; (4) decode those
 // tiles; (5) look x up in its tile by binary search; (6) per query, the
-// hits in order.
+// hits in order: every docID of a gets the number of hits before it in
+// all of a (a scan over spans of 4096 docIDs), so that a hit's place in
+// its query's results is its rank minus the rank of the query's first
+// docID -- the time does not hang on the longest query.
 
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -30,6 +33,9 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kTile = 1024;           // ints per tile
 constexpr uint32_t kUnmarked = 0xffffffffu;
 constexpr uint32_t kMarked = 0xfffffffeu;
+constexpr uint32_t kSpanThreads = 256;
+constexpr uint32_t kSpan = 16 * kSpanThreads;  // docIDs of a per span of the rank scan
+constexpr uint32_t kScan = 1024;               // span sums per round of their scan
 
 struct Args {
   const gc_list* lists;
@@ -54,6 +60,10 @@ struct Args {
   unsigned long long* count;  // [0] records
   uint64_t rec_cap;
   uint32_t* bdoc;          // decoded tiles, 1024 ints per record
+  uint32_t* span;          // per span: its hits, then the hits before it
+  uint64_t nspans;
+  uint32_t* total;         // hits in all of a
+  uint32_t* rank;          // per a docID: the hits before it in all of a (reuses at)
   uint32_t* out;           // results at aoff[q]
   uint32_t* counts;        // per query: results
   uint32_t* status;
@@ -173,22 +183,128 @@ __global__ void k_isect_probe(Args a) {
   a.hit[i] = found ? 1 : 0;
 }
 
-// (6) one warp per query: the hits of its a docIDs, in order
-__global__ void k_isect_compact(Args a) {
-  const uint64_t q = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  const uint32_t lane = threadIdx.x & 31u;
-  if (q >= a.nq) return;
-  const uint64_t b0 = a.aoff[q];
-  const uint64_t n = a.qa[q] < a.nlists ? a.lists[a.qa[q]].n : 0;
-  uint32_t c = 0;
-  for (uint64_t j = 0; j < n; j += 32) {
-    const uint64_t i = b0 + j + lane;
-    const bool h = j + lane < n && a.hit[i];
-    const uint32_t m = __ballot_sync(kFull, h);
-    if (h) a.out[b0 + c + __popc(m & ((1u << lane) - 1u))] = a.adoc[i];
-    c += __popc(m);
+// the hit flags (0 or 1 a byte) of a's docIDs i0 .. i0 + 15 as four words
+// and their sum (i0 a multiple of 16: whole groups are one 16-byte load)
+__device__ __forceinline__ uint32_t hits16(const Args& a, uint64_t i0, uint32_t w[4]) {
+  if (i0 + 16 <= a.a_ints) {
+    const uint4 v = *reinterpret_cast<const uint4*>(a.hit + i0);
+    w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+  } else {
+    w[0] = w[1] = w[2] = w[3] = 0;
+    for (uint32_t j = 0; i0 + j < a.a_ints && j < 16; ++j) w[j / 4] |= (uint32_t)a.hit[i0 + j] << (8 * (j % 4));
   }
-  if (lane == 0) a.counts[q] = c;
+  return __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
+}
+
+// exclusive scan of one value per thread over a block of kSpanThreads;
+// the block's sum to *sum
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t* sum) {
+  __shared__ uint32_t warp_sums[kSpanThreads / 32];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < kSpanThreads / 32; ++w) {
+    before += w < wid ? warp_sums[w] : 0u;
+    all += warp_sums[w];
+  }
+  *sum = all;
+  return before + x - v;
+}
+
+// (6a) the hits of each span
+__global__ void __launch_bounds__(kSpanThreads) k_isect_span_sums(Args a) {
+  uint32_t w[4], all;
+  block_scan(hits16(a, (uint64_t)blockIdx.x * kSpan + 16u * threadIdx.x, w), &all);
+  if (threadIdx.x == 0) a.span[blockIdx.x] = all;
+}
+
+// (6b) exclusive scan of the span sums (one block, rounds of kScan); the
+// total to *total
+__global__ void __launch_bounds__(kScan) k_isect_span_scan(Args a) {
+  __shared__ uint32_t warp_sums[kScan / 32];
+  __shared__ uint32_t carry;
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint64_t r = 0; r < a.nspans; r += kScan) {
+    const uint64_t i = r + threadIdx.x;
+    const uint32_t v = i < a.nspans ? a.span[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t y = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t z = __shfl_up_sync(kFull, y, o);
+        if (lane >= (uint32_t)o) y += z;
+      }
+      warp_sums[lane] = y;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t c = carry;
+    if (i < a.nspans) a.span[i] = c + (wid ? warp_sums[wid - 1] : 0u) + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry = c + warp_sums[kScan / 32 - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.total = carry;
+}
+
+// (6c) each docID of a: the hits before it in all of a
+__global__ void __launch_bounds__(kSpanThreads) k_isect_rank(Args a) {
+  const uint64_t i0 = (uint64_t)blockIdx.x * kSpan + 16u * threadIdx.x;
+  uint32_t w[4], all;
+  uint32_t r = a.span[blockIdx.x] + block_scan(hits16(a, i0, w), &all);
+  uint32_t rk[16];
+#pragma unroll
+  for (uint32_t j = 0; j < 16; ++j) {
+    rk[j] = r;
+    r += (w[j / 4] >> (8 * (j % 4))) & 1u;
+  }
+  if (i0 + 16 <= a.a_ints) {
+    uint4* d = reinterpret_cast<uint4*>(a.rank + i0);
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) d[j] = make_uint4(rk[4 * j], rk[4 * j + 1], rk[4 * j + 2], rk[4 * j + 3]);
+  } else {
+#pragma unroll
+    for (uint32_t j = 0; j < 16; ++j)
+      if (i0 + j < a.a_ints) a.rank[i0 + j] = rk[j];
+  }
+}
+
+// (6d) each hit to its query's results, in order; each query's count
+__global__ void k_isect_place(Args a) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.a_ints && a.hit[i]) {
+    const uint64_t q = query_of(a.aoff, a.nq, i);
+    const uint64_t p = a.aoff[q];
+    if (p > i) report(a.status, GC_ERR_INVALID, (uint32_t)q);
+    else a.out[p + (a.rank[i] - a.rank[p])] = a.adoc[i];
+  }
+  if (i < a.nq) {
+    const uint64_t p = a.aoff[i], e = i + 1 < a.nq ? a.aoff[i + 1] : a.a_ints;
+    if (p > e || e > a.a_ints) {
+      report(a.status, GC_ERR_INVALID, (uint32_t)i);
+      a.counts[i] = 0;
+    } else {
+      const uint32_t rp = p < a.a_ints ? a.rank[p] : *a.total, re = e < a.a_ints ? a.rank[e] : *a.total;
+      a.counts[i] = re - rp;
+    }
+  }
 }
 
 // the queries' lists exist
@@ -205,7 +321,7 @@ namespace {
 using namespace gcisect;
 
 struct Layout {
-  uint64_t hdr, work_a, dec_a, adoc, at, hit, mark, work_b, sel, outs, dec_b, bdoc, total;
+  uint64_t hdr, work_a, dec_a, adoc, at, hit, span, mark, work_b, sel, outs, dec_b, bdoc, total;
 };
 
 Layout layout(uint64_t a_tiles, uint64_t a_ints, uint64_t b_tiles) {
@@ -217,7 +333,7 @@ Layout layout(uint64_t a_tiles, uint64_t a_ints, uint64_t b_tiles) {
   Layout L;
   uint64_t o = 0;
   L.hdr = o;
-  o += 256;  // plan counts of a (2 uint64) and of b (2 uint64)
+  o += 256;  // plan counts of a (2 uint64) and of b (2 uint64); hits in all of a (uint32)
   L.work_a = o;
   o += align_up(a_tiles * sizeof(gc_work), 256);
   L.dec_a = o;
@@ -228,6 +344,8 @@ Layout layout(uint64_t a_tiles, uint64_t a_ints, uint64_t b_tiles) {
   o += align_up(a_ints * 4, 256);
   L.hit = o;
   o += align_up(a_ints, 256);
+  L.span = o;
+  o += align_up((a_ints + kSpan - 1) / kSpan * 4, 256);
   L.mark = o;
   o += align_up(b_tiles * 4, 256);
   L.work_b = o;
@@ -307,6 +425,10 @@ gc_status gc_intersect(const gc_codec* codec, const gc_list* d_lists, uint64_t n
   g.count = reinterpret_cast<unsigned long long*>(count_b);
   g.rec_cap = rec;
   g.bdoc = reinterpret_cast<uint32_t*>(base + L.bdoc);
+  g.span = reinterpret_cast<uint32_t*>(base + L.span);
+  g.nspans = (a_ints + kSpan - 1) / kSpan;
+  g.total = reinterpret_cast<uint32_t*>(base + L.hdr + 32);
+  g.rank = g.at;  // the tiles of b are looked up by then
   g.out = d_out;
   g.counts = d_counts;
   g.status = d_status;
@@ -355,9 +477,14 @@ gc_status gc_intersect(const gc_codec* codec, const gc_list* d_lists, uint64_t n
   // (5) lookups, (6) results in order
   if (a_ints) {
     k_isect_probe<<<grid(a_ints, 256), 256, 0, s>>>(g);
-    ++launches;
+    k_isect_span_sums<<<(unsigned)g.nspans, kSpanThreads, 0, s>>>(g);
+    k_isect_span_scan<<<1, kScan, 0, s>>>(g);
+    k_isect_rank<<<(unsigned)g.nspans, kSpanThreads, 0, s>>>(g);
+    launches += 4;
+  } else if (cudaMemsetAsync(g.total, 0, 4, s) != cudaSuccess) {
+    return GC_ERR_CUDA;
   }
-  k_isect_compact<<<grid(nqueries * 32, 256), 256, 0, s>>>(g);
+  k_isect_place<<<grid(a_ints > nqueries ? a_ints : nqueries, 256), 256, 0, s>>>(g);
   ++launches;
   gc_host::reset_launches();
   gc_host::count_launch(launches);
