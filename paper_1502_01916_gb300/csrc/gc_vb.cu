@@ -6,7 +6,9 @@
 // 64, where the vertical group codecs spend at least a whole vector. Groups
 // go most significant first and the last byte carries the set bit (the form
 // of the book the paper cites). A list of n < 64 numbers is a few dozen
-// bytes, so one thread encodes or decodes one list.
+// bytes: one thread encodes one list. A warp decodes 32 lists whose bytes
+// lie back to back as one stream cut into 32 equal segments, a lane each,
+// so that no lane waits for the longest list.
 
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -159,40 +161,198 @@ struct Dec {
   uint32_t* status;
 };
 
-// each list's numbers (its docIDs when restoring: the list's own prefix
-// sum, modulo 2^32)
-__global__ void k_vb_decode(Dec d) {
-  for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < d.nlists;
-       l += (uint64_t)gridDim.x * blockDim.x) {
-    const gc_vb_list L = d.lists[l];
-    if (L.byte_off + L.nbytes > d.bytes_len || L.out_off + L.n > d.out_len) {
-      report(d.status, GC_ERR_INVALID, (uint32_t)l);
-      continue;
+// The numbers of one list from its bytes p[0 .. nbytes) into o[0 .. n),
+// or its docIDs when restoring (the list's own prefix sum, modulo 2^32);
+// false when the bytes do not hold exactly n numbers of at most 32 bits.
+__device__ __forceinline__ bool vb_list(const uint8_t* p, uint32_t nbytes, uint32_t n, bool restore, uint32_t* o) {
+  uint32_t pos = 0, sum = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t v = 0;
+    for (;;) {
+      if (pos >= nbytes || (v >> 25)) return false;  // (v * 128 + 127 would not fit)
+      const uint32_t b = p[pos++];
+      v = (v << 7) | (b & 0x7fu);
+      if (b & 0x80u) break;
     }
-    const uint8_t* p = d.bytes + L.byte_off;
-    uint32_t* o = d.out + L.out_off;
-    uint32_t pos = 0, sum = 0;
-    bool ok = true;
-    for (uint32_t i = 0; i < L.n && ok; ++i) {
-      uint64_t v = 0;
-      for (;;) {
-        if (pos >= L.nbytes) {
-          ok = false;
-          break;
+    sum += v;
+    o[i] = restore ? sum : v;
+  }
+  return pos == nbytes;
+}
+
+// What a warp keeps of its group of 32 lists: list j's first byte (past
+// the group's lists, the group's length), its numbers and output offset;
+// the number ends before its first byte and the running sum of the group's
+// numbers before its first number, each first within the segment that
+// holds that byte, then within the group.
+struct GroupTab {
+  uint32_t s[33];
+  uint32_t n[32];
+  uint32_t m[32], mp[32];
+  uint32_t b[32], bp[32];
+  uint64_t oo[32];
+};
+
+// Lane t's part of a group whose bytes p[0 .. len) lie back to back: the
+// numbers that end (their byte with the high bit set) in its segment
+// [a, b). A number belongs to the list holding its last byte; its bytes
+// start after the number end before it, but not before its list's first
+// byte (what a list's bytes leave unended at its last byte is dropped).
+// Counts the segment's numbers (k) and sums their values (sum; a number
+// wider than 32 bits counts as 0). The first pass records, for each list
+// starting in the segment, k and sum before its first number; the second
+// writes each number to its list's output, at its index in the group (C +
+// k) less the number ends before the list, as a docID the running sum (E +
+// sum) less the sum before the list.
+template <bool WRITE>
+__device__ __forceinline__ void vb_segment(const Dec& d, uint64_t g0, const uint8_t* p, uint32_t nm, GroupTab& T,
+                                           uint32_t a, uint32_t b, uint32_t C, uint32_t E, uint32_t& k,
+                                           uint32_t& sum) {
+  k = 0;
+  sum = 0;
+  if (a >= b) return;
+  // the list holding byte a (the last one starting at or before a) and the
+  // first list starting at or after a
+  uint32_t lst = 0, jn = 0;
+#pragma unroll
+  for (uint32_t step = 16; step; step >>= 1)
+    if (lst + step < nm && T.s[lst + step] <= a) lst += step;
+#pragma unroll
+  for (uint32_t step = 32; step; step >>= 1)
+    if (jn + step <= nm && T.s[jn + step - 1] < a) jn += step;
+  uint32_t nxt = T.s[lst + 1];
+  uint32_t sjn = jn < nm ? T.s[jn] : 0xffffffffu;
+  uint32_t m_l = 0, n_l = 0, b_l = 0;
+  uint64_t o_l = 0;
+  if (WRITE) m_l = T.m[lst], n_l = T.n[lst], b_l = T.b[lst], o_l = T.oo[lst];
+  // the first byte of the number holding byte a
+  uint32_t q = a;
+  const uint32_t s0 = T.s[lst];
+  while (q > s0 && !(p[q - 1] & 0x80u)) --q;
+  uint32_t v = 0;
+  bool wide = false;
+  for (uint32_t pos = q; pos < b; ++pos) {
+    if (pos == nxt) {  // a list starts here
+      v = 0;
+      wide = false;
+      do {
+        ++lst;
+        nxt = T.s[lst + 1];
+      } while (nxt <= pos);
+      if (WRITE) m_l = T.m[lst], n_l = T.n[lst], b_l = T.b[lst], o_l = T.oo[lst];
+    }
+    const uint32_t x = p[pos];
+    if (v >> 25) wide = true;  // (v * 128 + 127 would not fit)
+    v = (v << 7) | (x & 0x7fu);
+    if (x & 0x80u) {
+      if (!WRITE) {
+        while (sjn <= pos && sjn < b) {
+          T.mp[jn] = k;
+          T.bp[jn] = sum;
+          ++jn;
+          sjn = jn < nm ? T.s[jn] : 0xffffffffu;
         }
-        const uint32_t b = p[pos++];
-        v = v * 128u + (b & 0x7fu);
-        if (v > 0xffffffffull) {
-          ok = false;
-          break;
-        }
-        if (b & 0x80u) break;
       }
-      if (!ok) break;
-      sum += (uint32_t)v;
-      o[i] = d.restore ? sum : (uint32_t)v;
+      sum += wide ? 0u : v;
+      if (WRITE) {
+        const uint32_t idx = C + k - m_l;
+        if (!wide && idx < n_l) d.out[o_l + idx] = d.restore ? E + sum - b_l : v;
+        else report(d.status, GC_ERR_CORRUPT, (uint32_t)(g0 + lst));
+      }
+      ++k;
+      v = 0;
+      wide = false;
     }
-    if (!ok || pos != L.nbytes) report(d.status, GC_ERR_CORRUPT, (uint32_t)l);
+  }
+  if (!WRITE) {
+    while (sjn < b) {
+      T.mp[jn] = k;
+      T.bp[jn] = sum;
+      ++jn;
+      sjn = jn < nm ? T.s[jn] : 0xffffffffu;
+    }
+  }
+}
+
+// A warp takes lists 32 g .. 32 g + 31, lane j holding list j. When their
+// bytes lie back to back, they are cut into 32 equal segments, lane t
+// taking segment t (vb_segment), so that every lane has the same bytes to
+// walk whatever the lists' lengths: a first pass counts and sums each
+// segment's numbers, two warp scans give every segment its numbers and sum
+// before it, and a second pass writes. A list is accepted exactly as by
+// the one-thread loop: its bytes hold n number ends (the segments' counts),
+// its last byte ends a number and every number fits 32 bits; a number that
+// is not accepted is not written, so a malformed list writes only inside
+// its own output. Lists whose bytes do not lie back to back go one per
+// thread.
+__device__ void vb_group(const Dec& d, uint64_t g, const gc_vb_list& L, bool mine, bool in, GroupTab& T) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t l = g * 32 + lane;
+  if (g * 32 >= d.nlists) return;
+  // back to back: each list starts where the one before ends
+  const uint64_t end = L.byte_off + L.nbytes;
+  const uint64_t prev_end = __shfl_up_sync(kFull, end, 1);
+  const uint64_t first = __shfl_sync(kFull, L.byte_off, 0);
+  const uint32_t nm = (uint32_t)min((uint64_t)32, d.nlists - g * 32);
+  const uint64_t last_end = __shfl_sync(kFull, end, nm - 1);
+  const bool joined = !mine || lane == 0 || L.byte_off == prev_end;
+  if (__ballot_sync(kFull, in && joined) != kFull || last_end - first >= (1ull << 31)) {
+    if (mine && in && !vb_list(d.bytes + L.byte_off, L.nbytes, L.n, d.restore, d.out + L.out_off))
+      report(d.status, GC_ERR_CORRUPT, (uint32_t)l);
+    return;
+  }
+  const uint8_t* p = d.bytes + first;
+  const uint32_t len = (uint32_t)(last_end - first);
+  const uint32_t sj = mine ? (uint32_t)(L.byte_off - first) : len;
+  __syncwarp();  // (the group before is written out)
+  T.s[lane] = sj;
+  if (lane == 0) T.s[32] = len;
+  if (mine) {
+    T.n[lane] = L.n;
+    T.oo[lane] = L.out_off;
+  }
+  __syncwarp();
+  const uint32_t S = (len + 31) / 32;  // bytes per segment
+  const uint32_t a = min(lane * S, len), b = min(a + S, len);
+  uint32_t k, sum;
+  vb_segment<false>(d, g * 32, p, nm, T, a, b, 0, 0, k, sum);
+  uint32_t C = k, E = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, C, o), z = __shfl_up_sync(kFull, E, o);
+    if (lane >= (uint32_t)o) C += y, E += z;
+  }
+  const uint32_t ends = __shfl_sync(kFull, C, 31);  // number ends in the group
+  C -= k;
+  E -= sum;
+  __syncwarp();
+  const uint32_t u = S && sj < len ? min(sj / S, 31u) : 0u;  // the segment holding list j's first byte
+  const uint32_t Cu = __shfl_sync(kFull, C, u), Eu = __shfl_sync(kFull, E, u);
+  const uint32_t mj = sj < len ? Cu + T.mp[lane] : ends;
+  T.m[lane] = mj;
+  T.b[lane] = sj < len ? Eu + T.bp[lane] : 0u;
+  const uint32_t m_next = __shfl_down_sync(kFull, mj, 1);
+  if (mine && ((lane + 1 < nm ? m_next : ends) - mj != L.n || (L.nbytes && !(p[sj + L.nbytes - 1] & 0x80u))))
+    report(d.status, GC_ERR_CORRUPT, (uint32_t)l);
+  __syncwarp();
+  vb_segment<true>(d, g * 32, p, nm, T, a, b, C, E, k, sum);
+}
+
+// Warp w takes lists 32 w .. 32 w + 31 as a group (vb_group).
+__global__ void __launch_bounds__(256) k_vb_decode(Dec d) {
+  __shared__ GroupTab tabs[8];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t groups = (d.nlists + 31) / 32;
+  for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; g < groups;
+       g += (uint64_t)gridDim.x * blockDim.x / 32) {
+    const uint64_t l = g * 32 + lane;
+    const bool mine = l < d.nlists;
+    gc_vb_list L = {};
+    if (mine) L = d.lists[l];
+    const bool in = !mine || (L.byte_off <= d.bytes_len && L.nbytes <= d.bytes_len - L.byte_off &&
+                              L.out_off <= d.out_len && L.n <= d.out_len - L.out_off);
+    if (!in) report(d.status, GC_ERR_INVALID, (uint32_t)l);
+    vb_group(d, g, L, mine, in, tabs[threadIdx.x >> 5]);
   }
 }
 
@@ -255,7 +415,7 @@ gc_status gc_vb_decode_batch(const gc_vb_list* d_lists, uint64_t nlists, const u
   d.out_len = out_len;
   d.restore = restore_docids;
   d.status = d_status;
-  const uint64_t want = (nlists + 255) / 256;
+  const uint64_t want = (nlists + 255) / 256;  // a warp per 32 lists, 8 warps per block
   const unsigned g = (unsigned)(want < 65536 ? want : 65536);
   gcvb::k_vb_decode<<<g, 256, 0, (cudaStream_t)stream>>>(d);
   gc_host::count_launch(1);
