@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--no-short", action="store_true", help="skip the short-list (Variable Byte rule) measurement")
     p.add_argument("--and-queries", type=int, default=4000, help="two-list AND queries in the timed batch")
     p.add_argument("--serve-seconds", type=float, default=0.5, help="trace length per request rate")
-    p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work budget per codec")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="seconds of oracle work per codec")
     return p.parse_args()
 
 
@@ -153,10 +153,10 @@ def cpu_oracle_rate(lengths, kinds, k, zeta, seconds, seed=7):
     import synth
     rng = np.random.default_rng(seed)
     # about seconds * 13e6 ints per codec: lists drawn uniformly at random
-    budget = int(seconds * 13e6)
+    work = int(seconds * 13e6)
     order = rng.permutation(len(lengths))
     cum = np.cumsum(lengths[order].astype(np.int64))
-    m = int(np.searchsorted(cum, budget)) + 1
+    m = int(np.searchsorted(cum, work)) + 1
     L = lengths[order[:m]]
     gaps, off = synth.uniform_index(seed, L, UNIVERSE)
     tot_ints, tot_s = 0, 0.0
@@ -202,10 +202,10 @@ def cpu_oracle_rate_parallel(lengths, kinds, k, zeta, seconds, seed=9, workers=N
     import multiprocessing as mp
     workers = workers or os.cpu_count() or 1
     rng = np.random.default_rng(seed)
-    budget = int(seconds * 13e6) * workers
+    work = int(seconds * 13e6) * workers
     order = rng.permutation(len(lengths))
     cum = np.cumsum(lengths[order].astype(np.int64))
-    m = int(np.searchsorted(cum, budget)) + 1
+    m = int(np.searchsorted(cum, work)) + 1
     chunks = np.array_split(order[:m], workers)
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         futs = [ex.submit(_oracle_worker, seed * 1000 + w, lengths[ch], kinds, k, zeta)

@@ -44,7 +44,7 @@ typedef enum {
   GC_ERR_CORRUPT = 3,     /* a control or data stream is malformed (device) */
   GC_ERR_CUDA = 4,        /* a CUDA call failed */
   GC_ERR_TIMEOUT = 5,     /* a bounded wait between tiles gave up (device) */
-  GC_ERR_UNSUPPORTED = 6  /* a valid request that this build does not serve */
+  GC_ERR_UNSUPPORTED = 6  /* a valid request that this library does not serve */
 } gc_status;
 
 enum { GC_SIMPLE = 0, GC_SCHEME = 1, GC_AFOR = 2, GC_PFD = 3 };
