@@ -1179,28 +1179,31 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   if (KIND != GC_PFD) {
     extract_line<KIND, RESTORE>(P, sh, msk, cross, r, R);
   } else {
-    // Group-PFD: the slots' values, then the exceptions over their slots in
-    // the line-major buffer (line l at words 32 l .., 16-byte chunk c at
-    // chunk c ^ (l & 7)), then the running sum over the patched line
+    // Group-PFD: the slots' values; when a tile of the pack has exceptions
+    // (most frames have none), the exceptions over their slots in the
+    // line-major buffer (line l at words 32 l .., 16-byte chunk c at chunk
+    // c ^ (l & 7)); then the running sum over the patched line
     extract_line<KIND, false>(P, sh, msk, cross, r, R);
-    uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
-    const uint32_t swz = lane & 7u;
-    __syncwarp();  // (the re-laid data is read)
-    if (act) {
+    if (__ballot_sync(kFull, px.e != 0) & heads) {
+      uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
+      const uint32_t swz = lane & 7u;
+      __syncwarp();  // (the re-laid data is read)
+      if (act) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) T[c ^ swz] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
-    }
-    __syncwarp();
-    pfd_patch_pack32(a, ws, lane, heads, px);
-    __syncwarp();
-    if (act) {
+        for (int c = 0; c < 8; ++c) T[c ^ swz] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+      }
+      __syncwarp();
+      pfd_patch_pack32(a, ws, lane, heads, px);
+      __syncwarp();
+      if (act) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const uint4 v = T[c ^ swz];
-        r[4 * c] = v.x;
-        r[4 * c + 1] = v.y;
-        r[4 * c + 2] = v.z;
-        r[4 * c + 3] = v.w;
+        for (int c = 0; c < 8; ++c) {
+          const uint4 v = T[c ^ swz];
+          r[4 * c] = v.x;
+          r[4 * c + 1] = v.y;
+          r[4 * c + 2] = v.z;
+          r[4 * c + 3] = v.w;
+        }
       }
     }
     R = 0;
