@@ -428,7 +428,7 @@ __device__ __forceinline__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit,
 // checked to lie inside the list (the exceptions themselves are patched in
 // after the rows are decoded, pfd_patch4).
 __device__ __forceinline__ bool parse_pfd4(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows,
-                                           const RowSink<4>& out) {
+                                           const RowSink<4>& out, bool& exc) {
   const uint32_t lane = lane_id();
   const uint32_t nfr = (rows + kPfdFrameRows - 1) / kPfdFrameRows;
   bool ok = true;
@@ -454,6 +454,7 @@ __device__ __forceinline__ bool parse_pfd4(const CtrlView& C, uint64_t f0, uint6
   }
   const uint64_t xrec0 = exc_at + (warp_incl_sum(xb) - xb);
   if (lane < nfr && xb && xrec0 + xb > C.size) ok = false;
+  exc = __any_sync(kFull, xb != 0);
   const uint32_t inclL = warp_incl_sum(32u * b);
   const uint32_t lstart = inclL - 32u * b;
   for (uint32_t fl = 0; fl < nfr; ++fl) {
@@ -625,6 +626,7 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
 
   // 1. per tile: re-lay its vectors, and turn its control patterns into one
   // (vector, shift, width) entry per row
+  bool exc = false;  // (Group-PFD) a tile of the pack has exceptions
   for (uint32_t lm = live; lm; lm &= lm - 1) {
     const uint32_t p = __ffs(lm) - 1;
     const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
@@ -676,7 +678,9 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
     } else if (KIND == GC_AFOR) {
       ok = parse_afor<4>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
     } else {
-      ok = parse_pfd4(C, row0 / kPfdFrameRows, w.exc_at, rows, out);
+      bool x;
+      ok = parse_pfd4(C, row0 / kPfdFrameRows, w.exc_at, rows, out, x);
+      exc |= x;
     }
     // rows of the last line past the tile's end read nothing
     if (lane < lines * RPL - rows) {
@@ -712,8 +716,9 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
       r[4 * rr + c] = __funnelshift_r(lo, hi, sh) & msk;
     }
   }
-  if (KIND == GC_PFD) {
-    // the values over the exception slots, in the line-major buffer
+  if (KIND == GC_PFD && exc) {
+    // the values over the exception slots, in the line-major buffer (when
+    // a tile of the pack has exceptions)
     uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
     const uint32_t swz = lane & 7u;
     __syncwarp();  // (the re-laid data is read)
