@@ -179,6 +179,15 @@ def _ptr(t) -> int | None:
     return t.data_ptr()
 
 
+def _n(t, esize: int, what: str) -> int:
+    """The element count of a device buffer whose size the C ABI takes in
+    esize-byte units, after checking that it is a contiguous CUDA tensor of
+    such elements (a wrong dtype would give the library a wrong size)."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.element_size() != esize:
+        raise ValueError(f"{what}: expected a contiguous CUDA tensor of {esize}-byte elements")
+    return t.numel()
+
+
 def _stream(stream=None) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -223,9 +232,9 @@ def gc_encode_scratch_size(codec: gc_codec, n: int) -> int:
 
 def gc_encode(codec, d_gaps, n, d_ctrl, d_data, d_tiles, d_sizes, d_scratch, stream=None):
     lib = load()
-    _check(lib.gc_encode(ctypes.byref(codec), _ptr(d_gaps), n, _ptr(d_ctrl), d_ctrl.numel(), _ptr(d_data),
-                         d_data.numel(), _ptr(d_tiles), _ptr(d_sizes), _ptr(d_scratch), d_scratch.numel(),
-                         _stream(stream)), "gc_encode")
+    _check(lib.gc_encode(ctypes.byref(codec), _ptr(d_gaps), n, _ptr(d_ctrl), _n(d_ctrl, 1, "d_ctrl"), _ptr(d_data),
+                         _n(d_data, 4, "d_data"), _ptr(d_tiles), _ptr(d_sizes), _ptr(d_scratch),
+                         _n(d_scratch, 1, "d_scratch"), _stream(stream)), "gc_encode")
 
 
 def gc_encode_batch_scratch_size(codec: gc_codec, h_n: np.ndarray) -> int:
@@ -241,9 +250,9 @@ def gc_encode_batch(codec, d_gaps, h_n, h_in_off, d_lists, d_ctrl, d_data, d_til
     h_n = np.ascontiguousarray(h_n, dtype=np.uint32)
     h_in_off = np.ascontiguousarray(h_in_off, dtype=np.uint64)
     _check(load().gc_encode_batch(ctypes.byref(codec), _ptr(d_gaps), h_n.ctypes.data, h_in_off.ctypes.data,
-                                  len(h_n), _ptr(d_lists), _ptr(d_ctrl), d_ctrl.numel(), _ptr(d_data),
-                                  d_data.numel(), _ptr(d_tiles), d_tiles.numel() // TILE_BYTES,
-                                  _ptr(d_totals), _ptr(d_scratch), d_scratch.numel(), _stream(stream)),
+                                  len(h_n), _ptr(d_lists), _ptr(d_ctrl), _n(d_ctrl, 1, "d_ctrl"), _ptr(d_data),
+                                  _n(d_data, 4, "d_data"), _ptr(d_tiles), _n(d_tiles, 1, "d_tiles") // TILE_BYTES,
+                                  _ptr(d_totals), _ptr(d_scratch), _n(d_scratch, 1, "d_scratch"), _stream(stream)),
            "gc_encode_batch")
 
 
@@ -256,7 +265,7 @@ def gc_decode_scratch_size(codec: gc_codec, n: int, have_tiles: bool) -> int:
 
 def gc_build_tiles(codec, d_ctrl, ctrl_bytes, n, d_tiles, d_scratch, d_status, stream=None):
     _check(load().gc_build_tiles(ctypes.byref(codec), _ptr(d_ctrl), ctrl_bytes, n, _ptr(d_tiles),
-                                 _ptr(d_scratch), d_scratch.numel(), _ptr(d_status), _stream(stream)),
+                                 _ptr(d_scratch), _n(d_scratch, 1, "d_scratch"), _ptr(d_status), _stream(stream)),
            "gc_build_tiles")
 
 
@@ -264,7 +273,7 @@ def gc_decode(codec, d_ctrl, ctrl_bytes, d_data, data_words, n, d_tiles, d_out, 
               d_status, stream=None):
     _check(load().gc_decode(ctypes.byref(codec), _ptr(d_ctrl), ctrl_bytes, _ptr(d_data), data_words, n,
                             _ptr(d_tiles), _ptr(d_out), int(bool(restore_docids)), _ptr(d_scratch),
-                            d_scratch.numel(), _ptr(d_status), _stream(stream)), "gc_decode")
+                            _n(d_scratch, 1, "d_scratch"), _ptr(d_status), _stream(stream)), "gc_decode")
 
 
 DECODE_STATIC_MAX_INTS = 1 << 20
@@ -279,9 +288,9 @@ def gc_decode_static(codec, d_ctrl, ctrl_bytes, d_data, data_words, n, d_tiles, 
 
 
 def gc_decode_paper(codec, d_buf, n, d_out, restore_docids, d_scratch, d_status, stream=None):
-    _check(load().gc_decode_paper(ctypes.byref(codec), _ptr(d_buf), d_buf.numel(), n, _ptr(d_out),
-                                  int(bool(restore_docids)), _ptr(d_scratch), d_scratch.numel(), _ptr(d_status),
-                                  _stream(stream)), "gc_decode_paper")
+    _check(load().gc_decode_paper(ctypes.byref(codec), _ptr(d_buf), _n(d_buf, 1, "d_buf"), n, _ptr(d_out),
+                                  int(bool(restore_docids)), _ptr(d_scratch), _n(d_scratch, 1, "d_scratch"),
+                                  _ptr(d_status), _stream(stream)), "gc_decode_paper")
 
 
 def gc_decode_batch_scratch_size(nlists: int, max_tiles: int) -> int:
@@ -293,27 +302,30 @@ def gc_decode_batch_scratch_size(nlists: int, max_tiles: int) -> int:
 def gc_decode_batch(codec, d_lists, nlists, d_ctrl_pool, d_data_pool, d_tile_pool, d_out_pool, restore_docids,
                     max_tiles, launch, d_scratch, d_status, stream=None):
     lp = ctypes.byref(launch) if launch is not None else None
-    tile_len = d_tile_pool.numel() // TILE_BYTES if d_tile_pool is not None else 0
+    tile_len = _n(d_tile_pool, 1, "d_tile_pool") // TILE_BYTES if d_tile_pool is not None else 0
     _check(load().gc_decode_batch(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_ctrl_pool),
-                                  d_ctrl_pool.numel(), _ptr(d_data_pool), d_data_pool.numel(),
-                                  _ptr(d_tile_pool), tile_len, _ptr(d_out_pool), d_out_pool.numel(),
-                                  int(bool(restore_docids)), max_tiles, lp, _ptr(d_scratch), d_scratch.numel(),
-                                  _ptr(d_status), _stream(stream)), "gc_decode_batch")
+                                  _n(d_ctrl_pool, 1, "d_ctrl_pool"), _ptr(d_data_pool),
+                                  _n(d_data_pool, 4, "d_data_pool"), _ptr(d_tile_pool), tile_len, _ptr(d_out_pool),
+                                  _n(d_out_pool, 4, "d_out_pool"), int(bool(restore_docids)), max_tiles, lp,
+                                  _ptr(d_scratch), _n(d_scratch, 1, "d_scratch"), _ptr(d_status), _stream(stream)),
+           "gc_decode_batch")
 
 
 def gc_plan_batch(codec, d_lists, nlists, d_tile_pool, d_ctrl_pool, d_work, d_count, d_status, stream=None):
-    tile_len = d_tile_pool.numel() // TILE_BYTES if d_tile_pool is not None else 0
+    tile_len = _n(d_tile_pool, 1, "d_tile_pool") // TILE_BYTES if d_tile_pool is not None else 0
     _check(load().gc_plan_batch(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_tile_pool), tile_len,
-                                _ptr(d_ctrl_pool), d_ctrl_pool.numel(), _ptr(d_work), d_work.numel() // WORK_BYTES,
-                                _ptr(d_count), _ptr(d_status), _stream(stream)), "gc_plan_batch")
+                                _ptr(d_ctrl_pool), _n(d_ctrl_pool, 1, "d_ctrl_pool"), _ptr(d_work),
+                                _n(d_work, 1, "d_work") // WORK_BYTES, _ptr(d_count), _ptr(d_status),
+                                _stream(stream)), "gc_plan_batch")
 
 
 def gc_plan_select(codec, d_lists, nlists, d_sel, d_out_offs, nsel, d_tile_pool, d_ctrl_pool, d_work, d_count,
                    d_status, stream=None):
-    tile_len = d_tile_pool.numel() // TILE_BYTES if d_tile_pool is not None else 0
+    tile_len = _n(d_tile_pool, 1, "d_tile_pool") // TILE_BYTES if d_tile_pool is not None else 0
     _check(load().gc_plan_select(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_sel), _ptr(d_out_offs), nsel,
-                                 _ptr(d_tile_pool), tile_len, _ptr(d_ctrl_pool), d_ctrl_pool.numel(), _ptr(d_work),
-                                 d_work.numel() // WORK_BYTES, _ptr(d_count), _ptr(d_status), _stream(stream)),
+                                 _ptr(d_tile_pool), tile_len, _ptr(d_ctrl_pool), _n(d_ctrl_pool, 1, "d_ctrl_pool"),
+                                 _ptr(d_work), _n(d_work, 1, "d_work") // WORK_BYTES, _ptr(d_count), _ptr(d_status),
+                                 _stream(stream)),
            "gc_plan_select")
 
 
@@ -326,10 +338,12 @@ def gc_decode_plan_scratch_size(work_cap: int) -> int:
 def gc_decode_plan(codec, d_work, d_count, d_ctrl_pool, d_data_pool, d_out_pool, restore_docids, launch, d_scratch,
                    d_status, stream=None):
     lp = ctypes.byref(launch) if launch is not None else None
-    _check(load().gc_decode_plan(ctypes.byref(codec), _ptr(d_work), _ptr(d_count), d_work.numel() // WORK_BYTES,
-                                 _ptr(d_ctrl_pool), d_ctrl_pool.numel(), _ptr(d_data_pool), d_data_pool.numel(),
-                                 _ptr(d_out_pool), d_out_pool.numel(), int(bool(restore_docids)), lp,
-                                 _ptr(d_scratch), d_scratch.numel(), _ptr(d_status), _stream(stream)),
+    _check(load().gc_decode_plan(ctypes.byref(codec), _ptr(d_work), _ptr(d_count),
+                                 _n(d_work, 1, "d_work") // WORK_BYTES, _ptr(d_ctrl_pool),
+                                 _n(d_ctrl_pool, 1, "d_ctrl_pool"), _ptr(d_data_pool),
+                                 _n(d_data_pool, 4, "d_data_pool"), _ptr(d_out_pool), _n(d_out_pool, 4, "d_out_pool"),
+                                 int(bool(restore_docids)), lp, _ptr(d_scratch), _n(d_scratch, 1, "d_scratch"),
+                                 _ptr(d_status), _stream(stream)),
            "gc_decode_plan")
 
 
@@ -590,12 +604,14 @@ def gc_intersect_scratch_size(a_ints: int, a_tiles: int, b_tiles: int) -> int:
 
 def gc_intersect(index, d_a, d_b, d_a_offs, d_b_tile_offs, nqueries, a_ints, a_tiles, b_tiles, d_out, d_counts,
                  d_scratch, d_status, stream=None):
-    tile_len = index.tiles.numel() // TILE_BYTES
+    tile_len = _n(index.tiles, 1, "index.tiles") // TILE_BYTES
+    if _n(d_out, 4, "d_out") < a_ints or _n(d_counts, 4, "d_counts") < nqueries:
+        raise ValueError("gc_intersect: d_out must hold a_ints and d_counts nqueries uint32")
     _check(load().gc_intersect(ctypes.byref(index.codec), _ptr(index.lists), index.nlists, _ptr(index.tiles), tile_len,
-                               _ptr(index.ctrl), index.ctrl.numel(), _ptr(index.data), index.data.numel(), _ptr(d_a),
-                               _ptr(d_b), _ptr(d_a_offs), _ptr(d_b_tile_offs), nqueries, a_ints, a_tiles, b_tiles,
-                               _ptr(d_out), _ptr(d_counts), _ptr(d_scratch), d_scratch.numel(), _ptr(d_status),
-                               _stream(stream)),
+                               _ptr(index.ctrl), _n(index.ctrl, 1, "index.ctrl"), _ptr(index.data),
+                               _n(index.data, 4, "index.data"), _ptr(d_a), _ptr(d_b), _ptr(d_a_offs),
+                               _ptr(d_b_tile_offs), nqueries, a_ints, a_tiles, b_tiles, _ptr(d_out), _ptr(d_counts),
+                               _ptr(d_scratch), _n(d_scratch, 1, "d_scratch"), _ptr(d_status), _stream(stream)),
            "gc_intersect")
 
 
@@ -698,16 +714,19 @@ def gc_vb_encode_batch(d_gaps, d_in_off, d_n, nlists, d_lists, d_bytes, d_total,
     scratch = torch.empty(max(256, b.value), dtype=torch.uint8, device=dev)
     st = new_status(dev) if status is None else status
     _check(load().gc_vb_encode_batch(_ptr(d_gaps), _ptr(d_in_off), _ptr(d_n), nlists, _ptr(d_lists), _ptr(d_bytes),
-                                     d_bytes.numel(), _ptr(d_total), _ptr(scratch), scratch.numel(), _ptr(st),
-                                     _stream(stream)),
+                                     _n(d_bytes, 1, "d_bytes"), _ptr(d_total), _ptr(scratch), scratch.numel(),
+                                     _ptr(st), _stream(stream)),
            "gc_vb_encode_batch")
     if status is None:
         check_status(st, "gc_vb_encode_batch")
 
 
 def gc_vb_decode_batch(d_lists, nlists, d_bytes, d_out, restore_docids, d_status, stream=None):
-    _check(load().gc_vb_decode_batch(_ptr(d_lists), nlists, _ptr(d_bytes), d_bytes.numel(), _ptr(d_out), d_out.numel(),
-                                     int(bool(restore_docids)), _ptr(d_status), _stream(stream)),
+    if _n(d_lists, 1, "d_lists") < nlists * VB_LIST_BYTES:
+        raise ValueError("d_lists: fewer than nlists records")
+    _check(load().gc_vb_decode_batch(_ptr(d_lists), nlists, _ptr(d_bytes), _n(d_bytes, 1, "d_bytes"), _ptr(d_out),
+                                     _n(d_out, 4, "d_out"), int(bool(restore_docids)), _ptr(d_status),
+                                     _stream(stream)),
            "gc_vb_decode_batch")
 
 

@@ -154,3 +154,19 @@ def test_vb_batch_validates_on_the_host(gc):
     assert lib.gc_vb_encode_batch(None, None, None, 3, None, None, 0, None, None, 0, None, None) == 1
     b = ctypes.c_uint64()
     assert lib.gc_vb_encode_batch_scratch_size(5000, ctypes.byref(b)) == 0 and b.value >= 5000 * 8
+
+
+def test_binding_refuses_buffers_of_the_wrong_kind(gc):
+    """The binding passes buffer sizes in the units the C ABI takes (bytes
+    for byte pools, uint32 for words): a buffer of another element size, or
+    one not on the GPU, is refused before the library is called."""
+    import torch
+    c = gc.make_codec(gc.SIMPLE, 32)
+    host = torch.zeros(64, dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        gc.gc_vb_decode_batch(host, 1, host, host, True, None)
+    with pytest.raises(ValueError):
+        gc.gc_decode(c, host, 4, host, 4, 10, None, host, True, host, None)
+    from paper_1502_01916_gb300 import gc as binding
+    with pytest.raises(ValueError):
+        binding._n(torch.zeros(4, dtype=torch.int64), 4, "d_out")
