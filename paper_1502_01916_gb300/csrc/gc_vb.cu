@@ -180,17 +180,15 @@ __device__ __forceinline__ bool vb_list(const uint8_t* p, uint32_t nbytes, uint3
   return pos == nbytes;
 }
 
-// What a warp keeps of its group of 32 lists: list j's first byte (past
-// the group's lists, the group's length), its numbers and output offset;
-// the number ends before its first byte and the running sum of the group's
-// numbers before its first number, each first within the segment that
-// holds that byte, then within the group.
+// What a warp keeps of its group of 32 lists, per list j.
 struct GroupTab {
-  uint32_t s[33];
-  uint32_t n[32];
-  uint32_t m[32], mp[32];
-  uint32_t b[32], bp[32];
-  uint64_t oo[32];
+  uint32_t s[33];   // its first byte in the group (past the group's lists: the group's length)
+  uint32_t n[32];   // its numbers
+  uint32_t m[32];   // number ends in the group before its first byte
+  uint32_t mp[32];  // ... within the segment that holds that byte
+  uint32_t b[32];   // running sum of the group's numbers before its first number
+  uint32_t bp[32];  // ... within the segment that holds its first byte
+  uint64_t oo[32];  // its output offset
 };
 
 // Lane t's part of a group whose bytes p[0 .. len) lie back to back: the
