@@ -401,8 +401,12 @@ gc_status gc_vb_encode_batch(const uint32_t* d_gaps, const uint64_t* d_in_off, c
  * list's docIDs (its own prefix sum, modulo 2^32) when restore_docids. A
  * record that points outside the pools reports GC_ERR_INVALID, a list whose
  * bytes end inside a number, hold a number wider than 32 bits or are left
- * over reports GC_ERR_CORRUPT (the list's list index in d_status[1]).
- * Asynchronous on `stream`. */
+ * over reports GC_ERR_CORRUPT (the list's list index in d_status[1]);
+ * leading zero groups are accepted. A malformed list writes only inside its
+ * own output range; the other lists decode as if it were absent. Lists
+ * whose bytes lie back to back (as gc_vb_encode_batch writes them) decode
+ * fastest: their warp splits their bytes evenly over its lanes. Asynchronous
+ * on `stream`. */
 gc_status gc_vb_decode_batch(const gc_vb_list* d_lists, uint64_t nlists, const uint8_t* d_bytes, uint64_t bytes_len,
                              uint32_t* d_out, uint64_t out_len, int restore_docids, uint32_t* d_status,
                              void* stream);
