@@ -373,6 +373,7 @@ gc_status gc_vb_encode_batch(const uint32_t* d_gaps, const uint64_t* d_in_off, c
   cudaStream_t s = (cudaStream_t)stream;
   if (nlists == 0) return cudaMemsetAsync(d_total, 0, 8, s) == cudaSuccess ? GC_OK : GC_ERR_CUDA;
   if (!d_gaps || !d_in_off || !d_n || !d_lists || !d_scratch || (!d_bytes && bytes_cap)) return GC_ERR_INVALID;
+  if (nlists > 0xffffffffull) return GC_ERR_UNSUPPORTED;  // (list indices are reported as uint32)
   uint64_t need = 0;
   gc_vb_encode_batch_scratch_size(nlists, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
@@ -404,6 +405,7 @@ gc_status gc_vb_decode_batch(const gc_vb_list* d_lists, uint64_t nlists, const u
   gc_host::reset_launches();
   if (nlists == 0) return GC_OK;
   if (!d_lists || !d_out || (!d_bytes && bytes_len)) return GC_ERR_INVALID;
+  if (nlists > 0xffffffffull) return GC_ERR_UNSUPPORTED;  // (list indices are reported as uint32)
   gcvb::Dec d = {};
   d.lists = d_lists;
   d.nlists = nlists;

@@ -152,6 +152,9 @@ def test_vb_batch_validates_on_the_host(gc):
     assert lib.gc_vb_decode_batch(None, 0, None, 0, None, 0, 1, None, None) == 0
     assert lib.gc_vb_decode_batch(None, 3, None, 0, None, 0, 1, None, None) == 1
     assert lib.gc_vb_encode_batch(None, None, None, 3, None, None, 0, None, None, 0, None, None) == 1
+    buf = (ctypes.c_uint8 * 64)()
+    p = ctypes.addressof(buf)
+    assert lib.gc_vb_decode_batch(p, 1 << 32, p, 64, p, 16, 1, None, None) == 6  # more lists than uint32 indices
     b = ctypes.c_uint64()
     assert lib.gc_vb_encode_batch_scratch_size(5000, ctypes.byref(b)) == 0 and b.value >= 5000 * 8
 
