@@ -56,7 +56,8 @@ def parse():
     p.add_argument("--zeta", type=float, default=0.10)
     p.add_argument("--warps", type=int, default=0, help="warps per block (0 = library default)")
     p.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = as many as fit)")
-    p.add_argument("--claim", type=int, default=0, help="tiles per claim (0 = library default)")
+    p.add_argument("--claim", type=int, default=0, help="plan records per claim (0 = library default)")
+    p.add_argument("--stage", type=int, default=0, help="staging ring bytes per block (0 = all that fits)")
     p.add_argument("--no-tune", action="store_true", help="library default launch shape instead of the autotuner's")
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -303,15 +304,15 @@ def main():
     # or the autotuner's choice (timed on this index, before the timed region)
     launches_cfg, tuned = {}, {}
     for n, idx in idxs.items():
-        if a.warps or a.bps or a.claim:
-            launches_cfg[n] = gc.gc_launch(a.warps, a.bps, a.claim)
+        if a.warps or a.bps or a.claim or a.stage:
+            launches_cfg[n] = gc.gc_launch(a.warps, a.bps, a.claim, a.stage)
         elif a.no_tune:
             launches_cfg[n] = None
         else:
             from paper_1502_01916_gb300.tune import tune
             launches_cfg[n], info = tune(idx, plans[n], use_cache=False)
             tuned[n] = {"shape": [launches_cfg[n].warps_per_block, launches_cfg[n].blocks_per_sm,
-                                  launches_cfg[n].items_per_claim], "ms": info["ms"]}
+                                  launches_cfg[n].items_per_claim, launches_cfg[n].stage_bytes], "ms": info["ms"]}
 
     # correctness at full size: every docID against the host's prefix sums
     # (the zeros between lists leave the running sum unchanged), and the
@@ -573,8 +574,9 @@ def main():
                    "k": a.k, "l2": "inputs and outputs larger than L2 (no flush)",
                    "output": f"each list at a 16-byte aligned offset ({out_len - total_ints} padding ints)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "launch": ({n: {"warps_per_block": l.warps_per_block, "blocks_per_sm": l.blocks_per_sm or "max",
-                                   "items_per_claim": l.items_per_claim} if l is not None else "library default"
+                   "launch": ({n: {"warps_per_block": l.warps_per_block, "blocks_per_sm": l.blocks_per_sm,
+                                   "items_per_claim": l.items_per_claim, "stage_bytes": l.stage_bytes}
+                               if l is not None else "library default"
                                for n, l in launches_cfg.items()}),
                    "autotuned": tuned or None,
                    "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},

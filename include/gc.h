@@ -162,18 +162,28 @@ enum {
   GC_WORK_PUBLISH = 1u << 30
 };
 
-/* Launch shape of the persistent decoder (NULL = the library default).
- * warps_per_block: 1..16 (default 4; lowered to what one block's shared
- * memory holds, about 15 KB a warp); blocks_per_sm: resident blocks per SM
- * to launch (0 = as many as fit); the persistent grid is blocks_per_sm *
- * SMs. items_per_claim: 1..16 tiles a warp takes from the shared counter
- * per atomic (0 = default 16). A plan with tiles that take their prefix by
- * look-back is claimed one tile at a time whatever this says, so that the
- * tiles a warp holds never delay the tiles after them for long. */
+/* Launch shape of the persistent decoder (NULL = the library default; a
+ * field left 0 takes its default). A block has one staging warp, which
+ * claims plan records, groups them into packs of up to 32 lines of 32 ints
+ * and copies each pack's bytes into a shared-memory ring, and
+ * warps_per_block decoding warps, which decode the packs in turn.
+ *   warps_per_block: decoding warps per block, 1..23 at k = 32 (default
+ *     7), 1..15 at k = 4 (default 7).
+ *   blocks_per_sm: resident blocks per SM, 1..8 (default 3 at k = 32, 2
+ *     at k = 4); the
+ *     persistent grid is blocks_per_sm * SMs (fewer when fewer fit). A
+ *     block takes 1/blocks_per_sm of the SM's shared memory.
+ *   items_per_claim: 1..32 plan records a block takes from the shared
+ *     counter per atomic (default 32).
+ *   stage_bytes: bytes of the block's staging ring (the staging depth:
+ *     how much compressed data is in flight per block); 0 = all the
+ *     shared memory the block's share leaves. A shape whose ring would be
+ *     smaller than 12 KB is refused with GC_ERR_INVALID. */
 typedef struct gc_launch {
   uint32_t warps_per_block;
   uint32_t blocks_per_sm;
   uint32_t items_per_claim;
+  uint32_t stage_bytes;
 } gc_launch;
 
 /* ------------------------------------------------------------- sizes */

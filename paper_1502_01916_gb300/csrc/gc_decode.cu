@@ -2,26 +2,31 @@
 //
 // Decoding runs a plan: one 64-byte record (gc_work) per 1024-int tile of
 // every list, giving the unit that holds the tile's first row and the exact
-// byte ranges of the tile's control and data streams. The persistent
-// kernel's warps work independently. Each warp
-//   1. claims records from a shared counter and keeps them in shared memory;
-//   2. stages every claimed tile's data vectors, control window and
-//      (Group-PFD) exception records in its own shared-memory ring with bulk
-//      asynchronous copies (cp.async.bulk, one mbarrier per tile), up to 16
-//      tiles ahead of the one it decodes;
-//   3. decodes a pack of up to 32 lines of 32 consecutive ints (one full
-//      tile, or several small tiles together): the control patterns become
-//      one (word, shift, width) entry per row -- Table III selectors
-//      (Sec 4.3), Eq. 2 length descriptors (Sec 5.2.3, 5.3.1), AFOR frame
-//      bytes (Sec 6.1), PFD frame headers (Sec 6.2 decoding Step 1) -- then
-//      lane l extracts the 32 ints of line l with funnel shifts, in a
-//      rotated column order that keeps shared-memory banks apart, patches
-//      Group-PFD exceptions over their slots (Step 3) and sums them;
-//   4. restores docIDs (Sec 2.1.1): a segmented warp scan joins the line
-//      sums of each tile, and a tile starts from its base (a skip entry of
-//      the index) or, without one, from the tiles before it by a bounded
-//      decoupled look-back;
-//   5. transposes the ints through shared memory and stores 128-byte rows.
+// byte ranges of the tile's control and data streams. The persistent kernel
+// gives each block one staging warp and several decoding warps that share a
+// shared-memory ring:
+//   - the staging warp claims 32 records at a time from a shared counter
+//     (one bulk copy brings them into shared memory), sizes every tile's
+//     staging in parallel (one lane per record), groups the records into
+//     packs of up to 32 lines of 32 consecutive ints (one whole tile, or
+//     several small tiles together), places each pack in the ring and
+//     issues its bulk asynchronous copies (cp.async.bulk, one mbarrier per
+//     pack). At k = 32 every 128-byte data vector lands at a 144-byte pitch,
+//     so that the lanes of a warp reading 32 different rows hit different
+//     banks;
+//   - decoding warp w takes packs w, w + W, w + 2W, ...: the control
+//     patterns become one (word, shift, width) entry per row -- Table III
+//     selectors (Sec 4.3), Eq. 2 length descriptors (Sec 5.2.3, 5.3.1),
+//     AFOR frame bytes (Sec 6.1), PFD frame headers (Sec 6.2 decoding
+//     Step 1) -- lane l extracts the 32 ints of line l with funnel shifts,
+//     Group-PFD exceptions are patched over their slots (Step 3), the
+//     running sum of the line goes to a per-warp transpose buffer, and the
+//     pack's ring bytes are given back;
+//   - docIDs (Sec 2.1.1): a warp scan joins the line sums of each tile, and
+//     a tile starts from its base (a skip entry of the index) or, without
+//     one, from the tiles before it by a bounded decoupled look-back;
+//   - 16-byte chunks of the transpose buffer, plus each line's base, go out
+//     as coalesced 16-byte stores.
 #include <cstdint>
 #include <mutex>
 #include <cuda_runtime.h>
@@ -41,17 +46,23 @@ __device__ __forceinline__ uint64_t now_ns() {
   return t;
 }
 
-constexpr int kRing = 6144;     // staging ring bytes per warp (one tile needs at most 5760)
-constexpr int kSeq = 16;        // claimed records kept per warp
-constexpr int kFly = 16;        // tiles staged at once per warp (one mbarrier each)
-constexpr int kCtrlCap = 512;   // control bytes staged per tile at most
-constexpr int kExcCap = 1024;   // exception bytes staged per tile (all or none)
+constexpr int kChunk = 32;               // plan records per claim (one per lane of the staging warp)
+constexpr int kNRec = 96;                // record slots per block
+constexpr int kNChunk = kNRec / kChunk;  // claims whose records a block holds at once
+constexpr int kMaxSlots = 64;            // pack slots per block (one mbarrier pair each)
+constexpr int kCtrlCap = 512;            // control bytes staged per tile at most
+constexpr int kExcCap = 1024;            // exception bytes staged per tile (all or none)
+constexpr int kVecPitch = 144;           // k = 32: ring bytes per staged 128-byte data vector
+constexpr int kVecWords = kVecPitch / 4;
+constexpr int kPackCap = 12288;          // ring bytes one pack may take at most
+constexpr int kPadVec4 = 272;            // k = 4: data vectors of a pack, re-laid at 4 words each plus one per 8
 
-static_assert(kFly == kSeq, "a claimed record's staging slot is its record slot");
+static_assert(kNRec % kChunk == 0, "record slots hold whole claims");
 
-constexpr int kPadVec = 34;     // k = 32: data vectors of a pack, re-laid at 33 words each
-constexpr int kPadVec4 = 272;   // k = 4: data vectors of a pack, re-laid at 4 words each plus one per 8
-constexpr int kPad = 33;        // words per re-laid vector (one bank apart per vector)
+// A record slot taken from a warp's buffers or a pack's first slot plus a
+// lane: kept inside the record arrays (a pack's records lie in one claim's
+// buffer, so for the pack's own lanes this is the identity).
+__device__ __forceinline__ uint32_t rslot(uint32_t x) { return x < (uint32_t)kNRec ? x : (uint32_t)kNRec - 1; }
 
 template <int K>
 struct Geo {
@@ -59,38 +70,44 @@ struct Geo {
   static constexpr int RPL = 32 / K;         // rows per 32-int line (K = 4: 8, K = 32: 1)
   static constexpr int PROWS = 32 * RPL;     // row entries of a pack
   static constexpr int MAXVEC = TR + 1;      // data vectors a tile spans at most
-  // k = 32: the pack's data re-laid at 33 words per vector; k = 4: a 32 x 32
-  // transpose buffer
-  static constexpr int TBW = K == 32 ? kPadVec * kPad : 4 * kPadVec4 + kPadVec4 / 8;
-
+  // k = 32: the pack's 32 lines (transpose buffer); k = 4: the pack's data
+  // re-laid, then the transpose buffer
+  static constexpr int TBW = K == 32 ? 32 * 32 : 4 * kPadVec4 + kPadVec4 / 8;
+  static constexpr int VB = K == 32 ? kVecPitch : 16;  // ring bytes per staged data vector
+  static constexpr int THREADS = K == 32 ? 768 : 512;  // launch bound of the kernel
 };
 
+// What the staging warp and the decoding warps of a block share.
+struct __align__(128) BlockSmem {
+  uint4 rec[kNRec][4];        // claimed plan records
+  uint32_t item[kNRec];       // plan index of each
+  uint32_t at[kNRec];         // ring offset of its staged bytes (its decoding warp writes it)
+  uint32_t rrel[kNRec];       // the same, from its pack's start
+  uint16_t fvecs[kNRec];      // data vectors staged for it
+  uint16_t cst[kNRec];        // control bytes staged
+  uint16_t xst[kNRec];        // exception bytes staged
+  uint8_t flines[kNRec];      // its 32-int lines (0: not decoded)
+  uint32_t pk[kMaxSlots];     // pack: first record slot | records << 8 | lines << 16 (0 records: stop)
+  uint32_t prel[kMaxSlots];   // ring bytes the pack gives back
+  uint32_t ppos[kMaxSlots];   // ring offset of the pack
+  unsigned long long full[kMaxSlots];   // pack staged
+  unsigned long long empty[kMaxSlots];  // pack decoded
+  unsigned long long recbar[kNChunk];   // records of a claim copied
+};
+
+// One decoding warp's own buffers.
 template <int K>
 struct __align__(128) WarpSmem {
-  uint8_t ring[kRing];                   // staged tiles (data 128-byte aligned)
-  uint32_t tb[Geo<K>::TBW];              // re-laid data / transpose buffer
-  uint4 rec[kSeq][4];                    // claimed records
-  unsigned long long mbar[kFly];
-  uint32_t item[kSeq];                   // plan index of each claimed record
-  uint32_t at[kFly];                     // ring offset of each staged tile
-  uint32_t end[kFly];                    // ring bytes it gives back when decoded
-  uint16_t cst[kFly], xst[kFly];         // control / exception bytes staged
-  uint16_t need[kFly];                   // ring bytes it takes (all staged bytes, 128-byte rounded)
-  uint8_t flines[kFly];                  // 32-int lines of each staged tile (0: not decoded)
-  uint16_t fvecs[kFly];                  // data vectors staged for it
-  unsigned long long iout[32];           // pack item (by rank among decoded ones): first output int
-  uint32_t inint[32];                    // its ints
-  uint32_t ibase[32];                    // its docID base
-  uint32_t irec[32];                     // its record slot | first re-laid vector << 8
-  uint32_t rw[Geo<K>::PROWS];            // row: ring word of its first word (lane 0)
+  uint32_t tb[Geo<K>::TBW];              // transpose buffer (k = 4: re-laid data first)
+  uint32_t rw[Geo<K>::PROWS];            // row: word of its first word (lane 0)
   uint32_t rs[Geo<K>::PROWS];            // row: shift | width << 8
+  unsigned long long iout[32];           // pack item (by rank among decoded ones): first output int
   unsigned long long lout[32];           // line: output index of its first int
+  uint32_t inint[32];                    // item: its ints
+  uint32_t ibase[32];                    // item: its docID base
+  uint32_t irec[32];                     // item: its record slot
   uint32_t lnv[32];                      // line: ints it holds
 };
-
-// k = 32: four blocks of four warps fit an SM's 228 KB (with 1 KB reserved
-// per block)
-static_assert(sizeof(WarpSmem<32>) * 4 + 1024 <= 233472 / 4, "per-warp shared memory outgrew 16 warps per SM");
 
 struct DecodeArgs {
   const gc_work* work;
@@ -105,7 +122,8 @@ struct DecodeArgs {
   uint32_t* counter;        // claim counter (zeroed before the launch)
   unsigned long long* lb;   // look-back word per record (zeroed when restoring)
   uint32_t cg, ld;
-  uint32_t claim;           // records per claim when no record needs look-back
+  uint32_t claim;           // records per claim (1..32)
+  uint32_t ring_bytes;      // staging ring of a block
   uint32_t* status;
 };
 
@@ -117,10 +135,12 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t coun
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
   asm volatile(
@@ -129,14 +149,43 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+// 16 bytes global -> shared through the load path (not the bulk-copy unit:
+// a 16-byte copy costs the issuing warp about as much as a load)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// whether the phase of `bar` with this parity has completed (no waiting)
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+// Waits for the phase of `bar` with this parity; the thread is suspended
+// (it issues nothing) until the phase completes or about 0.1 ms passes.
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+      : "memory");
+  return ok != 0;
+}
+// Every lane of the warp waits for the phase of `bar` with this parity to
+// complete; false (in every lane) when it has not after kWaitNs.
+__device__ __forceinline__ bool wait_warp(unsigned long long* bar, uint32_t parity) {
+  bool ok = mbar_try_wait(bar, parity);
+  if (__all_sync(kFull, ok)) return true;
+  const uint64_t t0 = now_ns();
+  for (;;) {
+    if (!ok) ok = mbar_try_wait(bar, parity);
+    if (__all_sync(kFull, ok)) return true;
+    if (__any_sync(kFull, now_ns() - t0 > kWaitNs)) return false;
+  }
 }
 
 // ------------------------------------------------------------ control view
@@ -471,7 +520,7 @@ __device__ __forceinline__ bool parse_pfd4(const CtrlView& C, uint64_t f0, uint6
 // 32 l .., 16-byte chunk c at chunk c ^ (l & 7)); the tile's first line is
 // line0. Headers and records were checked by parse_pfd4; a position
 // outside its frame is reported.
-__device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, WarpSmem<4>& ws, const CtrlView& C, uint64_t f0,
+__device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, uint32_t* tb, const CtrlView& C, uint64_t f0,
                                            uint64_t exc_at, uint32_t rows, uint32_t line0, uint32_t list) {
   const uint32_t lane = lane_id();
   const uint32_t nfr = (rows + kPfdFrameRows - 1) / kPfdFrameRows;
@@ -509,11 +558,10 @@ __device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, WarpSmem<4>& ws,
       if (wbf > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
       const uint32_t i = fl * 128 + pos;  // int of the tile
       const uint32_t line = line0 + (i >> 5), col = i & 31u;
-      ws.tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
+      tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
     }
   }
 }
-
 // ------------------------------------------------------------ look-back
 
 // Decoupled look-back over the tiles of one list, a warp at a time: the
@@ -563,8 +611,8 @@ __device__ uint32_t look_back(const unsigned long long* lb, uint64_t item, uint6
 
 // ------------------------------------------------------------------ pack
 
-__device__ __forceinline__ const gc_work& rec_at(const uint4 (*rec)[4], uint32_t s) {
-  return *reinterpret_cast<const gc_work*>(rec[s % kSeq]);
+__device__ __forceinline__ const gc_work& rec_of(const BlockSmem& h, uint32_t s) {
+  return *reinterpret_cast<const gc_work*>(h.rec[s]);
 }
 
 __device__ __forceinline__ uint32_t w_nint(uint32_t shape) { return (shape & 1023u) + 1; }
@@ -582,64 +630,140 @@ __device__ __forceinline__ bool w_live(const gc_work& w, const DecodeArgs& a) {
          w.data_at % K == 0 && w.data_at + (uint64_t)vecs * K <= a.data_pool_words;
 }
 
+// The records of a pack, one per lane p < np (record slot s0 + p): each
+// one's lines and data vectors and where they start in the pack, whether
+// it is decoded (live) or only reported (dead: it failed its checks), and
+// its rank among the live ones. The live ones' output offsets, sizes and
+// record slots go to the warp's buffers by rank.
+struct Items {
+  uint32_t s, lines, line0, vecs, vec0;
+  bool live, dead;
+  uint32_t live_mask, heads, rank;
+  uint32_t item, tile, base, shape, list;
+  uint64_t out;
+};
+
+template <int K>
+__device__ __forceinline__ Items load_items(const BlockSmem& h, WarpSmem<K>& ws, uint32_t s0, uint32_t np) {
+  Items t;
+  const uint32_t lane = lane_id();
+  const bool inp = lane < np;
+  t.s = rslot(s0 + lane);
+  const uint32_t lv = inp ? (uint32_t)h.flines[t.s] | (uint32_t)h.fvecs[t.s] << 16 : 0u;
+  const uint32_t lvi = np == 1 ? lv : warp_incl_sum(lv);
+  t.lines = lv & 0xffffu;
+  t.vecs = lv >> 16;
+  t.line0 = (lvi & 0xffffu) - t.lines;
+  t.vec0 = (lvi >> 16) - t.vecs;
+  t.live = t.lines > 0;
+  t.live_mask = __ballot_sync(kFull, t.live);
+  t.heads = np == 1 ? (t.live_mask & 1u) : __reduce_or_sync(kFull, t.live ? 1u << t.line0 : 0u);
+  t.item = 0;
+  t.tile = 0;
+  t.base = 0;
+  t.shape = 0;
+  t.list = 0xffffffffu;
+  t.out = 0;
+  if (inp) {
+    const gc_work& w = rec_of(h, t.s);
+    t.item = h.item[t.s];
+    t.tile = w.tile;
+    t.base = w.base;
+    t.shape = w.shape;
+    t.list = w.list;
+    t.out = w.out_at;
+  }
+  t.dead = inp && !t.live && t.list != 0xffffffffu;
+  t.rank = __popc(t.live_mask & ((1u << lane) - 1u));
+  if (t.live) {
+    ws.iout[t.rank] = t.out;
+    ws.inint[t.rank] = w_nint(t.shape);
+    ws.irec[t.rank] = t.s;
+  }
+  return t;
+}
+
+// docIDs (Sec 2.1.1): line l holds the running sum R of its own ints; a
+// plain warp scan of the line totals, less the scan before the first line
+// of the line's item, is the sum of the item's ints before the line, and
+// the item's base is its skip entry or, without one, the sum of the list's
+// tiles before it by look-back (every item publishes its aggregate, then
+// its inclusive prefix, for the tiles after it). Returns each line's base.
+template <int K>
+__device__ __forceinline__ uint32_t line_bases(const DecodeArgs& a, WarpSmem<K>& ws, const Items& t, uint32_t np,
+                                               bool act, uint32_t R, uint32_t rank, uint32_t lhead) {
+  const uint32_t lane = lane_id();
+  const uint32_t T = act ? R : 0u;
+  const uint32_t V = warp_incl_sum(T);
+  const uint32_t shape0 = __shfl_sync(kFull, t.shape, 0);
+  if (np == 1 && t.heads == 1u && (shape0 & (GC_WORK_HAS_BASE | GC_WORK_PUBLISH)) == GC_WORK_HAS_BASE) {
+    // a pack of one live tile with its skip entry, which no other tile
+    // waits for
+    return V - T + __shfl_sync(kFull, t.base, 0);
+  }
+  const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
+  const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
+  const uint32_t E = v - T;
+  const uint32_t lastl = t.live ? t.line0 + t.lines - 1 : 0u;
+  const uint32_t tot = __shfl_sync(kFull, v, lastl);
+  const bool has_base = (t.shape & GC_WORK_HAS_BASE) != 0;
+  const bool needs_lb = t.live && t.tile > 0 && !has_base;
+  uint32_t base = has_base ? t.base : 0u;
+  if (a.lb) {
+    if (t.live && !needs_lb && (t.shape & GC_WORK_PUBLISH))
+      st_release(a.lb + t.item, kFlagPrefix | (uint32_t)(base + tot));
+    if (t.dead) st_release(a.lb + t.item, kFlagPrefix);  // its error is reported
+    if (needs_lb) st_release(a.lb + t.item, kFlagAgg | tot);
+  }
+  for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
+    const uint32_t p = __ffs(pend) - 1;
+    const uint32_t it = __shfl_sync(kFull, t.item, p);
+    const uint32_t tl = __shfl_sync(kFull, t.tile, p);
+    const uint32_t lst = __shfl_sync(kFull, t.list, p);
+    const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
+    if (lane == p) {
+      base = ex;
+      if (a.lb) st_release(a.lb + t.item, kFlagPrefix | (uint32_t)(ex + tot));
+    }
+  }
+  if (t.live) ws.ibase[t.rank] = base;
+  __syncwarp();
+  return E + (act ? ws.ibase[rank] : 0u);
+}
+
 // The k = 4 pack decoder (the paper's own layout): records s0 .. s0 + np - 1
-// of this warp's sequence (staged, their mbarriers complete), `nl` lines
-// in all. Each staged tile's 16-byte vectors are re-laid in shared memory,
+// of the block (staged, the pack's mbarrier complete), `nl` lines in all.
+// Each staged tile's 16-byte vectors are re-laid in the warp's buffer,
 // vector v of the pack at word 4 v + v / 8 (one spare word per 8 vectors,
 // so that lanes reading different rows mostly hit different banks); every
 // tile's control patterns become one (vector, shift, width) entry per row;
 // lane l then reads line l (32 ints: rows 8 l .. 8 l + 7 of the pack, 4
 // components each) in natural order. Group-PFD exceptions are patched into
-// the line-major buffer before the running sum.
+// the line-major buffer before the running sum. The pack's ring bytes are
+// given back (`empty`) once the data and control bytes are read.
 template <int KIND, bool RESTORE>
-__device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, uint32_t np, uint32_t nl,
-                             uint32_t lv, uint32_t lvi) {
+__device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4>& ws, const uint8_t* ring,
+                             uint32_t s0, uint32_t np, uint32_t nl, unsigned long long* empty) {
   constexpr uint32_t RPL = Geo<4>::RPL;  // rows per line (8)
   const uint32_t lane = lane_id();
-
-  // items: lane p < np holds item p, its lines and vectors (lv: lines |
-  // vectors << 16) and their inclusive sums over the pack (lvi)
-  const uint32_t my_lines = lv & 0xffffu;
-  const uint32_t my_vecs = lv >> 16;
-  const uint32_t my_line0 = (lvi & 0xffffu) - my_lines;
-  const uint32_t my_vec0 = (lvi >> 16) - my_vecs;
-  const bool my_live = my_lines > 0;
-  const uint32_t live = __ballot_sync(kFull, my_live);
-  const uint32_t heads = np == 1 ? (live & 1u) : __reduce_or_sync(kFull, my_live ? 1u << my_line0 : 0u);
-  uint32_t my_item = 0, my_tile = 0, my_base = 0, my_shape = 0, my_list = 0xffffffffu;
-  uint64_t my_out = 0;
-  if (lane < np) {
-    const gc_work& w = rec_at(ws.rec, s0 + lane);
-    my_item = ws.item[(s0 + lane) % kSeq];
-    my_tile = w.tile;
-    my_base = w.base;
-    my_shape = w.shape;
-    my_list = w.list;
-    my_out = w.out_at;
-  }
-  const bool my_dead = lane < np && !my_live && my_list != 0xffffffffu;
-  const uint32_t my_rank = __popc(live & ((1u << lane) - 1u));
-  if (my_live) {
-    ws.iout[my_rank] = my_out;
-    ws.inint[my_rank] = w_nint(my_shape);
-  }
+  const Items t = load_items<4>(h, ws, s0, np);
 
   // 1. per tile: re-lay its vectors, and turn its control patterns into one
   // (vector, shift, width) entry per row
   bool exc = false;  // (Group-PFD) a tile of the pack has exceptions
-  for (uint32_t lm = live; lm; lm &= lm - 1) {
+  for (uint32_t lm = t.live_mask; lm; lm &= lm - 1) {
     const uint32_t p = __ffs(lm) - 1;
-    const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
-    const uint32_t lines = __shfl_sync(kFull, my_lines, p);
-    const uint32_t v0 = __shfl_sync(kFull, my_vec0, p);
-    const gc_work& w = rec_at(ws.rec, s0 + p);
-    const uint32_t f = (s0 + p) % kFly;
-    const uint32_t at = ws.at[f];
-    const uint32_t vecs = ws.fvecs[f];
+    const uint32_t line0 = __shfl_sync(kFull, t.line0, p);
+    const uint32_t lines = __shfl_sync(kFull, t.lines, p);
+    const uint32_t v0 = __shfl_sync(kFull, t.vec0, p);
+    const uint32_t sp = rslot(s0 + p);
+    const gc_work& w = rec_of(h, sp);
+    const uint32_t at = h.at[sp];
+    const uint32_t vecs = h.fvecs[sp];
     {
       // lane l moves vector 32 i + l (one 16-byte load, four stores; the
       // stores of a step hit 32 different banks)
-      const uint4* src = reinterpret_cast<const uint4*>(ws.ring + at);
+      const uint4* src = reinterpret_cast<const uint4*>(ring + at);
       for (uint32_t v = lane; v < vecs; v += 32) {
         const uint4 x = src[v];
         const uint32_t g = v0 + v;
@@ -654,12 +778,12 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
     CtrlView C;
     C.g = a.ctrl_pool + w.ctrl_at;
     C.size = w.ctrl_bytes;
-    C.s1 = ws.ring + at + dbytes;
+    C.s1 = ring + at + dbytes;
     C.lo1 = w.win_at;
-    C.len1 = ws.cst[f];
-    C.s2 = ws.ring + at + dbytes + ws.cst[f];
+    C.len1 = h.cst[sp];
+    C.s2 = ring + at + dbytes + h.cst[sp];
     C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
-    C.len2 = ws.xst[f];
+    C.len2 = h.xst[sp];
     RowSink<4> out;
     out.rw = ws.rw + line0 * RPL;
     out.rs = ws.rs + line0 * RPL;
@@ -693,9 +817,9 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
 
   // 2. lane l reads line l: rows 8 l .. 8 l + 7, four components each
   const bool act = lane < nl;
-  const uint32_t upto = heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
-  const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;  // its item among the decoded ones
-  const uint32_t lhead = act ? 31u - __clz(upto) : 0u;          // the item's first line
+  const uint32_t upto = t.heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
+  const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;    // its item among the decoded ones
+  const uint32_t lhead = act ? 31u - __clz(upto) : 0u;            // the item's first line
   uint32_t r[32];
   uint32_t R = 0;
 #pragma unroll
@@ -727,24 +851,24 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
       for (int c = 0; c < 8; ++c) T[c ^ swz] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
     }
     __syncwarp();
-    for (uint32_t lm = live; lm; lm &= lm - 1) {
+    for (uint32_t lm = t.live_mask; lm; lm &= lm - 1) {
       const uint32_t p = __ffs(lm) - 1;
-      const uint32_t line0 = __shfl_sync(kFull, my_line0, p);
-      const gc_work& w = rec_at(ws.rec, s0 + p);
-      const uint32_t f = (s0 + p) % kFly;
-      const uint32_t at = ws.at[f];
-      const uint32_t dbytes = ws.fvecs[f] * 16;
+      const uint32_t line0 = __shfl_sync(kFull, t.line0, p);
+      const uint32_t sp = rslot(s0 + p);
+      const gc_work& w = rec_of(h, sp);
+      const uint32_t at = h.at[sp];
+      const uint32_t dbytes = h.fvecs[sp] * 16;
       CtrlView C;
       C.g = a.ctrl_pool + w.ctrl_at;
       C.size = w.ctrl_bytes;
-      C.s1 = ws.ring + at + dbytes;
+      C.s1 = ring + at + dbytes;
       C.lo1 = w.win_at;
-      C.len1 = ws.cst[f];
-      C.s2 = ws.ring + at + dbytes + ws.cst[f];
+      C.len1 = h.cst[sp];
+      C.s2 = ring + at + dbytes + h.cst[sp];
       C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
-      C.len2 = ws.xst[f];
+      C.len2 = h.xst[sp];
       const uint64_t row0 = (uint64_t)w.tile * Geo<4>::TR;
-      pfd_patch4(a, ws, C, row0 / kPfdFrameRows, w.exc_at, (w_nint(w.shape) + 3) / 4, line0, w.list);
+      pfd_patch4(a, ws.tb, C, row0 / kPfdFrameRows, w.exc_at, (w_nint(w.shape) + 3) / 4, line0, w.list);
     }
     __syncwarp();
     if (act) {
@@ -758,6 +882,9 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
       }
     }
   }
+  // the pack's staged bytes are read: give its ring bytes back
+  __syncwarp();
+  if (lane == 0) mbar_arrive(empty);
   if (RESTORE) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -766,55 +893,15 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
     }
   }
 
-  // 3. docIDs: segmented scan of line totals, then each item's base
-  uint32_t k0 = 0;
-  if (RESTORE) {
-    // (a plain scan, less the scan before the item's first line)
-    const uint32_t T = act ? R : 0u;
-    const uint32_t V = warp_incl_sum(T);
-    const uint32_t shape0 = __shfl_sync(kFull, my_shape, 0);
-    if (np == 1 && heads == 1u && (shape0 & (GC_WORK_HAS_BASE | GC_WORK_PUBLISH)) == GC_WORK_HAS_BASE) {
-      // a pack of one live tile with its skip entry, which no other tile
-      // waits for
-      k0 = V - T + __shfl_sync(kFull, my_base, 0);
-    } else {
-      const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
-      const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
-      const uint32_t E = v - T;
-      const uint32_t lastl = my_live ? my_line0 + my_lines - 1 : 0u;
-      const uint32_t tot = __shfl_sync(kFull, v, lastl);
-      const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
-      const bool needs_lb = my_live && my_tile > 0 && !has_base;
-      uint32_t base = has_base ? my_base : 0u;
-      if (a.lb) {
-        if (my_live && !needs_lb && (my_shape & GC_WORK_PUBLISH))
-          st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(base + tot));
-        if (my_dead) st_release(a.lb + my_item, kFlagPrefix);  // its error is reported
-        if (needs_lb) st_release(a.lb + my_item, kFlagAgg | tot);
-      }
-      for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
-        const uint32_t p = __ffs(pend) - 1;
-        const uint32_t it = __shfl_sync(kFull, my_item, p);
-        const uint32_t tl = __shfl_sync(kFull, my_tile, p);
-        const uint32_t lst = __shfl_sync(kFull, my_list, p);
-        const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
-        if (lane == p) {
-          base = ex;
-          if (a.lb) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(ex + tot));
-        }
-      }
-      if (my_live) ws.ibase[my_rank] = base;
-      __syncwarp();
-      k0 = E + (act ? ws.ibase[rank] : 0u);
-    }
-  }
+  // 3. docIDs: each line's base
+  const uint32_t k0 = RESTORE ? line_bases<4>(a, ws, t, np, act, R, rank, lhead) : 0u;
 
   // the re-laid data is read: its buffer takes the results, line l at words
   // 32 l .. 32 l + 31 with its 16-byte chunk c at chunk c ^ (l & 7), so that
   // the eight lanes of each quarter-warp touch eight different chunks both
   // here (a line per lane) and when reading (a chunk per lane, below)
   __syncwarp();
-  const bool whole = heads == 1u && ws.inint[0] == (uint32_t)kTileInts;  // one whole tile
+  const bool whole = t.heads == 1u && ws.inint[0] == (uint32_t)kTileInts;  // one whole tile
   if (act) {
     uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
     const uint32_t sw = lane & 7u;
@@ -870,25 +957,35 @@ __device__ void decode_pack4(const DecodeArgs& a, WarpSmem<4>& ws, uint32_t s0, 
   __syncwarp();
 }
 
-// One line (32 ints) of the k = 32 decoder in natural column order: word
-// (P[j], P[33 + j]) >> shift & mask, and the running sum (the prefix within
-// the line) when restoring docIDs.
-template <int KIND, bool RESTORE>
-__device__ __forceinline__ void extract_line(const uint32_t* P, uint32_t sh, uint32_t msk, bool cross,
-                                             uint32_t (&r)[32], uint32_t& R) {
+// One line (32 ints) of the k = 32 decoder: lane l reads its row's 32 words
+// (and, for values that cross a word, the next vector's) as eight 16-byte
+// chunks from the ring, where vectors sit 144 bytes apart: the eight lanes
+// of a quarter-warp read rows at most one vector apart each, so their
+// chunks fall in eight different 16-byte bank groups. Each value is a
+// funnel shift and a mask; with SUM the running sum (the prefix within the
+// line) replaces it, and R ends as the line's total. The results go to the
+// line's 16-byte chunks in the transpose buffer, chunk c at c ^ swz.
+template <int KIND, bool SUM>
+__device__ __forceinline__ void extract_line32(const uint4* P, uint32_t sh, uint32_t msk, bool cross, uint4* T,
+                                               uint32_t swz, uint32_t& R) {
   R = 0;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const uint32_t lo = P[j];
-    uint32_t hi = 0;
-    if (KIND != GC_SIMPLE && cross) hi = P[kPad + j];  // Group-Simple values never cross a word
-    const uint32_t v = __funnelshift_r(lo, hi, sh) & msk;
-    if (RESTORE) {
-      R += v;
-      r[j] = R;
-    } else {
-      r[j] = v;
+  for (int c = 0; c < 8; ++c) {
+    const uint4 lo = P[c];
+    uint4 hi = make_uint4(0u, 0u, 0u, 0u);
+    if (KIND != GC_SIMPLE && cross) hi = P[kVecPitch / 16 + c];  // Group-Simple values never cross a word
+    uint32_t v0 = __funnelshift_r(lo.x, hi.x, sh) & msk;
+    uint32_t v1 = __funnelshift_r(lo.y, hi.y, sh) & msk;
+    uint32_t v2 = __funnelshift_r(lo.z, hi.z, sh) & msk;
+    uint32_t v3 = __funnelshift_r(lo.w, hi.w, sh) & msk;
+    if (SUM) {
+      v0 += R;
+      v1 += v0;
+      v2 += v1;
+      v3 += v2;
+      R = v3;
     }
+    T[c ^ swz] = make_uint4(v0, v1, v2, v3);
   }
 }
 
@@ -900,25 +997,26 @@ __device__ __forceinline__ void extract_line(const uint32_t* P, uint32_t sh, uin
 // counts (less the scan before the tile's first lane) gives each
 // selector's first row; a line then takes the last of its tile's
 // selectors that starts at or before it. Returns the line's row entry in
-// registers (re-laid word of the row's first word, shift | width << 8) and
-// reports a tile whose selectors are malformed or do not cover its rows.
-__device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, WarpSmem<32>& ws, bool act, uint32_t lane,
-                                                    uint32_t heads, uint32_t nl, uint32_t rank, uint32_t lhead,
-                                                    uint32_t& ent, uint32_t& sw) {
-  // this line's tile (its record slot is also its staging slot)
-  const uint32_t im = act ? ws.irec[rank] : 0u;
-  const uint32_t f = im & 255u, v0 = im >> 8;
-  const gc_work& w = *reinterpret_cast<const gc_work*>(ws.rec[f]);
+// registers (ring word of the row's word in lane 0's stream, shift | width
+// << 8) and reports a tile whose selectors are malformed or do not cover
+// its rows.
+__device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, const BlockSmem& h, const WarpSmem<32>& ws,
+                                                    const uint8_t* ring, bool act, uint32_t lane, uint32_t heads,
+                                                    uint32_t nl, uint32_t rank, uint32_t lhead, uint32_t& ent,
+                                                    uint32_t& sw) {
+  // this line's tile (a lane past the pack's lines takes the first tile's)
+  const uint32_t s = rslot(ws.irec[act ? rank : 0u]);
+  const gc_work& w = rec_of(h, s);
+  const uint32_t at = h.at[s], vecs = h.fvecs[s];
   const uint32_t after = heads & ~(0xffffffffu >> (31u - lane));  // heads of later tiles
   const uint32_t rows = (after ? __ffs(after) - 1 : nl) - lhead;
   const uint32_t q = lane - lhead;
-  const uint32_t vecs = ws.fvecs[f];
   CtrlView C;
   C.g = a.ctrl_pool + w.ctrl_at;
   C.size = w.ctrl_bytes;
-  C.s1 = ws.ring + ws.at[f] + vecs * 128u;
+  C.s1 = ring + at + vecs * kVecPitch;
   C.lo1 = w.win_at;
-  C.len1 = ws.cst[f];
+  C.len1 = h.cst[s];
   C.s2 = nullptr;
   C.lo2 = 0;
   C.len2 = 0;
@@ -945,7 +1043,7 @@ __device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, WarpSme
   // selectors disagree)
   const bool out_of_range = k == 0 || (uint32_t)((int32_t)q - st) >= nu || b + wu > 32u * vecs;
   if (act && out_of_range) ok = false;
-  ent = act && !out_of_range ? v0 * kPad + (b >> 5) * kPad : v0 * kPad;
+  ent = (at >> 2) + (act && !out_of_range ? (b >> 5) * kVecWords : 0u);
   sw = act && !out_of_range ? (b & 31u) | (wu << 8) : 0u;
   if (!ok) report(a.status, GC_ERR_CORRUPT, w.list);
 }
@@ -955,7 +1053,7 @@ __device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, WarpSme
 // chunk c at chunk c ^ (l & 7)): e 16-bit positions at rp, then e values of
 // wb bytes (Sec 6.2, decoding Step 3); the tile's first line is hl, its
 // frame holds lim ints. A position outside the frame is reported.
-__device__ __forceinline__ void pfd_patch(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t lane, uint32_t hl, uint32_t e,
+__device__ __forceinline__ void pfd_patch(const DecodeArgs& a, uint32_t* tb, uint32_t lane, uint32_t hl, uint32_t e,
                                           uint32_t lim, uint32_t wb, const uint8_t* rp, uint32_t list) {
   const uint8_t* vp = rp + (size_t)e * 2;
   for (uint32_t x = lane; x < e; x += 32) {
@@ -969,7 +1067,7 @@ __device__ __forceinline__ void pfd_patch(const DecodeArgs& a, WarpSmem<32>& ws,
     if (wb > 1) v |= (uint32_t)v8[1] << 8;
     if (wb > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
     const uint32_t line = hl + (pos >> 5), col = pos & 31u;
-    ws.tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
+    tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
   }
 }
 
@@ -986,30 +1084,30 @@ struct PfdExc {
 // the first tile's). Returns the line's row entry in registers and its
 // tile's exception record; reports a tile whose header, row widths or
 // exception record are malformed.
-__device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, WarpSmem<32>& ws, bool act, uint32_t lane,
-                                                 uint32_t heads, uint32_t nl, uint32_t rank, uint32_t lhead,
-                                                 uint32_t& ent, uint32_t& sw, PfdExc& x) {
-  // this line's tile (its record slot is also its staging slot)
-  const uint32_t im = heads ? ws.irec[rank] : 0u;
-  const uint32_t f = im % kSeq, v0 = im >> 8;
-  const gc_work& w = *reinterpret_cast<const gc_work*>(ws.rec[f]);
+__device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, const BlockSmem& h, const WarpSmem<32>& ws,
+                                                 const uint8_t* ring, bool act, uint32_t lane, uint32_t heads,
+                                                 uint32_t nl, uint32_t rank, uint32_t lhead, uint32_t& ent,
+                                                 uint32_t& sw, PfdExc& x) {
+  // this line's tile (a lane past the pack's lines takes the first tile's)
+  const uint32_t s = rslot(ws.irec[heads ? rank : 0u]);
+  const gc_work& w = rec_of(h, s);
+  const uint32_t at = h.at[s], vecs = h.fvecs[s];
   const uint32_t after = heads & ~(0xffffffffu >> (31u - lane));  // heads of later tiles
   const uint32_t rows = (after ? __ffs(after) - 1 : nl) - lhead;
   const uint32_t q = lane - lhead;
-  const uint32_t vecs = ws.fvecs[f];
   CtrlView C;
   C.g = a.ctrl_pool + w.ctrl_at;
   C.size = w.ctrl_bytes;
-  C.s1 = ws.ring + ws.at[f] + vecs * 128u;
+  C.s1 = ring + at + vecs * kVecPitch;
   C.lo1 = w.win_at;
-  C.len1 = ws.cst[f];
-  C.s2 = C.s1 + ws.cst[f];
+  C.len1 = h.cst[s];
+  C.s2 = C.s1 + h.cst[s];
   C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
-  C.len2 = ws.xst[f];
+  C.len2 = h.xst[s];
   // the header
-  const uint64_t h = 4ull * w.tile;
-  bool ok = h + 4 <= C.size;
-  const uint32_t hdr = heads && ok ? C.le4(h) : 0u;
+  const uint64_t hp = 4ull * w.tile;
+  bool ok = hp + 4 <= C.size;
+  const uint32_t hdr = heads && ok ? C.le4(hp) : 0u;
   uint32_t b = hdr & 63u, wcode = (hdr >> 6) & 3u, e = hdr >> 8;
   if (b > 32 || wcode > 2) {
     ok = false;
@@ -1031,7 +1129,7 @@ __device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, WarpSmem<3
   const uint32_t rb = w_bit0(w.shape) + q * b;
   const bool oor = rb + b > 32u * vecs;
   if (oor) ok = false;
-  ent = !act ? 0u : oor ? v0 * kPad : v0 * kPad + (rb >> 5) * kPad;
+  ent = (at >> 2) + (act && !oor ? (rb >> 5) * kVecWords : 0u);
   sw = act && !oor ? (rb & 31u) | (b << 8) : 0u;
   if (act && !ok) report(a.status, GC_ERR_CORRUPT, w.list);
   x.rp = C.addr(w.exc_at, (uint64_t)e * (2 + wb));
@@ -1043,10 +1141,10 @@ __device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, WarpSmem<3
 
 // Group-PFD, k = 32: the exceptions of every tile of the pack over their
 // slots (a pack of one tile: every lane already holds its facts).
-__device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t lane, uint32_t heads,
+__device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, uint32_t* tb, uint32_t lane, uint32_t heads,
                                                  const PfdExc& x) {
   if (heads == 1u) {
-    pfd_patch(a, ws, lane, 0, x.e, x.lim, x.wb, x.rp, x.list);
+    pfd_patch(a, tb, lane, 0, x.e, x.lim, x.wb, x.rp, x.list);
     return;
   }
   for (uint32_t hm = heads; hm; hm &= hm - 1) {
@@ -1056,239 +1154,139 @@ __device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, WarpSmem<3
     const uint32_t wb = __shfl_sync(kFull, x.wb, hl);
     const uint32_t list = __shfl_sync(kFull, x.list, hl);
     const uint8_t* rp = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, (unsigned long long)x.rp, hl));
-    pfd_patch(a, ws, lane, hl, e, lim, wb, rp, list);
+    pfd_patch(a, tb, lane, hl, e, lim, wb, rp, list);
   }
 }
 
-// The k = 32 pack decoder. Each staged tile's data vectors are first re-laid
-// at 33 words per vector, so that the rows of a pack, one per lane, sit in
-// different banks whichever vectors they start in; lane l then reads line l
-// (one row of 32 ints) in natural column order with fixed offsets, and its
-// running sum is directly the prefix within the line.
+// The k = 32 pack decoder. Lane l decodes line l (row l of the pack) from
+// the ring, where the staging warp put every data vector 144 bytes apart,
+// and writes its running sums to line l of the transpose buffer; the scan
+// of the line totals gives each line's base, which is added as the buffer
+// goes out in 16-byte chunks. The pack's ring bytes are given back
+// (`empty`) once they are read.
 template <int KIND, bool RESTORE>
-__device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0, uint32_t np, uint32_t nl,
-                              uint32_t lv, uint32_t lvi) {
+__device__ void decode_pack32(const DecodeArgs& a, const BlockSmem& h, WarpSmem<32>& ws, const uint8_t* ring,
+                              uint32_t s0, uint32_t np, uint32_t nl, unsigned long long* empty) {
   const uint32_t lane = lane_id();
+  const Items t = load_items<32>(h, ws, s0, np);
 
-  // items: lane p < np holds item p, its lines and vectors (lv: lines |
-  // vectors << 16) and their inclusive sums over the pack (lvi)
-  const uint32_t my_lines = lv & 0xffffu;
-  const uint32_t my_vecs = lv >> 16;
-  const uint32_t my_line0 = (lvi & 0xffffu) - my_lines;
-  const uint32_t my_vec0 = (lvi >> 16) - my_vecs;
-  const bool my_live = my_lines > 0;
-  const uint32_t live = __ballot_sync(kFull, my_live);
-  const uint32_t heads = np == 1 ? (live & 1u) : __reduce_or_sync(kFull, my_live ? 1u << my_line0 : 0u);
-  uint32_t my_item = 0, my_tile = 0, my_base = 0, my_shape = 0, my_list = 0xffffffffu;
-  uint64_t my_out = 0;
-  if (lane < np) {
-    const gc_work& w = rec_at(ws.rec, s0 + lane);
-    my_item = ws.item[(s0 + lane) % kSeq];
-    my_tile = w.tile;
-    my_base = w.base;
-    my_shape = w.shape;
-    my_list = w.list;
-    my_out = w.out_at;
-  }
-  const bool my_dead = lane < np && !my_live && my_list != 0xffffffffu;
-  const uint32_t my_rank = __popc(live & ((1u << lane) - 1u));
-  if (my_live) {
-    ws.iout[my_rank] = my_out;
-    ws.inint[my_rank] = w_nint(my_shape);
-    if (KIND == GC_SIMPLE || KIND == GC_PFD) ws.irec[my_rank] = (s0 + lane) % kSeq | my_vec0 << 8;
-  }
-
-  // 1. per tile: re-lay its data vectors at 33 words per vector, and turn
-  // its control patterns into one (word, shift, width) entry per row
-  for (uint32_t lm = live; lm; lm &= lm - 1) {
-    const uint32_t p = __ffs(lm) - 1;
-    // (a pack of one: line 0, its nl lines, vector 0)
-    const uint32_t line0 = np == 1 ? 0u : __shfl_sync(kFull, my_line0, p);
-    const uint32_t rows = np == 1 ? nl : __shfl_sync(kFull, my_lines, p);
-    const uint32_t v0 = np == 1 ? 0u : __shfl_sync(kFull, my_vec0, p);
-    const gc_work& w = rec_at(ws.rec, s0 + p);
-    const uint32_t f = (s0 + p) % kFly;
-    const uint32_t at = ws.at[f];
-    const uint32_t vecs = ws.fvecs[f];
-    {
-      // lane l moves 16-byte chunk l % 8 of vectors 4 i + l / 8: one 16-byte
-      // load, and four stores that hit 32 different banks across the warp
-      const uint32_t q = lane >> 3;
-      const uint4* src = reinterpret_cast<const uint4*>(ws.ring + at) + lane;
-      uint32_t* dst = ws.tb + (v0 + q) * kPad + 4 * (lane & 7u);
-      for (uint32_t i = 0; 4 * i < vecs; ++i) {
-        if (4 * i + q < vecs) {
-          const uint4 x = src[i * 32];
-          uint32_t* d = dst + i * 4 * kPad;
-          d[0] = x.x;
-          d[1] = x.y;
-          d[2] = x.z;
-          d[3] = x.w;
-        }
+  // 1. Group-Scheme, Group-AFOR: per tile, the control patterns become one
+  // (word, shift, width) entry per row
+  if (KIND == GC_SCHEME || KIND == GC_AFOR) {
+    for (uint32_t lm = t.live_mask; lm; lm &= lm - 1) {
+      const uint32_t p = __ffs(lm) - 1;
+      // (a pack of one: line 0, its nl lines)
+      const uint32_t line0 = np == 1 ? 0u : __shfl_sync(kFull, t.line0, p);
+      const uint32_t rows = np == 1 ? nl : __shfl_sync(kFull, t.lines, p);
+      const uint32_t sp = rslot(s0 + p);
+      const gc_work& w = rec_of(h, sp);
+      const uint32_t at = h.at[sp];
+      const uint32_t vecs = h.fvecs[sp];
+      const uint32_t dbytes = vecs * kVecPitch;
+      CtrlView C;
+      C.g = a.ctrl_pool + w.ctrl_at;
+      C.size = w.ctrl_bytes;
+      C.s1 = ring + at + dbytes;
+      C.lo1 = w.win_at;
+      C.len1 = h.cst[sp];
+      C.s2 = nullptr;
+      C.lo2 = 0;
+      C.len2 = 0;
+      RowSink<32> out;
+      out.rw = ws.rw + line0;
+      out.rs = ws.rs + line0;
+      out.word0 = at >> 2;
+      out.stride = kVecWords;
+      out.bit0 = w_bit0(w.shape);
+      out.vec_bits = 32 * vecs;
+      bool ok;
+      if (KIND == GC_SCHEME) {
+        const uint64_t row0 = (uint64_t)w.tile * Geo<32>::TR;
+        if (a.ld == GC_LD_BINARY) ok = parse_scheme_binary<32>(C, row0, rows, a.cg, out);
+        else ok = parse_scheme_unary<32>(C, w.ctrl_bit, rows, a.cg, a.ld == GC_LD_IU, out);
+      } else {
+        ok = parse_afor<32>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
       }
+      if (!ok && lane == 0) report(a.status, GC_ERR_CORRUPT, w.list);
     }
-    const uint32_t dbytes = vecs * 32 * 4;
-    CtrlView C;
-    C.g = a.ctrl_pool + w.ctrl_at;
-    C.size = w.ctrl_bytes;
-    C.s1 = ws.ring + at + dbytes;
-    C.lo1 = w.win_at;
-    C.len1 = ws.cst[f];
-    C.s2 = ws.ring + at + dbytes + ws.cst[f];
-    C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
-    C.len2 = ws.xst[f];
-    RowSink<32> out;
-    out.rw = ws.rw + line0;
-    out.rs = ws.rs + line0;
-    out.word0 = v0 * kPad;
-    out.stride = kPad;
-    out.bit0 = w_bit0(w.shape);
-    out.vec_bits = 32 * vecs;
-    bool ok = true;
-    if (KIND == GC_SIMPLE) {
-      // parsed below, all of the pack's tiles at once
-    } else if (KIND == GC_SCHEME) {
-      const uint64_t row0 = (uint64_t)w.tile * Geo<32>::TR;
-      if (a.ld == GC_LD_BINARY) ok = parse_scheme_binary<32>(C, row0, rows, a.cg, out);
-      else ok = parse_scheme_unary<32>(C, w.ctrl_bit, rows, a.cg, a.ld == GC_LD_IU, out);
-    } else if (KIND == GC_AFOR) {
-      ok = parse_afor<32>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
-    } else {
-      // parsed below, all of the pack's tiles at once
-    }
-    if (!ok && lane == 0) report(a.status, GC_ERR_CORRUPT, w.list);
   }
   __syncwarp();
 
-  // 2. lane l extracts line l (row l of the pack): ints in column order
+  // 2. lane l extracts line l (row l of the pack)
   const bool act = lane < nl;
-  const uint32_t upto = heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
-  const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;  // its item among the decoded ones
-  const uint32_t lhead = act ? 31u - __clz(upto) : 0u;          // the item's first line
+  const uint32_t upto = t.heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
+  const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;    // its item among the decoded ones
+  const uint32_t lhead = act ? 31u - __clz(upto) : 0u;            // the item's first line
   uint32_t ent, sw;
   PfdExc px;
   if (KIND == GC_SIMPLE) {
-    parse_simple_pack32(a, ws, act, lane, heads, nl, rank, lhead, ent, sw);
+    parse_simple_pack32(a, h, ws, ring, act, lane, t.heads, nl, rank, lhead, ent, sw);
   } else if (KIND == GC_PFD) {
-    parse_pfd_pack32(a, ws, act, lane, heads, nl, rank, lhead, ent, sw, px);
+    parse_pfd_pack32(a, h, ws, ring, act, lane, t.heads, nl, rank, lhead, ent, sw, px);
   } else {
-    ent = act ? ws.rw[lane] : 0u;
+    ent = ws.rw[lane];
     sw = act ? ws.rs[lane] : 0u;
   }
   const uint32_t sh = sw & 31u, wd = sw >> 8;
   const uint32_t msk = low_mask(wd);
   const bool cross = sh + wd > 32;
-  const uint32_t* P = ws.tb + ent;
-  uint32_t r[32];
+  // A row of no bits (Group-PFD b = 0, Group-AFOR's all-zero frames, an
+  // entry left by a malformed stream) may lie past the tile's staged data,
+  // which need not hold even one vector: such rows, and lanes past the
+  // pack's lines, read their own line of the buffer instead (the mask
+  // makes every value 0).
+  const uint4* P = act && wd != 0 ? reinterpret_cast<const uint4*>(ring + 4ull * ent)
+                                  : reinterpret_cast<const uint4*>(ws.tb + 32 * lane);
+  uint4* T = reinterpret_cast<uint4*>(ws.tb + 32 * lane);
+  const uint32_t swz = lane & 7u;
+  bool patch = false;  // (Group-PFD) a tile of the pack has exceptions
+  if (KIND == GC_PFD) patch = (__ballot_sync(kFull, px.e != 0) & t.heads) != 0;
   uint32_t R = 0;
-  if (KIND != GC_PFD) {
-    extract_line<KIND, RESTORE>(P, sh, msk, cross, r, R);
+  if (RESTORE && !patch) {
+    extract_line32<KIND, true>(P, sh, msk, cross, T, swz, R);
   } else {
-    // Group-PFD: the slots' values; when a tile of the pack has exceptions
-    // (most frames have none), the exceptions over their slots in the
-    // line-major buffer (line l at words 32 l .., 16-byte chunk c at chunk
-    // c ^ (l & 7)); then the running sum over the patched line
-    extract_line<KIND, false>(P, sh, msk, cross, r, R);
-    if (__ballot_sync(kFull, px.e != 0) & heads) {
-      uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
-      const uint32_t swz = lane & 7u;
-      __syncwarp();  // (the re-laid data is read)
-      if (act) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) T[c ^ swz] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
-      }
-      __syncwarp();
-      pfd_patch_pack32(a, ws, lane, heads, px);
-      __syncwarp();
-      if (act) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const uint4 v = T[c ^ swz];
-          r[4 * c] = v.x;
-          r[4 * c + 1] = v.y;
-          r[4 * c + 2] = v.z;
-          r[4 * c + 3] = v.w;
-        }
-      }
-    }
-    R = 0;
+    extract_line32<KIND, false>(P, sh, msk, cross, T, swz, R);
+  }
+  if (KIND == GC_PFD && patch) {
+    // the slots' values are in the buffer: the exceptions over them (most
+    // frames have none), then the running sum over the patched line
+    __syncwarp();
+    pfd_patch_pack32(a, ws.tb, lane, t.heads, px);
+    __syncwarp();
     if (RESTORE) {
+      R = 0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        R += r[j];
-        r[j] = R;
+      for (int c = 0; c < 8; ++c) {
+        uint4 v = T[c ^ swz];
+        v.x += R;
+        v.y += v.x;
+        v.z += v.y;
+        v.w += v.z;
+        R = v.w;
+        T[c ^ swz] = v;
       }
     }
   }
-
-  // 3. docIDs: segmented scan of line totals, then each item's base
-  uint32_t k0 = 0;
-  if (RESTORE) {
-    // (a plain scan, less the scan before the item's first line)
-    const uint32_t T = act ? R : 0u;
-    const uint32_t V = warp_incl_sum(T);
-    const uint32_t shape0 = __shfl_sync(kFull, my_shape, 0);
-    if (np == 1 && heads == 1u && (shape0 & (GC_WORK_HAS_BASE | GC_WORK_PUBLISH)) == GC_WORK_HAS_BASE) {
-      // a pack of one live tile with its skip entry, which no other tile
-      // waits for
-      k0 = V - T + __shfl_sync(kFull, my_base, 0);
-    } else {
-      const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
-      const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
-      const uint32_t E = v - T;
-      const uint32_t lastl = my_live ? my_line0 + my_lines - 1 : 0u;
-      const uint32_t tot = __shfl_sync(kFull, v, lastl);
-      const bool has_base = (my_shape & GC_WORK_HAS_BASE) != 0;
-      const bool needs_lb = my_live && my_tile > 0 && !has_base;
-      uint32_t base = has_base ? my_base : 0u;
-      if (a.lb) {
-        if (my_live && !needs_lb && (my_shape & GC_WORK_PUBLISH))
-          st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(base + tot));
-        if (my_dead) st_release(a.lb + my_item, kFlagPrefix);  // its error is reported
-        if (needs_lb) st_release(a.lb + my_item, kFlagAgg | tot);
-      }
-      for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
-        const uint32_t p = __ffs(pend) - 1;
-        const uint32_t it = __shfl_sync(kFull, my_item, p);
-        const uint32_t tl = __shfl_sync(kFull, my_tile, p);
-        const uint32_t lst = __shfl_sync(kFull, my_list, p);
-        const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
-        if (lane == p) {
-          base = ex;
-          if (a.lb) st_release(a.lb + my_item, kFlagPrefix | (uint32_t)(ex + tot));
-        }
-      }
-      if (my_live) ws.ibase[my_rank] = base;
-      __syncwarp();
-      k0 = E + (act ? ws.ibase[rank] : 0u);
-    }
-  }
-
-  // the re-laid data is read: its buffer takes the results, line l at words
-  // 32 l .. 32 l + 31 with its 16-byte chunk c at chunk c ^ (l & 7), so that
-  // the eight lanes of each quarter-warp touch eight different chunks both
-  // here (a line per lane) and when reading (a chunk per lane, below)
+  // the pack's staged bytes are read: give its ring bytes back
   __syncwarp();
-  const bool whole = heads == 1u && ws.inint[0] == (uint32_t)kTileInts;  // one whole tile
-  if (act) {
-    uint4* T = reinterpret_cast<uint4*>(ws.tb + lane * 32);
-    const uint32_t sw = lane & 7u;
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-      T[c ^ sw] = make_uint4(r[4 * c] + k0, r[4 * c + 1] + k0, r[4 * c + 2] + k0, r[4 * c + 3] + k0);
-    if (!whole) {
-      ws.lout[lane] = ws.iout[rank] + 32ull * (lane - lhead);
-      const uint32_t left = ws.inint[rank] - 32u * (lane - lhead);
-      ws.lnv[lane] = left < 32u ? left : 32u;
-    }
+  if (lane == 0) mbar_arrive(empty);
+
+  // 3. docIDs: each line's base
+  const uint32_t k0 = RESTORE ? line_bases<32>(a, ws, t, np, act, R, rank, lhead) : 0u;
+  const bool whole = t.heads == 1u && ws.inint[0] == (uint32_t)kTileInts;  // one whole tile
+  if (act && !whole) {
+    ws.lout[lane] = ws.iout[rank] + 32ull * (lane - lhead);
+    const uint32_t left = ws.inint[rank] - 32u * (lane - lhead);
+    ws.lnv[lane] = left < 32u ? left : 32u;
   }
   __syncwarp();
 
-  // 4. stores. Lane j takes chunk c = j % 8 of lines 4 q + j / 8 and stores
-  // it with one 16-byte store where the chunk is whole and its output
-  // 16-byte aligned, else word by word. A whole tile whose output is not
-  // aligned goes out line by line instead, lane j storing word j (word j of
-  // line l sits at word 32 l + 4 ((j / 4) ^ (l & 7)) + j % 4).
+  // 4. stores. Lane j takes chunk c = j % 8 of lines 4 q + j / 8, adds the
+  // line's base, and stores it with one 16-byte store where the chunk is
+  // whole and its output 16-byte aligned, else word by word. A whole tile
+  // whose output is not aligned goes out line by line instead, lane j
+  // storing word j (word j of line l sits at word 32 l + 4 ((j / 4) ^ (l &
+  // 7)) + j % 4).
   const uint32_t c = lane & 7u;
   uint32_t* o1 = a.out_pool + ws.iout[0];
   if (whole) {
@@ -1296,20 +1294,35 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint32_t rr = 4u * q + (lane >> 3);
-        const uint4 v = reinterpret_cast<const uint4*>(ws.tb + rr * 32)[c ^ (rr & 7u)];
+        uint4 v = reinterpret_cast<const uint4*>(ws.tb + rr * 32)[c ^ (rr & 7u)];
+        if (RESTORE) {
+          const uint32_t kk = __shfl_sync(kFull, k0, rr);
+          v.x += kk;
+          v.y += kk;
+          v.z += kk;
+          v.w += kk;
+        }
         reinterpret_cast<uint4*>(o1 + rr * 32)[c] = v;
       }
     } else {
       const uint32_t wsw = 4u * (lane >> 2), wlo = lane & 3u;
 #pragma unroll
-      for (int rr = 0; rr < 32; ++rr) o1[rr * 32 + lane] = ws.tb[rr * 32 + (wsw ^ (4u * (rr & 7))) + wlo];
+      for (int rr = 0; rr < 32; ++rr) {
+        const uint32_t kk = RESTORE ? __shfl_sync(kFull, k0, rr) : 0u;
+        o1[rr * 32 + lane] = ws.tb[rr * 32 + (wsw ^ (4u * (rr & 7))) + wlo] + kk;
+      }
     }
   } else {
     for (uint32_t q = 0; 4 * q < nl; ++q) {
       const uint32_t ln = 4 * q + (lane >> 3);
+      const uint32_t kk = RESTORE ? __shfl_sync(kFull, k0, ln & 31u) : 0u;
       if (ln < nl) {
         const uint32_t n = ws.lnv[ln];
-        const uint4 v = reinterpret_cast<const uint4*>(ws.tb + ln * 32)[c ^ (ln & 7u)];
+        uint4 v = reinterpret_cast<const uint4*>(ws.tb + ln * 32)[c ^ (ln & 7u)];
+        v.x += kk;
+        v.y += kk;
+        v.z += kk;
+        v.w += kk;
         uint32_t* o = a.out_pool + ws.lout[ln] + 4 * c;
         if (4 * c + 4 <= n && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
           *reinterpret_cast<uint4*>(o) = v;
@@ -1325,214 +1338,374 @@ __device__ void decode_pack32(const DecodeArgs& a, WarpSmem<32>& ws, uint32_t s0
   __syncwarp();
 }
 
-// What staging a claimed record takes, found once when it is claimed: its
-// data vectors, control window and (Group-PFD) exception window, all in
-// the ring at 128-byte granularity; a record that fails its checks stages
-// nothing and decodes to nothing (its error is reported here).
+// ---------------------------------------------------------- staging warp
+
+// What staging a claimed record takes, found when its claim arrives: its
+// 32-int lines, data vectors, control window and (Group-PFD) exception
+// window; a record that fails its checks stages nothing and decodes to
+// nothing (its error is reported here).
 template <int KIND, int K>
-__device__ __forceinline__ void stage_sizes(const gc_work& w, const DecodeArgs& a, WarpSmem<K>& ws, uint32_t f) {
-  uint32_t dbytes = 0, cb = 0, xb = 0, lines = 0;
+__device__ __forceinline__ void stage_sizes(const gc_work& w, const DecodeArgs& a, uint32_t& lines, uint32_t& nv,
+                                            uint32_t& cb, uint32_t& xb) {
+  lines = 0;
+  nv = 0;
+  cb = 0;
+  xb = 0;
   const bool live = w_live<K>(w, a);
   if (!live && w.list != 0xffffffffu)
     report(a.status, w.out_at + w_nint(w.shape) > a.out_pool_len ? GC_ERR_INVALID : GC_ERR_CORRUPT, w.list);
-  if (live) {
-    lines = (w_nint(w.shape) + 31) / 32;
-    dbytes = w_vecs(w.shape) * K * 4;
-    const int64_t ws0 = (int64_t)w.ctrl_at + w.win_at;
-    cb = w.win_len < kCtrlCap ? w.win_len : (uint32_t)kCtrlCap;
-    if (ws0 < 0 || (ws0 & 15) || (uint64_t)ws0 + cb > a.ctrl_pool_bytes) cb = 0;
-    if (KIND == GC_PFD) {
-      const uint64_t xs = (w.ctrl_at + w.exc_at) & ~15ull;
-      xb = w.exc_len;
-      if (xb > (uint32_t)kExcCap || xs + xb > a.ctrl_pool_bytes) xb = 0;
-    }
+  if (!live) return;
+  lines = (w_nint(w.shape) + 31) / 32;
+  nv = w_vecs(w.shape);
+  const int64_t ws0 = (int64_t)w.ctrl_at + w.win_at;
+  cb = w.win_len < kCtrlCap ? w.win_len : (uint32_t)kCtrlCap;
+  if (ws0 < 0 || (ws0 & 15) || (uint64_t)ws0 + cb > a.ctrl_pool_bytes) cb = 0;
+  if (KIND == GC_PFD) {
+    const uint64_t xs = (w.ctrl_at + w.exc_at) & ~15ull;
+    xb = w.exc_len;
+    if (xb > (uint32_t)kExcCap || xs + xb > a.ctrl_pool_bytes) xb = 0;
   }
-  ws.need[f] = (uint16_t)((dbytes + cb + xb + 127u) & ~127u);
-  ws.cst[f] = (uint16_t)cb;
-  ws.xst[f] = (uint16_t)xb;
-  ws.flines[f] = (uint8_t)lines;
-  ws.fvecs[f] = (uint16_t)(dbytes / (K * 4));
 }
 
-template <int KIND, int K, bool RESTORE>
-__global__ void __launch_bounds__(512, 1) k_decode(DecodeArgs a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  WarpSmem<K>& ws = reinterpret_cast<WarpSmem<K>*>(smem_raw)[threadIdx.x >> 5];
+// The staging warp's side of the ring: the bytes it holds (padding
+// included), where the next pack goes, and the packs issued and given back.
+struct Ring {
+  uint32_t bytes, head, used;
+  uint32_t issued, tail;     // packs issued / given back
+  uint32_t ps;               // slot of the next pack
+  uint32_t ts, tph;          // slot and phase of the oldest pack not given back
+};
+
+// Wait until the oldest pack not given back is decoded, and take its bytes
+// back. False (every lane) when the wait runs out.
+__device__ __forceinline__ void ring_take(BlockSmem& h, Ring& r, uint32_t S) {
+  r.used -= h.prel[r.ts];
+  ++r.tail;
+  if (++r.ts == S) {
+    r.ts = 0;
+    r.tph ^= 1u;
+  }
+}
+// (and every later pack that is decoded already, without waiting)
+__device__ __forceinline__ bool ring_drain(BlockSmem& h, Ring& r, uint32_t S) {
+  if (!wait_warp(&h.empty[r.ts], r.tph)) return false;
+  ring_take(h, r, S);
+  while (r.tail < r.issued && __all_sync(kFull, mbar_test_wait(&h.empty[r.ts], r.tph))) ring_take(h, r, S);
+  return true;
+}
+
+// Claim up to `claim` records for record buffer b and start the bulk copy
+// that brings them in; returns their first plan index (lane-uniform) and
+// count.
+__device__ __forceinline__ void claim_records(const DecodeArgs& a, BlockSmem& h, uint32_t b, uint32_t claim,
+                                              uint64_t total, uint32_t& x, uint32_t& cnt) {
+  const uint32_t lane = lane_id();
+  uint32_t v = 0;
+  if (lane == 0) v = atomicAdd(a.counter, claim);
+  x = __shfl_sync(kFull, v, 0);
+  cnt = (uint64_t)x < total ? (uint32_t)min64(claim, total - x) : 0u;
+  if (lane == 0 && cnt) {
+    mbar_expect_tx(&h.recbar[b], cnt * (uint32_t)sizeof(gc_work));
+    bulk_g2s(h.rec[b * kChunk], a.work + x, cnt * (uint32_t)sizeof(gc_work), &h.recbar[b]);
+  }
+}
+
+// Group the claim's records (lanes 0 .. cnt - 1) into packs: a pack is a run
+// of consecutive records whose lines fit 32, whose ring bytes fit kPackCap
+// and, at k = 4, whose data vectors fit the re-lay buffer; packs are formed
+// greedily from the first record (a whole tile is a pack by itself). Lane i
+// finds by binary search how many records from i on fit one pack (next_i
+// is the first record after them); the packs start at the records reached
+// from record 0 by following next, found by pointer doubling in five
+// rounds. Returns the mask of pack starts; P is each lane's inclusive sum
+// of (lines | ring bytes / 16 << 11 | vectors << 32) and nxt its next_i.
+template <int K>
+__device__ __forceinline__ uint32_t pack_starts(uint64_t v, uint32_t cnt, uint64_t& P, uint32_t& nxt) {
+  const uint32_t lane = lane_id();
+  P = warp_incl_sum(v);
+  const uint64_t Pex = P - v;
+  uint32_t len = 0;
+#pragma unroll
+  for (uint32_t step = 16; step; step >>= 1) {
+    const uint32_t j = lane + len + step - 1;  // the last record of the candidate
+    const uint64_t s = __shfl_sync(kFull, P, j < 32 ? j : 31u) - Pex;
+    const bool fits = j < cnt && (s & 2047u) <= 32u && ((s >> 11) & 0x1fffffu) * 16u <= (uint64_t)kPackCap &&
+                      (K != 4 || (s >> 32) <= (uint64_t)kPadVec4);
+    if (fits) len += step;
+  }
+  nxt = lane < cnt ? lane + (len ? len : 1u) : 32u;
+  uint32_t g = nxt, reach = cnt ? 1u : 0u;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    reach |= __reduce_or_sync(kFull, ((reach >> lane) & 1u) && g < 32u ? 1u << g : 0u);
+    const uint32_t gg = __shfl_sync(kFull, g, g & 31u);
+    g = g < 32u ? gg : 32u;
+  }
+  // (the last pack's next is record cnt, which is not the claim's)
+  return cnt >= 32u ? reach : reach & ((1u << cnt) - 1u);
+}
+
+// The staging warp. Claims records (the next claim's copy in flight while
+// the current one is placed), sizes them one per lane, groups them into
+// packs (pack_starts) and places the packs in the ring in order, as many at
+// once as the ring and the pack slots allow: a pack never wraps (one that
+// would cross the ring's end starts at 0, and the bytes it skips are held
+// with it), and the ring's bytes come back in pack order as the decoding
+// warps finish. Each placed pack's records get their ring offsets and the
+// pack its slot descriptor, then one arrival on the slot's mbarrier tells
+// its decoding warp, which copies the pack's bytes in itself. After the
+// last record, one empty pack per decoding warp tells it to stop.
+template <int KIND, int K>
+__device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t S) {
   const uint32_t lane = lane_id();
   uint64_t total = a.count[0];
   if (total > a.work_cap) total = a.work_cap;
-  const bool lookback = RESTORE && a.count[1] != 0;
-  // a claim must fit the record slots, or the warp could never claim again
-  const uint32_t C = lookback ? 1u : (a.claim < 1u ? 1u : a.claim > (uint32_t)kSeq ? (uint32_t)kSeq : a.claim);
-  if (lane < kFly) mbar_init(&ws.mbar[lane], 1);
+  const uint32_t claim = a.claim < 1u ? 1u : a.claim > (uint32_t)kChunk ? (uint32_t)kChunk : a.claim;
+  Ring r = {a.ring_bytes, 0, 0, 0, 0, 0, 0, 0};
+  bool failed = false;
+  uint32_t busy = 0;  // lane b < kNChunk: record buffer b is free once this many packs are given back
+  uint32_t x, cnt;
+  claim_records(a, h, 0, claim, total, x, cnt);
+  for (uint32_t c = 0; cnt && !failed; ++c) {
+    const uint32_t b = c % kNChunk;
+    // the next claim goes to the next buffer once that buffer's packs are given back
+    const uint32_t nb = (c + 1) % kNChunk;
+    const uint32_t nbusy = __shfl_sync(kFull, busy, nb);
+    while (!failed && r.tail < nbusy) failed = !ring_drain(h, r, S);
+    if (failed) break;
+    uint32_t nx, ncnt;
+    claim_records(a, h, nb, claim, total, nx, ncnt);
+    if (!wait_warp(&h.recbar[b], (c / kNChunk) & 1u)) {
+      failed = true;
+      break;
+    }
+    // sizes, one record per lane
+    const bool valid = lane < cnt;
+    const uint32_t rs = b * kChunk + lane;
+    uint32_t lines = 0, nv = 0, cb = 0, xb = 0;
+    if (valid) {
+      h.item[rs] = x + lane;
+      stage_sizes<KIND, K>(rec_of(h, rs), a, lines, nv, cb, xb);
+      h.fvecs[rs] = (uint16_t)nv;
+      h.cst[rs] = (uint16_t)cb;
+      h.xst[rs] = (uint16_t)xb;
+      h.flines[rs] = (uint8_t)lines;
+    }
+    const uint32_t need16 = (nv * (uint32_t)Geo<K>::VB + cb + xb) / 16;  // ring bytes / 16
+    const uint64_t v = valid ? (uint64_t)lines | (uint64_t)need16 << 11 | (uint64_t)nv << 32 : 0ull;
+    uint64_t P;
+    uint32_t nxt;
+    const uint32_t starts = pack_starts<K>(v, cnt, P, nxt);
+    const uint64_t Pex = P - v;
+    // each record's offset from its pack's start; at a pack's first record,
+    // the pack's ring bytes / 16, records and lines
+    const uint32_t le = 0xffffffffu >> (31u - lane);  // lanes <= this one
+    const uint32_t s0 = (31u - __clz(starts & le)) & 31u;
+    const uint32_t ex16 = (uint32_t)((Pex >> 11) & 0x1fffffu);  // ring bytes / 16 before this record
+    const uint32_t sex16 = __shfl_sync(kFull, ex16, s0);
+    if (valid) h.rrel[rs] = (ex16 - sex16) * 16;
+    const uint64_t Pl = __shfl_sync(kFull, P, (nxt - 1u) & 31u);
+    const uint32_t pinfo = ((uint32_t)((Pl >> 11) & 0x1fffffu) - ex16) | (nxt - lane) << 16 |
+                           ((uint32_t)(Pl & 2047u) - (uint32_t)(Pex & 2047u)) << 24;
+    __threadfence_block();
+    __syncwarp();
+    // place the packs in order
+    for (uint32_t m = starts; m && !failed; m &= m - 1) {
+      const uint32_t sp = __ffs(m) - 1;
+      const uint32_t pi = __shfl_sync(kFull, pinfo, sp);
+      const uint32_t B = (pi & 0xffffu) * 16;
+      uint32_t off, pad;
+      for (;;) {
+        if (r.used == 0) r.head = 0;
+        off = r.head;
+        pad = 0;
+        if (off + B > r.bytes) {
+          pad = r.bytes - off;
+          off = 0;
+        }
+        if (r.used + pad + B <= r.bytes && r.issued - r.tail < S) break;
+        if (!ring_drain(h, r, S)) {
+          failed = true;
+          break;
+        }
+      }
+      if (failed) break;
+      if (lane == 0) {
+        h.pk[r.ps] = (b * kChunk + sp) | ((pi >> 16) & 255u) << 8 | (pi >> 24) << 16;
+        h.prel[r.ps] = pad + B;
+        h.ppos[r.ps] = off;
+        mbar_arrive(&h.full[r.ps]);
+      }
+      r.head = off + B;
+      r.used += pad + B;
+      ++r.issued;
+      if (++r.ps == S) r.ps = 0;
+    }
+    if (lane == b) busy = r.issued;
+    x = nx;
+    cnt = ncnt;
+  }
+  if (failed) {
+    if (lane == 0) report(a.status, GC_ERR_TIMEOUT, 0xfffffffdu);
+    return;
+  }
+  // one stop per decoding warp
+  while (r.issued + W - r.tail > S) {
+    if (!ring_drain(h, r, S)) {
+      if (lane == 0) report(a.status, GC_ERR_TIMEOUT, 0xfffffffdu);
+      return;
+    }
+  }
+  const uint32_t slot = (r.ps + lane) % S;
+  if (lane < W) {
+    h.pk[slot] = 0;
+    h.prel[slot] = 0;
+  }
+  __threadfence_block();
+  __syncwarp();
+  if (lane < W) mbar_arrive(&h.full[slot]);
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// A decoding warp copies a pack's bytes into the ring (the places the
+// staging warp gave its records), tile by tile: lane j takes 16-byte chunks
+// j, j + 32, ... of the tile's data vectors (at the ring's pitch), then of
+// its control and exception windows. Each lane's copies are its own
+// cp.async group once committed.
+template <int K>
+__device__ __forceinline__ void copy_pack(const DecodeArgs& a, BlockSmem& h, uint8_t* ring, uint32_t d, uint32_t slot) {
+  const uint32_t lane = lane_id();
+  const uint32_t s0 = d & 255u, np = (d >> 8) & 255u;
+  // the records' ring offsets: the pack's, plus each one's from the pack's start
+  if (lane < np) {
+    const uint32_t s = rslot(s0 + lane);
+    h.at[s] = h.ppos[slot] + h.rrel[s];
+  }
+  __syncwarp();
+  constexpr uint32_t CPV = K * 4 / 16;  // 16-byte chunks per data vector
+  for (uint32_t p = 0; p < np; ++p) {
+    const uint32_t s = rslot(s0 + p);
+    const uint32_t nvp = h.fvecs[s], cbp = h.cst[s], xbp = h.xst[s];
+    const uint32_t dch = nvp * CPV, cch = cbp >> 4, tch = dch + cch + (xbp >> 4);
+    if (tch == 0) continue;
+    const gc_work& w = rec_of(h, s);
+    const uint32_t atp = h.at[s];
+    const uint8_t* dsrc = reinterpret_cast<const uint8_t*>(a.data_pool + w.data_at);
+    const uint8_t* csrc = a.ctrl_pool + (w.ctrl_at + w.win_at);
+    const uint8_t* xsrc = a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull);
+    for (uint32_t j = lane; j < tch; j += 32) {
+      const uint8_t* src;
+      uint32_t dst;
+      if (j < dch) {
+        const uint32_t v = j / CPV, c = j % CPV;
+        dst = atp + v * (uint32_t)Geo<K>::VB + 16 * c;
+        src = dsrc + (size_t)v * (K * 4) + 16 * c;
+      } else if (j < dch + cch) {
+        dst = atp + nvp * (uint32_t)Geo<K>::VB + 16 * (j - dch);
+        src = csrc + 16 * (j - dch);
+      } else {
+        dst = atp + nvp * (uint32_t)Geo<K>::VB + cbp + 16 * (j - dch - cch);
+        src = xsrc + 16 * (j - dch - cch);
+      }
+      cp_async16(ring + dst, src);
+    }
+  }
+}
+
+// A decoding warp: packs w, w + W, w + 2W, ... (slot w + (t mod S/W) W of
+// the block's S = W * (kMaxSlots / W) slots), until an empty one. It copies
+// the next pack in while it decodes the current one when the staging warp
+// has placed it already; it never waits for the next pack before decoding
+// the current one (the staging warp may need the current pack's ring bytes
+// back first).
+template <int KIND, int K, bool RESTORE>
+__device__ void consume(const DecodeArgs& a, BlockSmem& h, WarpSmem<K>& ws, uint8_t* ring, uint32_t w,
+                        uint32_t W, uint32_t S) {
+  const uint32_t lane = lane_id();
   // row entries start in range (a parser stopped by a corrupt stream leaves
   // earlier, in-range entries behind, never garbage)
   for (uint32_t i = lane; i < (uint32_t)Geo<K>::PROWS; i += 32) {
     ws.rw[i] = 0;
     ws.rs[i] = 0;
   }
-  fence_mbar_init();
+  ws.irec[lane] = 0;
   __syncwarp();
-
-  uint32_t s_claimed = 0, s_issued = 0, s_done = 0;  // positions in this warp's record sequence
-  uint32_t rpos = 0, used = 0;  // ring: next free offset, bytes held (padding included)
-  bool more = true;
-  bool failed = false;
-  for (;;) {
-    // claim records
-    if (more && s_claimed - s_done + C <= (uint32_t)kSeq) {
-      uint32_t x = 0;
-      if (lane == 0) x = atomicAdd(a.counter, C);
-      x = __shfl_sync(kFull, x, 0);
-      const uint32_t cnt = (uint64_t)x < total ? (uint32_t)min64(C, total - x) : 0u;
-      if (cnt == 0) {
-        more = false;
-      } else {
-        if (lane < cnt) {
-          const uint32_t f = (s_claimed + lane) % kSeq;
-          const uint4* src = reinterpret_cast<const uint4*>(a.work + x + lane);
-          union {
-            uint4 q[4];
-            gc_work w;
-          } u;
-          u.q[0] = __ldg(src);
-          u.q[1] = __ldg(src + 1);
-          u.q[2] = __ldg(src + 2);
-          u.q[3] = __ldg(src + 3);
-          uint4* dst = ws.rec[f];
-          dst[0] = u.q[0];
-          dst[1] = u.q[1];
-          dst[2] = u.q[2];
-          dst[3] = u.q[3];
-          ws.item[f] = x + lane;
-          stage_sizes<KIND, K>(u.w, a, ws, f);
-        }
-        __syncwarp();
-        s_claimed += cnt;
-      }
-    }
-    // stage claimed tiles while the ring and the mbarriers allow. A tile
-    // never wraps: it starts at offset 0 when it would run past the end, and
-    // the bytes skipped there are held until it is decoded. When only the
-    // first candidate fits (whole tiles, mostly) it is placed directly;
-    // when more fit, lane p takes record s_issued + p and every offset
-    // follows from one scan of the sizes (the tiles that fit are a prefix of
-    // the candidates); when none fits (the ring is full) nothing happens.
-    if (s_issued < s_claimed && s_issued - s_done < (uint32_t)kFly) {
-      const uint32_t r0 = used ? rpos : 0u;  // empty: restart at offset 0
-      const uint32_t f0 = s_issued % kFly;
-      const uint32_t need0 = ws.need[f0];
-      const bool wrap0 = r0 + need0 > (uint32_t)kRing;  // (the pad is 0 when r0 is the ring's end)
-      const uint32_t pad0 = wrap0 ? kRing - r0 : 0u;
-      const uint32_t off0 = wrap0 ? 0u : r0;
-      const uint32_t cands = min(s_claimed - s_issued, (uint32_t)kFly - (s_issued - s_done));
-      // does a second candidate fit after the first?
-      bool more2 = false;
-      if (cands > 1) {
-        const uint32_t r1 = off0 + need0;
-        const uint32_t need1 = ws.need[(s_issued + 1) % kFly];
-        const uint32_t pad1 = r1 + need1 > (uint32_t)kRing ? kRing - r1 : 0u;
-        more2 = used + pad0 + need0 + pad1 + need1 <= (uint32_t)kRing;
-      }
-      if (used + pad0 + need0 <= (uint32_t)kRing && !more2) {
-        // the first only (the usual case for whole tiles): no scan
-        const uint32_t off = off0;
-        if (lane == 0) {
-          const gc_work& w = rec_at(ws.rec, s_issued);
-          const uint32_t dbytes = ws.fvecs[f0] * (K * 4u), cb = ws.cst[f0], xb = ws.xst[f0];
-          ws.at[f0] = off;
-          ws.end[f0] = need0 + pad0;
-          mbar_expect_tx(&ws.mbar[f0], dbytes + cb + xb);
-          if (dbytes) bulk_g2s(ws.ring + off, a.data_pool + w.data_at, dbytes, &ws.mbar[f0]);
-          if (cb) bulk_g2s(ws.ring + off + dbytes, a.ctrl_pool + (w.ctrl_at + w.win_at), cb, &ws.mbar[f0]);
-          if (xb)
-            bulk_g2s(ws.ring + off + dbytes + cb, a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull), xb,
-                     &ws.mbar[f0]);
-        }
-        rpos = off + need0;
-        used += pad0 + need0;
-        __syncwarp();
-        s_issued += 1;
-      } else if (more2) {
-        const uint32_t s = s_issued + lane;
-        const uint32_t f = s % kFly;
-        const bool cand = lane < cands;
-        const uint32_t need = cand ? ws.need[f] : 0u;
-        const uint32_t incl = warp_incl_sum(need);
-        const uint32_t excl = incl - need;
-        const uint32_t wrapm = __ballot_sync(kFull, cand && r0 + incl > (uint32_t)kRing);
-        const uint32_t pw = wrapm ? __ffs(wrapm) - 1 : 32u;  // the first tile that would run past the end
-        const uint32_t ew = __shfl_sync(kFull, excl, pw & 31u);
-        const uint32_t pad = wrapm ? kRing - (r0 + ew) : 0u;
-        const bool after = lane >= pw;
-        const uint32_t off = after ? excl - ew : r0 + excl;
-        const uint32_t n =
-            __popc(__ballot_sync(kFull, cand && used + incl + (after ? pad : 0u) <= (uint32_t)kRing));
-        if (lane < n) {
-          const gc_work& w = rec_at(ws.rec, s);
-          const uint32_t dbytes = ws.fvecs[f] * (K * 4u), cb = ws.cst[f], xb = ws.xst[f];
-          ws.at[f] = off;
-          ws.end[f] = need + (lane == pw ? pad : 0u);  // bytes the tile gives back
-          mbar_expect_tx(&ws.mbar[f], dbytes + cb + xb);
-          if (dbytes) bulk_g2s(ws.ring + off, a.data_pool + w.data_at, dbytes, &ws.mbar[f]);
-          if (cb) bulk_g2s(ws.ring + off + dbytes, a.ctrl_pool + (w.ctrl_at + w.win_at), cb, &ws.mbar[f]);
-          if (xb)
-            bulk_g2s(ws.ring + off + dbytes + cb, a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull), xb,
-                     &ws.mbar[f]);
-        }
-        rpos = __shfl_sync(kFull, off + need, n - 1);
-        used += __shfl_sync(kFull, incl, n - 1) + (pw < n ? pad : 0u);
-        __syncwarp();
-        s_issued += n;
-      }
-    }
-    if (s_done == s_issued) {
-      if (!more && s_issued == s_claimed) break;
-      continue;
-    }
-    // a pack: the staged records from s_done on while their lines fit 32
-    // (and, k = 32, their vectors the re-lay buffer); one scan of both
-    const uint32_t staged = s_issued - s_done;
-    const uint32_t fp = (s_done + lane) % kFly;
-    const uint32_t lv0 = ws.flines[s_done % kFly] | (uint32_t)ws.fvecs[s_done % kFly] << 16;
-    uint32_t lv, lvi, np, nl;
-    if ((lv0 & 0xffffu) == 32u) {
-      // a whole tile is a pack by itself
-      lv = lane == 0 ? lv0 : 0u;
-      lvi = lv0;
-      np = 1;
-      nl = 32;
-    } else {
-      lv = lane < staged ? ws.flines[fp] | (uint32_t)ws.fvecs[fp] << 16 : 0u;
-      lvi = warp_incl_sum(lv);
-      np = __popc(__ballot_sync(
-          kFull, lane < staged && (lvi & 0xffffu) <= 32u &&
-                     (lvi >> 16) <= (uint32_t)(K == 32 ? kPadVec : kPadVec4)));
-      nl = __shfl_sync(kFull, lvi & 0xffffu, np - 1);
-    }
-    // wait for their copies
-    for (uint32_t p = 0; p < np && !failed; ++p) {
-      const uint32_t s = s_done + p;
-      if (!mbar_try_wait(&ws.mbar[s % kFly], (s / kFly) & 1u)) {
-        const uint64_t t0 = now_ns();
-        while (!mbar_try_wait(&ws.mbar[s % kFly], (s / kFly) & 1u)) {
-          if (now_ns() - t0 > kWaitNs) {
-            failed = true;
-            break;
-          }
-        }
-      }
-    }
-    if (__any_sync(kFull, failed)) {
-      // a copy never completed: stop this warp (its records stay undecoded)
-      if (lane == 0) report(a.status, GC_ERR_TIMEOUT, 0xfffffffeu);
-      break;
-    }
-    if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, ws, s_done, np, nl, lane < np ? lv : 0u, lvi);
-    else decode_pack4<KIND, RESTORE>(a, ws, s_done, np, nl, lane < np ? lv : 0u, lvi);
-    used -= np == 1 ? ws.end[s_done % kFly] : __reduce_add_sync(kFull, lane < np ? ws.end[fp] : 0u);
-    s_done += np;
+  uint32_t slot = w, par = 0;
+  if (!wait_warp(&h.full[slot], par)) {
+    if (lane == 0) report(a.status, GC_ERR_TIMEOUT, 0xfffffffeu);
+    return;
   }
+  uint32_t d = h.pk[slot];
+  if (((d >> 8) & 255u) == 0) return;
+  copy_pack<K>(a, h, ring, d, slot);
+  cp_async_commit();
+  for (;;) {
+    uint32_t nslot = slot + W, npar = par;
+    if (nslot >= S) {
+      nslot -= S;
+      npar ^= 1u;
+    }
+    // the next pack's copies, when it is placed already
+    const bool pre = __all_sync(kFull, mbar_test_wait(&h.full[nslot], npar));
+    uint32_t nd = 0;
+    if (pre) {
+      nd = h.pk[nslot];
+      if ((nd >> 8) & 255u) copy_pack<K>(a, h, ring, nd, nslot);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    const uint32_t s0 = d & 255u, np = (d >> 8) & 255u, nl = d >> 16;
+    if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+    else decode_pack4<KIND, RESTORE>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+    slot = nslot;
+    par = npar;
+    if (!pre) {
+      if (!wait_warp(&h.full[slot], par)) {
+        if (lane == 0) report(a.status, GC_ERR_TIMEOUT, 0xfffffffeu);
+        break;
+      }
+      nd = h.pk[slot];
+      if ((nd >> 8) & 255u) {
+        copy_pack<K>(a, h, ring, nd, slot);
+        cp_async_commit();
+      }
+    }
+    if (((nd >> 8) & 255u) == 0) break;
+    d = nd;
+  }
+  cp_async_wait<0>();
+}
+
+// The persistent decoder: warp 0 stages, warps 1 .. W decode. Dynamic
+// shared memory: BlockSmem, W WarpSmem<K>, then the ring (a.ring_bytes).
+template <int KIND, int K, bool RESTORE>
+__global__ void __launch_bounds__(Geo<K>::THREADS, 1) k_decode(DecodeArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  BlockSmem& h = *reinterpret_cast<BlockSmem*>(smem_raw);
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t W = (blockDim.x >> 5) - 1;
+  const uint32_t S = (kMaxSlots / W) * W;
+  WarpSmem<K>* ws = reinterpret_cast<WarpSmem<K>*>(smem_raw + sizeof(BlockSmem));
+  uint8_t* ring = smem_raw + sizeof(BlockSmem) + W * sizeof(WarpSmem<K>);
+  if (warp == 0) {
+    for (uint32_t i = lane; i < S; i += 32) {
+      mbar_init(&h.full[i], 1);
+      mbar_init(&h.empty[i], 1);
+    }
+    if (lane < kNChunk) mbar_init(&h.recbar[lane], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == 0) produce<KIND, K>(a, h, W, S);
+  else consume<KIND, K, RESTORE>(a, h, ws[warp - 1], ring, warp - 1, W, S);
 }
 
 // --------------------------------------------------------------- the plan
@@ -1745,90 +1918,117 @@ using namespace gcdev;
 
 namespace {
 
-constexpr uint32_t kMaxWarps = 16;     // warps per block (launch bounds: 512 threads)
-constexpr uint32_t kDefaultWarps = 4;
-constexpr uint32_t kMaxClaim = kSeq;   // records per claim
-constexpr uint32_t kDefaultClaim = 16;
-constexpr uint64_t kHdr = 256;         // scratch header: claim counter, record counts
+constexpr uint32_t kMaxClaim = kChunk;  // records per claim
+constexpr uint64_t kHdr = 256;           // scratch header: claim counter, record counts
+// plans the 32-bit claim counter serves: every block may claim twice past
+// the end, with up to 8 blocks on each of up to 512 SMs
+constexpr uint64_t kMaxWork = 0xffffffffull - 2ull * kMaxClaim * 8 * 512;
+
+// A launch shape of the persistent decoder: decoding warps per block (plus
+// the staging warp), blocks per SM, records per claim, ring bytes per block
+// (0: all the shared memory the block's share of the SM leaves).
+struct Shape {
+  uint32_t warps, bps, claim, stage;
+};
+
+Shape default_shape(uint32_t k) { return k == 32 ? Shape{7, 3, kMaxClaim, 0} : Shape{7, 2, kMaxClaim, 0}; }
+
+// Device facts the launches need, looked up once per device.
+struct DevInfo {
+  int optin = 0;      // shared memory a block may opt in to
+  int per_sm = 0;     // shared memory of an SM
+};
+
+std::mutex g_launch_mu;
+DevInfo g_dev[64];
 
 template <int KIND, int K, bool RESTORE>
-cudaError_t launch_t(const DecodeArgs& a, uint32_t warps, uint32_t blocks_per_sm, uint64_t work, cudaStream_t s) {
+gc_status launch_t(DecodeArgs a, Shape sh, uint64_t work, cudaStream_t s) {
   auto fn = k_decode<KIND, K, RESTORE>;
-  // the shared-memory limit only grows, and the occupancy is fixed per
-  // (device, warps): both are cached so a launch costs one API call
-  static size_t smem_limit[64] = {};
-  static int cached_occ[64][kMaxWarps + 1] = {};
-  static int optin[64] = {};
+  // per device: the opted-in shared-memory size of this kernel (it only
+  // grows) and the occupancy of the last shape asked for
+  static size_t smem_set[64] = {};
+  static uint32_t occ_key[64][2] = {};
+  static int occ_val[64] = {};
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const bool cache = dev >= 0 && dev < 64;
-  // a block holds as many warps as its shared memory allows
-  int max_smem = cache ? optin[dev] : 0;
-  if (max_smem == 0) {
-    e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    if (cache) optin[dev] = max_smem;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GC_ERR_CUDA;
+  if (dev < 0 || dev >= 64) return GC_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_launch_mu);
+  DevInfo& di = g_dev[dev];
+  if (di.optin == 0) {
+    if (cudaDeviceGetAttribute(&di.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&di.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+      return GC_ERR_CUDA;
   }
-  const uint32_t fit = (uint32_t)(max_smem / sizeof(WarpSmem<K>));
-  if (fit == 0) return cudaErrorInvalidConfiguration;
-  if (warps > fit) warps = fit;
-  const size_t smem = warps * sizeof(WarpSmem<K>);
-  if (!cache || smem > smem_limit[dev]) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (cache) smem_limit[dev] = smem;
+  const uint32_t max_warps = Geo<K>::THREADS / 32 - 1;
+  const uint32_t W = sh.warps < 1 ? 1u : sh.warps > max_warps ? max_warps : sh.warps;
+  const uint32_t bps = sh.bps ? sh.bps : default_shape(K).bps;
+  // the block's share of the SM's shared memory (1 KB of it is reserved per block)
+  int64_t budget = (int64_t)di.per_sm / bps - 1024;
+  if (budget > di.optin) budget = di.optin;
+  const int64_t fixed = (int64_t)sizeof(BlockSmem) + (int64_t)W * sizeof(WarpSmem<K>);
+  int64_t ring = (budget - fixed) & ~127ll;
+  if (sh.stage && (int64_t)sh.stage < ring) ring = (int64_t)sh.stage & ~127ll;
+  if (ring < kPackCap) return GC_ERR_INVALID;  // the shape leaves no room for a pack
+  const size_t smem = (size_t)(fixed + ring);
+  if (smem > smem_set[dev]) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GC_ERR_CUDA;
+    smem_set[dev] = smem;
   }
-  int occ = cache ? cached_occ[dev][warps] : 0;
-  if (occ == 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, (int)(warps * 32), smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    if (cache) cached_occ[dev][warps] = occ;
+  const uint32_t threads = 32 * (W + 1);
+  if (occ_key[dev][0] != threads || occ_key[dev][1] != (uint32_t)smem || occ_val[dev] == 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, (int)threads, smem) != cudaSuccess) return GC_ERR_CUDA;
+    if (occ < 1) return GC_ERR_INVALID;
+    occ_key[dev][0] = threads;
+    occ_key[dev][1] = (uint32_t)smem;
+    occ_val[dev] = occ;
   }
-  const int sms = gc_host::sm_count();
-  uint32_t bps = blocks_per_sm ? blocks_per_sm : (uint32_t)occ;
-  if (bps > (uint32_t)occ) bps = (uint32_t)occ;
-  uint64_t grid = (uint64_t)bps * sms;
-  const uint64_t need = (work + warps - 1) / warps;  // at least one record per warp
-  if (grid > need) grid = need ? need : 1;
-  fn<<<(unsigned)grid, warps * 32, smem, s>>>(a);
+  const uint32_t fit = bps < (uint32_t)occ_val[dev] ? bps : (uint32_t)occ_val[dev];
+  uint64_t grid = (uint64_t)fit * gc_host::sm_count();
+  a.claim = sh.claim < 1 ? 1u : sh.claim > kMaxClaim ? kMaxClaim : sh.claim;
+  a.ring_bytes = (uint32_t)ring;
+  const uint64_t chunks = (work + a.claim - 1) / a.claim;  // at least one claim per block
+  if (grid > chunks) grid = chunks ? chunks : 1;
+  fn<<<(unsigned)grid, threads, smem, s>>>(a);
   gc_host::count_launch();
-  return cudaGetLastError();
+  return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;
 }
 
 template <bool RESTORE>
-cudaError_t launch_r(uint32_t kind, uint32_t k, const DecodeArgs& a, uint32_t warps, uint32_t bps, uint64_t work,
-                     cudaStream_t s) {
-#define GC_DISPATCH(KIND)                                                      \
-  if (kind == KIND) {                                                           \
-    if (k == 4) return launch_t<KIND, 4, RESTORE>(a, warps, bps, work, s);      \
-    return launch_t<KIND, 32, RESTORE>(a, warps, bps, work, s);                 \
+gc_status launch_r(uint32_t kind, uint32_t k, const DecodeArgs& a, Shape sh, uint64_t work, cudaStream_t s) {
+#define GC_DISPATCH(KIND)                                                 \
+  if (kind == KIND) {                                                      \
+    if (k == 4) return launch_t<KIND, 4, RESTORE>(a, sh, work, s);         \
+    return launch_t<KIND, 32, RESTORE>(a, sh, work, s);                    \
   }
   GC_DISPATCH(GC_SIMPLE)
   GC_DISPATCH(GC_SCHEME)
   GC_DISPATCH(GC_AFOR)
   GC_DISPATCH(GC_PFD)
 #undef GC_DISPATCH
-  return cudaErrorInvalidValue;
+  return GC_ERR_INVALID;
 }
 
-cudaError_t launch_decode(uint32_t kind, uint32_t k, bool restore, const DecodeArgs& a, uint32_t warps, uint32_t bps,
-                          uint64_t work, cudaStream_t s) {
-  return restore ? launch_r<true>(kind, k, a, warps, bps, work, s) : launch_r<false>(kind, k, a, warps, bps, work, s);
+gc_status launch_decode(uint32_t kind, uint32_t k, bool restore, const DecodeArgs& a, Shape sh, uint64_t work,
+                        cudaStream_t s) {
+  return restore ? launch_r<true>(kind, k, a, sh, work, s) : launch_r<false>(kind, k, a, sh, work, s);
 }
 
-// Launch shape from the caller's request (NULL = defaults); GC_ERR_INVALID
-// for a shape out of range.
-gc_status launch_shape(const gc_launch* l, uint32_t* warps, uint32_t* bps, uint32_t* claim) {
-  *warps = kDefaultWarps;
-  *bps = 0;
-  *claim = kDefaultClaim;
+// Launch shape from the caller's request (NULL = the library default for
+// this k, every field 0 = its default); GC_ERR_INVALID for a shape out of
+// range.
+gc_status launch_shape(const gc_codec& c, const gc_launch* l, Shape* sh) {
+  *sh = default_shape(c.k);
   if (!l) return GC_OK;
-  if (l->warps_per_block > kMaxWarps || l->items_per_claim > kMaxClaim) return GC_ERR_INVALID;
-  if (l->warps_per_block) *warps = l->warps_per_block;
-  *bps = l->blocks_per_sm;
-  if (l->items_per_claim) *claim = l->items_per_claim;
+  const uint32_t max_warps = (c.k == 32 ? Geo<32>::THREADS : Geo<4>::THREADS) / 32 - 1;
+  if (l->warps_per_block > max_warps || l->items_per_claim > kMaxClaim || l->blocks_per_sm > 8)
+    return GC_ERR_INVALID;
+  if (l->warps_per_block) sh->warps = l->warps_per_block;
+  if (l->blocks_per_sm) sh->bps = l->blocks_per_sm;
+  if (l->items_per_claim) sh->claim = l->items_per_claim;
+  sh->stage = l->stage_bytes;
   return GC_OK;
 }
 
@@ -1901,8 +2101,7 @@ namespace {
 gc_status decode_plan_impl(const gc_codec& c, const gc_work* work, const uint64_t* count, uint64_t work_cap,
                            const uint8_t* ctrl_pool, uint64_t ctrl_pool_bytes, const uint32_t* data_pool,
                            uint64_t data_pool_words, uint32_t* out_pool, uint64_t out_pool_len, int restore,
-                           uint32_t warps, uint32_t bps, uint32_t claim, unsigned char* scratch, uint32_t* status,
-                           cudaStream_t s) {
+                           Shape sh, unsigned char* scratch, uint32_t* status, cudaStream_t s) {
   uint32_t* counter = reinterpret_cast<uint32_t*>(scratch);
   unsigned long long* lb = reinterpret_cast<unsigned long long*>(scratch + kHdr);
   if (cudaMemsetAsync(scratch, 0, 64, s) != cudaSuccess) return GC_ERR_CUDA;
@@ -1921,10 +2120,8 @@ gc_status decode_plan_impl(const gc_codec& c, const gc_work* work, const uint64_
   a.lb = restore ? lb : nullptr;
   a.cg = c.cg;
   a.ld = c.ld;
-  a.claim = claim;
   a.status = status;
-  const cudaError_t e = launch_decode(c.kind, c.k, restore != 0, a, warps, bps, work_cap, s);
-  return e == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+  return launch_decode(c.kind, c.k, restore != 0, a, sh, work_cap, s);
 }
 
 uint64_t tiles_of(const gc_codec& c, uint64_t n) {
@@ -2000,7 +2197,7 @@ gc_status gc_decode(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t ctrl_
   // the look-back words sit right after the header, as gc_decode_plan expects
   gc_host::reset_launches();
   st = decode_plan_impl(*codec, work, count, nt, pool, lead + ctrl_bytes, d_data, data_words, d_out, n,
-                        restore_docids, kDefaultWarps, 0, kDefaultClaim, base, d_status, s);
+                        restore_docids, default_shape(codec->k), base, d_status, s);
   gc_host::count_launch(launches);
   return st;
 }
@@ -2055,7 +2252,7 @@ gc_status gc_decode_paper(const gc_codec* codec, const uint8_t* d_buf, uint64_t 
   launches += gc_host::launches();
   gc_host::reset_launches();
   st = decode_plan_impl(*codec, work, count, nt, d_buf, doff, data, data_words, d_out, n, restore_docids,
-                        kDefaultWarps, 0, kDefaultClaim, base, d_status, s);
+                        default_shape(codec->k), base, d_status, s);
   gc_host::count_launch(launches);
   return st;
 }
@@ -2107,16 +2304,16 @@ gc_status gc_decode_plan(const gc_codec* codec, const gc_work* d_work, const uin
     return GC_ERR_INVALID;
   if (((uintptr_t)d_data_pool & 15) != 0 || ((uintptr_t)d_ctrl_pool & 15) != 0 || ((uintptr_t)d_work & 15) != 0)
     return GC_ERR_INVALID;
-  if (work_cap > 0xffffffffull - kMaxClaim * 64ull) return GC_ERR_UNSUPPORTED;
+  if (work_cap > kMaxWork) return GC_ERR_UNSUPPORTED;
   uint64_t need = 0;
   gc_decode_plan_scratch_size(work_cap, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
-  uint32_t warps, bps, claim;
-  st = launch_shape(launch, &warps, &bps, &claim);
+  Shape sh;
+  st = launch_shape(*codec, launch, &sh);
   if (st != GC_OK) return st;
   return decode_plan_impl(*codec, d_work, d_count, work_cap, d_ctrl_pool, ctrl_pool_bytes, d_data_pool,
-                          data_pool_words, d_out_pool, out_pool_len, restore_docids, warps, bps, claim,
-                          (unsigned char*)d_scratch, d_status, (cudaStream_t)stream);
+                          data_pool_words, d_out_pool, out_pool_len, restore_docids, sh, (unsigned char*)d_scratch,
+                          d_status, (cudaStream_t)stream);
 }
 
 gc_status gc_decode_batch_scratch_size(uint64_t nlists, uint64_t max_tiles, uint64_t* bytes) {
@@ -2142,12 +2339,12 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
       !d_scratch)
     return GC_ERR_INVALID;
   if (((uintptr_t)d_data_pool & 15) != 0 || ((uintptr_t)d_ctrl_pool & 15) != 0) return GC_ERR_INVALID;
-  if (max_tiles > 0xffffffffull - kMaxClaim * 64ull || nlists > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  if (max_tiles > kMaxWork || nlists > 0xffffffffull) return GC_ERR_UNSUPPORTED;
   uint64_t need = 0;
   gc_decode_batch_scratch_size(nlists, max_tiles, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
-  uint32_t warps, bps, claim;
-  st = launch_shape(launch, &warps, &bps, &claim);
+  Shape sh;
+  st = launch_shape(*codec, launch, &sh);
   if (st != GC_OK) return st;
   unsigned char* base = (unsigned char*)d_scratch;
   uint64_t* count = reinterpret_cast<uint64_t*>(base + 64);
@@ -2160,7 +2357,7 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
   const uint32_t planned = gc_host::launches();
   gc_host::reset_launches();
   st = decode_plan_impl(*codec, work, count, max_tiles, d_ctrl_pool, ctrl_pool_bytes, d_data_pool, data_pool_words,
-                        d_out_pool, out_pool_len, restore_docids, warps, bps, claim, rest, d_status, s);
+                        d_out_pool, out_pool_len, restore_docids, sh, rest, d_status, s);
   gc_host::count_launch(planned);
   return st;
 }

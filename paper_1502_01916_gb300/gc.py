@@ -79,7 +79,7 @@ class gc_list(ctypes.Structure):
 
 class gc_launch(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
-                ("items_per_claim", ctypes.c_uint32)]
+                ("items_per_claim", ctypes.c_uint32), ("stage_bytes", ctypes.c_uint32)]
 
 
 class gc_work(ctypes.Structure):

@@ -1,12 +1,13 @@
 """Autotuner of the persistent decoder's launch shape.
 
-The decoder's speed on a given index depends on how many warps share a block
-(shared memory per block, claims per SM) and on how many tiles a warp claims
-at once (atomics against the pipeline depth of its staging ring). This module
+The decoder's speed on a given index depends on how many decoding warps
+share a block's staging warp and ring, how many blocks share an SM, how many
+plan records a block claims per atomic, and how deep the staging ring is
+(how many bytes of compressed data each block keeps in flight). This module
 times gc_decode_plan on the caller's resident index for a small grid of
-shapes, keeps the fastest, and caches it in a JSON file keyed by the device,
-the codec and the workload class (how long the index's lists are), so that a
-server or benchmark tunes once per kind of index.
+those shapes, keeps the fastest, and caches it in a JSON file keyed by the
+device, the codec and the workload class (how long the index's lists are),
+so that a server or benchmark tunes once per kind of index.
 """
 from __future__ import annotations
 
@@ -18,7 +19,20 @@ import numpy as np
 
 from . import gc as _gc
 
-DEFAULT_CANDIDATES = [(w, 0, c) for w in (2, 4, 8) for c in (4, 8, 16)]
+# (decoding warps per block, blocks per SM, records per claim, ring bytes; 0 = all that fits)
+CANDIDATES = {
+    32: [(7, 3, 32, 0), (6, 3, 32, 0), (8, 3, 32, 0), (5, 4, 32, 0), (4, 4, 32, 0), (9, 2, 32, 0), (11, 2, 32, 0),
+         (7, 3, 16, 0), (7, 3, 32, 16384)],
+    4: [(7, 2, 32, 0), (7, 2, 32, 24576), (7, 2, 16, 0), (3, 4, 32, 0), (15, 1, 32, 0)],
+}
+
+
+
+
+def candidates_for(k: int):
+    return CANDIDATES[32 if k == 32 else 4]
+
+
 _lock = threading.Lock()
 
 
@@ -73,15 +87,14 @@ def tune(index, plan=None, restore_docids: bool = True, candidates=None, reps: i
     if use_cache:
         with _lock:
             hit = load_cache(path).get(key)
-        if hit:
-            w, b, c = hit["shape"]
-            return _gc.gc_launch(w, b, c), {"key": key, "best_ms": hit["ms"], "ms": {}, "cached": True}
+        if hit and len(hit.get("shape", ())) == 4:
+            return _gc.gc_launch(*hit["shape"]), {"key": key, "best_ms": hit["ms"], "ms": {}, "cached": True}
     plan = plan if plan is not None else _gc.plan_index(index)
     out = torch.empty(max(1, index.out_ints), dtype=torch.int32, device=dev)
     scratch = torch.empty(_gc.gc_decode_plan_scratch_size(index.max_tiles), dtype=torch.uint8, device=dev)
     st = _gc.new_status(dev)
     times = {}
-    for shape in candidates or DEFAULT_CANDIDATES:
+    for shape in candidates or candidates_for(index.codec.k):
         launch = _gc.gc_launch(*shape)
         _gc.decode_index(index, out=out, restore_docids=restore_docids, launch=launch, scratch=scratch, status=st,
                          plan=plan, check=False)
@@ -101,4 +114,4 @@ def tune(index, plan=None, restore_docids: bool = True, candidates=None, reps: i
             cache[key] = {"shape": list(best), "ms": times[best]}
             save_cache(path, cache)
     return _gc.gc_launch(*best), {"key": key, "best_ms": times[best],
-                                  "ms": {f"{w}x{b}x{c}": t for (w, b, c), t in times.items()}, "cached": False}
+                                  "ms": {"x".join(map(str, sh)): t for sh, t in times.items()}, "cached": False}

@@ -50,7 +50,7 @@ def test_struct_sizes_match_header(gc):
     assert ctypes.sizeof(gc.gc_tile) == 32
     assert ctypes.sizeof(gc.gc_list) == 40
     assert ctypes.sizeof(gc.gc_work) == 64
-    assert ctypes.sizeof(gc.gc_launch) == 12
+    assert ctypes.sizeof(gc.gc_launch) == 16
     assert O.TILE_DTYPE.itemsize == 32
     assert gc.TILE_DTYPE == O.TILE_DTYPE
     assert gc.LIST_DTYPE.itemsize == 40 and gc.WORK_DTYPE.itemsize == 64

@@ -260,35 +260,53 @@ def test_batch_aligned_outputs(gc, kind, k):
         assert (got[hole] == np.uint32(0xFFFFFFF9)).all()
 
 
-@pytest.mark.parametrize("warps,bps,claim", [(1, 1, 1), (4, 2, 2), (8, 0, 0), (16, 0, 7), (2, 1, 16)])
+@pytest.mark.parametrize("warps,bps,claim,stage", [(1, 1, 1, 0), (4, 2, 2, 0), (8, 0, 0, 0), (15, 1, 7, 0),
+                                                   (2, 1, 16, 12288), (11, 2, 32, 20480), (3, 4, 5, 0)])
 @pytest.mark.parametrize("k", [4, 32])
-def test_batch_launch_shapes(gc, warps, bps, claim, k):
-    """The result does not depend on the launch shape or the claim size, with
-    a plan built once and reused."""
+def test_batch_launch_shapes(gc, warps, bps, claim, stage, k):
+    """The result does not depend on the launch shape (decoding warps per
+    block, blocks per SM, records per claim, ring bytes), with a plan built
+    once and reused."""
     oc, gcc = pair(gc, (O.PFD, k, 0, 0, 0.1))
     lens, gaps, off = small_index(5)
     idx = gc.encode_index(gcc, upload_u32(gaps), lens)
     want = np.concatenate([O.prefix_sum(gaps[off[i]:off[i + 1]]) for i in range(len(lens))])
-    out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps, claim))
+    out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps, claim, stage))
     assert (gc.as_u32(out)[:len(gaps)] == want).all()
     plan = gc.plan_index(idx)
     assert int(plan.count[0].item()) == idx.max_tiles
     assert int(plan.count[1].item()) == 0  # every tile has its skip entry
     for _ in range(2):
-        out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps, claim), plan=plan)
+        out = gc.decode_index(idx, launch=gc.gc_launch(warps, bps, claim, stage), plan=plan)
+        assert (gc.as_u32(out)[:len(gaps)] == want).all()
+
+
+@pytest.mark.parametrize("c", [(O.SIMPLE, 32, 0, 0, 0.1), (O.SCHEME, 32, 4, 1, 0.1), (O.AFOR, 32, 0, 0, 0.1)])
+def test_batch_widest_block(gc, c):
+    """k = 32 with the most decoding warps a block can have (23, one block
+    per SM) and the smallest ring a shape may ask for."""
+    _, gcc = pair(gc, c)
+    lens, gaps, off = small_index(8)
+    idx = gc.encode_index(gcc, upload_u32(gaps), lens)
+    want = np.concatenate([O.prefix_sum(gaps[off[i]:off[i + 1]]) for i in range(len(lens))])
+    for launch in (gc.gc_launch(23, 1, 32, 0), gc.gc_launch(23, 1, 32, 12288)):
+        out = gc.decode_index(idx, launch=launch)
         assert (gc.as_u32(out)[:len(gaps)] == want).all()
 
 
 def test_launch_shape_out_of_range_rejected(gc):
-    """Claims of more than 16 tiles or blocks of more than 16 warps are
-    refused on the host, before any launch."""
-    _, gcc = pair(gc, (O.SIMPLE, 32, 0, 0, 0.1))
-    lens, gaps, off = small_index(4, nlists=20)
-    idx = gc.encode_index(gcc, upload_u32(gaps), lens)
-    for bad in (gc.gc_launch(4, 0, 17), gc.gc_launch(17, 0, 1)):
-        with pytest.raises(gc.GcError) as ei:
-            gc.decode_index(idx, launch=bad)
-        assert ei.value.code == 1
+    """Claims of more than 32 records, more decoding warps than a block may
+    have, more than 8 blocks per SM, and shapes that leave the ring less
+    than 12 KB are refused on the host, before any launch."""
+    for k, too_many in ((32, 24), (4, 16)):
+        _, gcc = pair(gc, (O.SIMPLE, k, 0, 0, 0.1))
+        lens, gaps, off = small_index(4, nlists=20)
+        idx = gc.encode_index(gcc, upload_u32(gaps), lens)
+        for bad in (gc.gc_launch(4, 0, 33), gc.gc_launch(too_many, 0, 1), gc.gc_launch(4, 9, 1),
+                    gc.gc_launch(4, 1, 1, 4096), gc.gc_launch(too_many - 1, 4, 1)):
+            with pytest.raises(gc.GcError) as ei:
+                gc.decode_index(idx, launch=bad)
+            assert ei.value.code == 1, (k, bad.warps_per_block, bad.blocks_per_sm, bad.stage_bytes)
 
 
 def test_plan_records(gc):

@@ -19,8 +19,8 @@ def test_cache_round_trip(tmp_path):
     assert load_cache(path) == {}
     key = cache_key("GB300", make_codec(SIMPLE, 32), np.full(10, 5000), True)
     assert key.endswith("|long-multi|ids") and key.startswith("GB300|GS/k32")
-    save_cache(path, {key: {"shape": [4, 0, 8], "ms": 1.5}})
-    assert load_cache(path)[key]["shape"] == [4, 0, 8]
+    save_cache(path, {key: {"shape": [11, 2, 32, 0], "ms": 1.5}})
+    assert load_cache(path)[key]["shape"] == [11, 2, 32, 0]
     with open(path, "w") as f:
         f.write("not json")
     assert load_cache(path) == {}
