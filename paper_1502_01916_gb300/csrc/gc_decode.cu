@@ -29,6 +29,7 @@
 //     as coalesced 16-byte stores.
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "gc_device.cuh"
@@ -519,7 +520,8 @@ __device__ __forceinline__ bool parse_pfd4(const CtrlView& C, uint64_t f0, uint6
 // overwrites its slot in the pack's line-major buffer (line l at words
 // 32 l .., 16-byte chunk c at chunk c ^ (l & 7)); the tile's first line is
 // line0. Headers and records were checked by parse_pfd4; a position
-// outside its frame is reported.
+// outside its frame, or one that does not increase on the one before, is
+// reported.
 __device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, uint32_t* tb, const CtrlView& C, uint64_t f0,
                                            uint64_t exc_at, uint32_t rows, uint32_t line0, uint32_t list) {
   const uint32_t lane = lane_id();
@@ -548,7 +550,7 @@ __device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, uint32_t* tb, co
     const uint8_t* vp = rp + ef;
     for (uint32_t x = lane; x < ef; x += 32) {
       const uint32_t pos = rp[x];
-      if (pos >= limf) {
+      if (pos >= limf || (x && rp[x - 1] >= pos)) {
         report(a.status, GC_ERR_CORRUPT, list);
         continue;
       }
@@ -571,7 +573,7 @@ __device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, uint32_t* tb, co
 // a prefix, so the walk ends inside the list. Returns the exclusive prefix
 // (all lanes). Every wait is bounded; one that runs out reports
 // GC_ERR_TIMEOUT and the walk stops.
-__device__ uint32_t look_back(const unsigned long long* lb, uint64_t item, uint64_t t, uint32_t* status,
+__device__ __noinline__ uint32_t look_back(const unsigned long long* lb, uint64_t item, uint64_t t, uint32_t* status,
                               uint32_t where) {
   const uint32_t lane = lane_id();
   uint32_t excl = 0;
@@ -683,16 +685,55 @@ __device__ __forceinline__ Items load_items(const BlockSmem& h, WarpSmem<K>& ws,
   return t;
 }
 
+// docIDs (Sec 2.1.1), the general case of line_bases: each item's base is
+// its skip entry or, without one, the sum of the list's tiles before it by
+// look-back (every item publishes its aggregate, then its inclusive
+// prefix, for the tiles after it). Lane p holds item p's facts; V is the
+// plain warp scan of the line totals T. Returns each line's base. (Kept
+// out of line: packs of one tile with a skip entry, most of the work, do
+// not need it.)
+template <int K>
+__device__ __noinline__ uint32_t line_bases_chain(const DecodeArgs& a, WarpSmem<K>& ws, uint32_t V, uint32_t T, bool act,
+                                                  uint32_t rank, uint32_t lhead, bool live, bool dead, uint32_t line0,
+                                                  uint32_t lines, uint32_t shape, uint32_t tile, uint32_t base_in,
+                                                  uint32_t item, uint32_t list, uint32_t irank) {
+  const uint32_t lane = lane_id();
+  const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
+  const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
+  const uint32_t E = v - T;
+  const uint32_t lastl = live ? line0 + lines - 1 : 0u;
+  const uint32_t tot = __shfl_sync(kFull, v, lastl);
+  const bool has_base = (shape & GC_WORK_HAS_BASE) != 0;
+  const bool needs_lb = live && tile > 0 && !has_base;
+  uint32_t base = has_base ? base_in : 0u;
+  if (a.lb) {
+    if (live && !needs_lb && (shape & GC_WORK_PUBLISH)) st_release(a.lb + item, kFlagPrefix | (uint32_t)(base + tot));
+    if (dead) st_release(a.lb + item, kFlagPrefix);  // its error is reported
+    if (needs_lb) st_release(a.lb + item, kFlagAgg | tot);
+  }
+  for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
+    const uint32_t p = __ffs(pend) - 1;
+    const uint32_t it = __shfl_sync(kFull, item, p);
+    const uint32_t tl = __shfl_sync(kFull, tile, p);
+    const uint32_t lst = __shfl_sync(kFull, list, p);
+    const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
+    if (lane == p) {
+      base = ex;
+      if (a.lb) st_release(a.lb + item, kFlagPrefix | (uint32_t)(ex + tot));
+    }
+  }
+  if (live) ws.ibase[irank] = base;
+  __syncwarp();
+  return E + (act ? ws.ibase[rank] : 0u);
+}
+
 // docIDs (Sec 2.1.1): line l holds the running sum R of its own ints; a
 // plain warp scan of the line totals, less the scan before the first line
-// of the line's item, is the sum of the item's ints before the line, and
-// the item's base is its skip entry or, without one, the sum of the list's
-// tiles before it by look-back (every item publishes its aggregate, then
-// its inclusive prefix, for the tiles after it). Returns each line's base.
+// of the line's item, is the sum of the item's ints before the line, plus
+// the item's base. Returns each line's base.
 template <int K>
 __device__ __forceinline__ uint32_t line_bases(const DecodeArgs& a, WarpSmem<K>& ws, const Items& t, uint32_t np,
                                                bool act, uint32_t R, uint32_t rank, uint32_t lhead) {
-  const uint32_t lane = lane_id();
   const uint32_t T = act ? R : 0u;
   const uint32_t V = warp_incl_sum(T);
   const uint32_t shape0 = __shfl_sync(kFull, t.shape, 0);
@@ -701,34 +742,8 @@ __device__ __forceinline__ uint32_t line_bases(const DecodeArgs& a, WarpSmem<K>&
     // waits for
     return V - T + __shfl_sync(kFull, t.base, 0);
   }
-  const uint32_t Vb = __shfl_sync(kFull, V, (lhead - 1u) & 31u);
-  const uint32_t v = V - (lhead ? Vb : 0u);  // inclusive within the item
-  const uint32_t E = v - T;
-  const uint32_t lastl = t.live ? t.line0 + t.lines - 1 : 0u;
-  const uint32_t tot = __shfl_sync(kFull, v, lastl);
-  const bool has_base = (t.shape & GC_WORK_HAS_BASE) != 0;
-  const bool needs_lb = t.live && t.tile > 0 && !has_base;
-  uint32_t base = has_base ? t.base : 0u;
-  if (a.lb) {
-    if (t.live && !needs_lb && (t.shape & GC_WORK_PUBLISH))
-      st_release(a.lb + t.item, kFlagPrefix | (uint32_t)(base + tot));
-    if (t.dead) st_release(a.lb + t.item, kFlagPrefix);  // its error is reported
-    if (needs_lb) st_release(a.lb + t.item, kFlagAgg | tot);
-  }
-  for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
-    const uint32_t p = __ffs(pend) - 1;
-    const uint32_t it = __shfl_sync(kFull, t.item, p);
-    const uint32_t tl = __shfl_sync(kFull, t.tile, p);
-    const uint32_t lst = __shfl_sync(kFull, t.list, p);
-    const uint32_t ex = a.lb ? look_back(a.lb, it, tl, a.status, lst) : 0u;
-    if (lane == p) {
-      base = ex;
-      if (a.lb) st_release(a.lb + t.item, kFlagPrefix | (uint32_t)(ex + tot));
-    }
-  }
-  if (t.live) ws.ibase[t.rank] = base;
-  __syncwarp();
-  return E + (act ? ws.ibase[rank] : 0u);
+  return line_bases_chain<K>(a, ws, V, T, act, rank, lhead, t.live, t.dead, t.line0, t.lines, t.shape, t.tile, t.base,
+                             t.item, t.list, t.rank);
 }
 
 // The k = 4 pack decoder (the paper's own layout): records s0 .. s0 + np - 1
@@ -933,7 +948,7 @@ __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4
       }
     } else {
       const uint32_t wsw = 4u * (lane >> 2), wlo = lane & 3u;
-#pragma unroll
+#pragma unroll 1
       for (int rr = 0; rr < 32; ++rr) o1[rr * 32 + lane] = ws.tb[rr * 32 + (wsw ^ (4u * (rr & 7))) + wlo];
     }
   } else {
@@ -1052,13 +1067,21 @@ __device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, const B
 // pack's line-major buffer (line l at words 32 l .. 32 l + 31, its 16-byte
 // chunk c at chunk c ^ (l & 7)): e 16-bit positions at rp, then e values of
 // wb bytes (Sec 6.2, decoding Step 3); the tile's first line is hl, its
-// frame holds lim ints. A position outside the frame is reported.
+// frame holds lim ints. A position outside the frame, or one that does not
+// increase on the one before, is reported.
 __device__ __forceinline__ void pfd_patch(const DecodeArgs& a, uint32_t* tb, uint32_t lane, uint32_t hl, uint32_t e,
                                           uint32_t lim, uint32_t wb, const uint8_t* rp, uint32_t list) {
   const uint8_t* vp = rp + (size_t)e * 2;
-  for (uint32_t x = lane; x < e; x += 32) {
-    const uint32_t pos = (uint32_t)rp[2 * x] | ((uint32_t)rp[2 * x + 1] << 8);
-    if (pos >= lim) {
+  uint32_t last = 0;  // the position before this round's first
+#pragma unroll 1
+  for (uint32_t x0 = 0; x0 < e; x0 += 32) {
+    const uint32_t x = x0 + lane;
+    const uint32_t pos = x < e ? (uint32_t)rp[2 * x] | ((uint32_t)rp[2 * x + 1] << 8) : 0xffffu;
+    const uint32_t up = __shfl_up_sync(kFull, pos, 1);
+    const uint32_t before = lane ? up : last;
+    last = __shfl_sync(kFull, pos, 31);
+    if (x >= e) continue;
+    if (pos >= lim || (x && before >= pos)) {
       report(a.status, GC_ERR_CORRUPT, list);
       continue;
     }
@@ -1140,13 +1163,9 @@ __device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, const Bloc
 }
 
 // Group-PFD, k = 32: the exceptions of every tile of the pack over their
-// slots (a pack of one tile: every lane already holds its facts).
+// slots.
 __device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, uint32_t* tb, uint32_t lane, uint32_t heads,
                                                  const PfdExc& x) {
-  if (heads == 1u) {
-    pfd_patch(a, tb, lane, 0, x.e, x.lim, x.wb, x.rp, x.list);
-    return;
-  }
   for (uint32_t hm = heads; hm; hm &= hm - 1) {
     const uint32_t hl = __ffs(hm) - 1;  // the tile's first line
     const uint32_t e = __shfl_sync(kFull, x.e, hl);
@@ -1239,21 +1258,22 @@ __device__ void decode_pack32(const DecodeArgs& a, const BlockSmem& h, WarpSmem<
                                   : reinterpret_cast<const uint4*>(ws.tb + 32 * lane);
   uint4* T = reinterpret_cast<uint4*>(ws.tb + 32 * lane);
   const uint32_t swz = lane & 7u;
-  bool patch = false;  // (Group-PFD) a tile of the pack has exceptions
-  if (KIND == GC_PFD) patch = (__ballot_sync(kFull, px.e != 0) & t.heads) != 0;
   uint32_t R = 0;
-  if (RESTORE && !patch) {
-    extract_line32<KIND, true>(P, sh, msk, cross, T, swz, R);
+  if (KIND != GC_PFD) {
+    extract_line32<KIND, RESTORE>(P, sh, msk, cross, T, swz, R);
   } else {
-    extract_line32<KIND, false>(P, sh, msk, cross, T, swz, R);
-  }
-  if (KIND == GC_PFD && patch) {
-    // the slots' values are in the buffer: the exceptions over them (most
-    // frames have none), then the running sum over the patched line
-    __syncwarp();
-    pfd_patch_pack32(a, ws.tb, lane, t.heads, px);
-    __syncwarp();
-    if (RESTORE) {
+    // Group-PFD: without exceptions in the pack, the running sums at once;
+    // with them, the slots' values, the exceptions over them, then the
+    // running sum over the patched line
+    const bool pp = (__ballot_sync(kFull, px.e != 0) & t.heads) != 0;
+    if (RESTORE && !pp) extract_line32<KIND, true>(P, sh, msk, cross, T, swz, R);
+    else extract_line32<KIND, false>(P, sh, msk, cross, T, swz, R);
+    if (pp) {
+      __syncwarp();
+      pfd_patch_pack32(a, ws.tb, lane, t.heads, px);
+      __syncwarp();
+    }
+    if (RESTORE && pp) {
       R = 0;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
@@ -1306,7 +1326,7 @@ __device__ void decode_pack32(const DecodeArgs& a, const BlockSmem& h, WarpSmem<
       }
     } else {
       const uint32_t wsw = 4u * (lane >> 2), wlo = lane & 3u;
-#pragma unroll
+#pragma unroll 1
       for (int rr = 0; rr < 32; ++rr) {
         const uint32_t kk = RESTORE ? __shfl_sync(kFull, k0, rr) : 0u;
         o1[rr * 32 + lane] = ws.tb[rr * 32 + (wsw ^ (4u * (rr & 7))) + wlo] + kk;
@@ -1395,19 +1415,20 @@ __device__ __forceinline__ bool ring_drain(BlockSmem& h, Ring& r, uint32_t S) {
 }
 
 // Claim up to `claim` records for record buffer b and start the bulk copy
-// that brings them in; returns their first plan index (lane-uniform) and
-// count.
-__device__ __forceinline__ void claim_records(const DecodeArgs& a, BlockSmem& h, uint32_t b, uint32_t claim,
-                                              uint64_t total, uint32_t& x, uint32_t& cnt) {
+// that brings them in; returns their first plan index and count (x, y;
+// lane-uniform).
+__device__ __noinline__ uint2 claim_records(const DecodeArgs& a, BlockSmem& h, uint32_t b, uint32_t claim,
+                                            uint64_t total) {
   const uint32_t lane = lane_id();
   uint32_t v = 0;
   if (lane == 0) v = atomicAdd(a.counter, claim);
-  x = __shfl_sync(kFull, v, 0);
-  cnt = (uint64_t)x < total ? (uint32_t)min64(claim, total - x) : 0u;
+  const uint32_t x = __shfl_sync(kFull, v, 0);
+  const uint32_t cnt = (uint64_t)x < total ? (uint32_t)min64(claim, total - x) : 0u;
   if (lane == 0 && cnt) {
     mbar_expect_tx(&h.recbar[b], cnt * (uint32_t)sizeof(gc_work));
     bulk_g2s(h.rec[b * kChunk], a.work + x, cnt * (uint32_t)sizeof(gc_work), &h.recbar[b]);
   }
+  return make_uint2(x, cnt);
 }
 
 // Group the claim's records (lanes 0 .. cnt - 1) into packs: a pack is a run
@@ -1417,20 +1438,21 @@ __device__ __forceinline__ void claim_records(const DecodeArgs& a, BlockSmem& h,
 // finds by binary search how many records from i on fit one pack (next_i
 // is the first record after them); the packs start at the records reached
 // from record 0 by following next, found by pointer doubling in five
-// rounds. Returns the mask of pack starts; P is each lane's inclusive sum
-// of (lines | ring bytes / 16 << 11 | vectors << 32) and nxt its next_i.
-template <int K>
-__device__ __forceinline__ uint32_t pack_starts(uint64_t v, uint32_t cnt, uint64_t& P, uint32_t& nxt) {
+// rounds. v packs (lines | ring bytes / 16 << 11 | vectors << 32, the
+// vectors only at k = 4, whose sums then need 64 bits); returns the mask of
+// pack starts, P is each lane's inclusive sum of v and nxt its next_i.
+template <int K, class U>
+__device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_t& nxt) {
   const uint32_t lane = lane_id();
   P = warp_incl_sum(v);
-  const uint64_t Pex = P - v;
+  const U Pex = P - v;
   uint32_t len = 0;
 #pragma unroll
   for (uint32_t step = 16; step; step >>= 1) {
     const uint32_t j = lane + len + step - 1;  // the last record of the candidate
-    const uint64_t s = __shfl_sync(kFull, P, j < 32 ? j : 31u) - Pex;
-    const bool fits = j < cnt && (s & 2047u) <= 32u && ((s >> 11) & 0x1fffffu) * 16u <= (uint64_t)kPackCap &&
-                      (K != 4 || (s >> 32) <= (uint64_t)kPadVec4);
+    const U s = __shfl_sync(kFull, P, j < 32 ? j : 31u) - Pex;
+    bool fits = j < cnt && (uint32_t)(s & 2047u) <= 32u && (uint32_t)((s >> 11) & 0x1fffffu) * 16u <= (uint32_t)kPackCap;
+    if constexpr (K == 4) fits = fits && (uint64_t)(s >> 32) <= (uint64_t)kPadVec4;
     if (fits) len += step;
   }
   nxt = lane < cnt ? lane + (len ? len : 1u) : 32u;
@@ -1464,8 +1486,8 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
   Ring r = {a.ring_bytes, 0, 0, 0, 0, 0, 0, 0};
   bool failed = false;
   uint32_t busy = 0;  // lane b < kNChunk: record buffer b is free once this many packs are given back
-  uint32_t x, cnt;
-  claim_records(a, h, 0, claim, total, x, cnt);
+  const uint2 c0 = claim_records(a, h, 0, claim, total);
+  uint32_t x = c0.x, cnt = c0.y;
   for (uint32_t c = 0; cnt && !failed; ++c) {
     const uint32_t b = c % kNChunk;
     // the next claim goes to the next buffer once that buffer's packs are given back
@@ -1473,8 +1495,8 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
     const uint32_t nbusy = __shfl_sync(kFull, busy, nb);
     while (!failed && r.tail < nbusy) failed = !ring_drain(h, r, S);
     if (failed) break;
-    uint32_t nx, ncnt;
-    claim_records(a, h, nb, claim, total, nx, ncnt);
+    const uint2 cn = claim_records(a, h, nb, claim, total);
+    const uint32_t nx = cn.x, ncnt = cn.y;
     if (!wait_warp(&h.recbar[b], (c / kNChunk) & 1u)) {
       failed = true;
       break;
@@ -1492,11 +1514,12 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
       h.flines[rs] = (uint8_t)lines;
     }
     const uint32_t need16 = (nv * (uint32_t)Geo<K>::VB + cb + xb) / 16;  // ring bytes / 16
-    const uint64_t v = valid ? (uint64_t)lines | (uint64_t)need16 << 11 | (uint64_t)nv << 32 : 0ull;
-    uint64_t P;
+    using U = typename std::conditional<K == 4, uint64_t, uint32_t>::type;
+    const U v = valid ? (U)lines | (U)need16 << 11 | (K == 4 ? (U)((uint64_t)nv << 32) : (U)0) : (U)0;
+    U P;
     uint32_t nxt;
-    const uint32_t starts = pack_starts<K>(v, cnt, P, nxt);
-    const uint64_t Pex = P - v;
+    const uint32_t starts = pack_starts<K, U>(v, cnt, P, nxt);
+    const U Pex = P - v;
     // each record's offset from its pack's start; at a pack's first record,
     // the pack's ring bytes / 16, records and lines
     const uint32_t le = 0xffffffffu >> (31u - lane);  // lanes <= this one
@@ -1504,7 +1527,7 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
     const uint32_t ex16 = (uint32_t)((Pex >> 11) & 0x1fffffu);  // ring bytes / 16 before this record
     const uint32_t sex16 = __shfl_sync(kFull, ex16, s0);
     if (valid) h.rrel[rs] = (ex16 - sex16) * 16;
-    const uint64_t Pl = __shfl_sync(kFull, P, (nxt - 1u) & 31u);
+    const U Pl = __shfl_sync(kFull, P, (nxt - 1u) & 31u);
     const uint32_t pinfo = ((uint32_t)((Pl >> 11) & 0x1fffffu) - ex16) | (nxt - lane) << 16 |
                            ((uint32_t)(Pl & 2047u) - (uint32_t)(Pex & 2047u)) << 24;
     __threadfence_block();

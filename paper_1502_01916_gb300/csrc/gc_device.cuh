@@ -92,7 +92,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // ------------------------------------------------------------ status
 
 // First error wins; the second word records where (tile or list).
-__device__ __forceinline__ void report(uint32_t* status, uint32_t code, uint32_t where) {
+// (kept out of line: it sits on many paths that almost never run)
+static __device__ __noinline__ void report(uint32_t* status, uint32_t code, uint32_t where) {
   if (status && atomicCAS(status, 0u, code) == 0u) atomicExch(status + 1, where);
 }
 
