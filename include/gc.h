@@ -353,11 +353,13 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
                           const gc_launch* launch, void* d_scratch, uint64_t scratch_bytes,
                           uint32_t* d_status, void* stream);
 
-/* gc_decode for callers that cannot allocate device memory: code that runs
- * while a stream is being captured into a CUDA graph (cudaMalloc is not
- * allowed there), or latency-critical code that cannot afford the implicit
- * device-wide synchronisation of cudaMalloc / cudaFree. The paper has no
- * counterpart: this is a service of the library, not a step of the method.
+/* gc_decode for callers that cannot allocate device memory: a plug-in or
+ * service embedded in a host application that owns all of the device's
+ * memory through its own allocator (a search server that reserves the GPU's
+ * memory at start-up), or latency-critical code that cannot afford the
+ * implicit device-wide synchronisation of cudaMalloc / cudaFree. The paper
+ * has no counterpart: this is a service of the library, not a step of the
+ * method.
  *
  * Same arguments and results as gc_decode, without d_scratch: the scratch is
  * a fixed 128 KiB array inside the library, which every GPU that loads the
@@ -367,8 +369,11 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
  * cudaMalloc, cudaFree or allocating library routine).
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and keeps it; make that first call before any
- * stream capture. Every call on a device shares the one array, and each call
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the
+ * life of the process; make that first call before any stream capture.
+ * cudaDeviceReset unloads the library's device code, so the kept address is
+ * no longer valid after it: do not call gc_decode_static on a device after
+ * resetting it. Every call on a device shares the one array, and each call
  * clears what must start at zero before use: calls that overlap on the GPU
  * (on two streams, or from two threads) race and must be ordered by the
  * caller. */
