@@ -162,11 +162,12 @@ enum {
   GC_WORK_PUBLISH = 1u << 30
 };
 
-/* Launch shape of the persistent decoder (NULL = the library default; a
- * field left 0 takes its default). A block has one staging warp, which
- * claims plan records, groups them into packs of up to 32 lines of 32 ints
- * and copies each pack's bytes into a shared-memory ring, and
- * warps_per_block decoding warps, which decode the packs in turn.
+/* Launch shape of the persistent decoder (NULL = the shape registered with
+ * gc_set_launch, else the library default; a field left 0 takes its
+ * default). A block has one staging warp, which claims plan records, groups
+ * them into packs of up to 32 lines of 32 ints and places each pack in a
+ * shared-memory ring, and warps_per_block decoding warps, which copy the
+ * packs' bytes into the ring and decode them in turn.
  *   warps_per_block: decoding warps per block, 1..23 at k = 32 (default
  *     7), 1..15 at k = 4 (default 7).
  *   blocks_per_sm: resident blocks per SM, 1..8 (default 3 at k = 32, 2
@@ -174,7 +175,10 @@ enum {
  *     persistent grid is blocks_per_sm * SMs (fewer when fewer fit). A
  *     block takes 1/blocks_per_sm of the SM's shared memory.
  *   items_per_claim: 1..32 plan records a block takes from the shared
- *     counter per atomic (default 32).
+ *     counter per atomic (default 32). A plan with records that take their
+ *     prefix by look-back (its count[1] > 0) is claimed one record at a
+ *     time whatever this says: a record queued in one block would hold back
+ *     the later tiles of its list in the others.
  *   stage_bytes: bytes of the block's staging ring (the staging depth:
  *     how much compressed data is in flight per block); 0 = all the
  *     shared memory the block's share leaves. A shape whose ring would be
@@ -278,6 +282,34 @@ gc_status gc_decode_paper(const gc_codec* codec, const uint8_t* d_buf, uint64_t 
                           uint64_t n, uint32_t* d_out, int restore_docids, void* d_scratch,
                           uint64_t scratch_bytes, uint32_t* d_status, void* stream);
 
+/* Bytes of the paper's single buffer (Sec 4.3 step 1) for a control area of
+ * ctrl_bytes and a data area of data_words: the data area starts at the
+ * first 16-byte boundary after the 4-byte head and the control area. */
+uint64_t gc_paper_bytes(uint64_t ctrl_bytes, uint64_t data_words);
+
+/* Build the paper's single buffer (Sec 4.3 step 1) from a list's control
+ * and data areas (as gc_encode wrote them), all on the device: d_buf (16-byte
+ * aligned, buf_bytes >= gc_paper_bytes) receives the data offset in words,
+ * the control bytes, zeros to the 16-byte boundary, and the data words.
+ * Asynchronous on `stream` (one small kernel and two device copies).
+ * GC_ERR_NOSPACE when the buffer is too small, GC_ERR_INVALID for a missing
+ * or misaligned pointer. */
+gc_status gc_pack_paper(const uint8_t* d_ctrl, uint64_t ctrl_bytes, const uint32_t* d_data, uint64_t data_words,
+                        uint8_t* d_buf, uint64_t buf_bytes, void* stream);
+
+/* Split the paper's single buffer (d_buf, buf_bytes, 16-byte aligned) back
+ * into a control area and a data area. The head is copied to the host, so
+ * the call synchronises `stream` once. *ctrl_bytes receives the control
+ * area's length as the buffer gives it (up to its 16-byte boundary: the
+ * padding zeros are included, which decode as they did inside the buffer)
+ * and *data_words the words after it; both are set before the capacity
+ * check, so a call that returns GC_ERR_NOSPACE tells the sizes it needs. A
+ * head that points outside the buffer or off a 16-byte boundary returns
+ * GC_ERR_CORRUPT. The copies are asynchronous on `stream`. */
+gc_status gc_unpack_paper(const uint8_t* d_buf, uint64_t buf_bytes, uint8_t* d_ctrl, uint64_t ctrl_cap,
+                          uint32_t* d_data, uint64_t data_cap, uint64_t* ctrl_bytes, uint64_t* data_words,
+                          void* stream);
+
 /* The work plan of a batch: one gc_work per tile of every list, a list's
  * tiles in order at consecutive records, built on the device from the
  * descriptors, the tile pool and the control pool (read only where a
@@ -316,14 +348,16 @@ gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes);
 
 /* Decode every tile of a plan in one persistent launch (Sec 4.3, 5.2.3,
  * 6.2 decoding per tile; docIDs by Sec 2.1.1 when restore_docids != 0).
- * Each warp claims tiles from a shared counter in plan order, copies their
- * control and data bytes into a shared-memory ring with bulk asynchronous
- * copies several tiles ahead, and decodes up to 32 rows of 32 ints at a
- * time (several small tiles together). A tile with a base starts from it;
- * one without takes its prefix from the tiles before it by a bounded
- * decoupled look-back. The pools are those the plan's records point into
- * (16-byte aligned); every read is bounds-checked against these sizes, and
- * a record whose tile does not fit out_pool_len reports GC_ERR_INVALID.
+ * Each block's staging warp claims tiles from a shared counter in plan
+ * order and groups them into packs of up to 32 lines of 32 ints (several
+ * small tiles together); its decoding warps copy each pack's control and
+ * data bytes into a shared-memory ring one pack ahead and decode it. A tile
+ * with a base starts from it; one without takes its prefix from the tiles
+ * before it by a bounded decoupled look-back. The pools are those the
+ * plan's records point into (16-byte aligned); every read is bounds-checked
+ * against these sizes, and a record whose tile does not fit out_pool_len
+ * reports GC_ERR_INVALID. launch = NULL takes the shape registered with
+ * gc_set_launch for this codec, else the library default (gc_launch).
  * Asynchronous on `stream`; graph-capturable (memsets and one kernel). */
 gc_status gc_decode_plan(const gc_codec* codec, const gc_work* d_work, const uint64_t* d_count,
                          uint64_t work_cap, const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
@@ -344,6 +378,8 @@ gc_status gc_decode_batch_scratch_size(uint64_t nlists, uint64_t max_tiles, uint
  *   d_out_pool / out_pool_len: outputs; list i goes to out_off.
  *   max_tiles: the scratch was sized for this many tiles; a batch with more
  *     reports GC_ERR_NOSPACE in d_status.
+ *   launch: as for gc_decode_plan (NULL = the registered shape, else the
+ *     library default).
  * The call is graph-capturable (no host synchronisation). */
 gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists,
                           const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
@@ -468,6 +504,55 @@ gc_status gc_intersect(const gc_codec* codec, const gc_list* d_lists, uint64_t n
                        const uint32_t* d_b, const uint64_t* d_a_offs, const uint64_t* d_b_tile_offs, uint64_t nqueries,
                        uint64_t a_ints, uint64_t a_tiles, uint64_t b_tiles, uint32_t* d_out, uint32_t* d_counts,
                        void* d_scratch, uint64_t scratch_bytes, uint32_t* d_status, void* stream);
+
+/* ------------------------------------------- launch shapes and host buffers */
+
+/* Register the launch shape that decode calls given launch = NULL use for
+ * this codec kind and k, with or without docIDs, on the current device (the
+ * autotuner does this after timing its candidates on an index); launch =
+ * NULL clears it. Without one, NULL means the library default. A shape out
+ * of range returns GC_ERR_INVALID. Not a step of the paper's method: a
+ * service of the library. */
+gc_status gc_set_launch(const gc_codec* codec, int restore_docids, const gc_launch* launch);
+
+/* The shape a decode call with launch = NULL uses now on the current
+ * device (registered, or the library default), every field filled in
+ * (stage_bytes 0 = all the shared memory the block's share leaves). */
+gc_status gc_get_launch(const gc_codec* codec, int restore_docids, gc_launch* launch);
+
+/* Device bytes gc_decode_plan_host needs for a plan of nwork records over
+ * pools of these sizes and an output pool of out_pool_len ints. */
+gc_status gc_decode_plan_host_buffer_size(uint64_t nwork, uint64_t ctrl_pool_bytes, uint64_t data_pool_words,
+                                          uint64_t out_pool_len, uint64_t* bytes);
+
+/* gc_decode_plan for a caller whose plan, pools and output are in host
+ * memory (the decode of Sec 4.3, 5.2.3, 6.2 and the prefix sum of Sec 2.1.1,
+ * as gc_decode_plan). On `stream`: the nwork records of h_work (a plan
+ * gc_plan_batch or gc_plan_select made, copied to the host) and both pools
+ * are copied into d_buffers, the plan's counts are rebuilt there, the
+ * output area is zeroed and decoded, and all out_pool_len ints of it are
+ * copied back to h_out_pool (ints no record writes come back as 0).
+ *   d_buffers / buffer_bytes: device memory, 256-byte aligned, at least
+ *     gc_decode_plan_host_buffer_size bytes, owned by the caller; the call
+ *     only uses it while the stream runs the call's work.
+ *   launch: as for gc_decode_plan.
+ *   d_status: device pointer, as for every decode call.
+ * Asynchronous: the host buffers must stay alive and unchanged until the
+ * stream reaches the end of the call's work, and copies overlap other work
+ * only when the host buffers are page-locked (cudaHostAlloc). Errors as for
+ * gc_decode_plan; GC_ERR_NOSPACE when buffer_bytes is too small. */
+gc_status gc_decode_plan_host(const gc_codec* codec, const gc_work* h_work, uint64_t nwork, const uint8_t* h_ctrl_pool,
+                              uint64_t ctrl_pool_bytes, const uint32_t* h_data_pool, uint64_t data_pool_words,
+                              uint32_t* h_out_pool, uint64_t out_pool_len, int restore_docids, const gc_launch* launch,
+                              void* d_buffers, uint64_t buffer_bytes, uint32_t* d_status, void* stream);
+
+/* Drop the library's host-side state: the registered launch shapes and the
+ * device facts and kernel attributes it looked up (call it after
+ * cudaDeviceReset, before the next gc_* call). Safe whenever no other gc_*
+ * call is running; later calls look up again what they need. The fixed
+ * scratch of gc_decode_static is device memory of the library's code: it is
+ * not released. */
+void gc_shutdown(void);
 
 /* Number of kernels the last gc_* call on this host thread launched (for
  * launch accounting). */

@@ -44,6 +44,10 @@ int sm_count() {
   return g_sms[dev];
 }
 
+void forget_devices() {
+  for (int& v : g_sms) v = 0;
+}
+
 void reset_launches() { t_launches = 0; }
 void count_launch(uint32_t n) { t_launches += n; }
 uint32_t launches() { return t_launches; }

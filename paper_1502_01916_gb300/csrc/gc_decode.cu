@@ -5,16 +5,18 @@
 // byte ranges of the tile's control and data streams. The persistent kernel
 // gives each block one staging warp and several decoding warps that share a
 // shared-memory ring:
-//   - the staging warp claims 32 records at a time from a shared counter
-//     (one bulk copy brings them into shared memory), sizes every tile's
-//     staging in parallel (one lane per record), groups the records into
-//     packs of up to 32 lines of 32 consecutive ints (one whole tile, or
-//     several small tiles together), places each pack in the ring and
-//     issues its bulk asynchronous copies (cp.async.bulk, one mbarrier per
-//     pack). At k = 32 every 128-byte data vector lands at a 144-byte pitch,
-//     so that the lanes of a warp reading 32 different rows hit different
-//     banks;
-//   - decoding warp w takes packs w, w + W, w + 2W, ...: the control
+//   - the staging warp claims up to 32 records at a time from a shared
+//     counter (one bulk copy brings them into shared memory, the next
+//     claim's copy in flight while the current one is placed), sizes every
+//     tile's staging in parallel (one lane per record), groups the records
+//     into packs of up to 32 lines of 32 consecutive ints (one whole tile,
+//     or several small tiles together), places each pack in the ring and
+//     hands it to its decoding warp through the pack slot's mbarrier;
+//   - decoding warp w takes packs w, w + W, w + 2W, ...; it copies the next
+//     pack's bytes into the ring (16-byte cp.async per lane, one commit
+//     group per pack) while it decodes the current one. At k = 32 every
+//     128-byte data vector lands at a 144-byte pitch, so that the lanes of a
+//     warp reading 32 different rows hit different banks. The control
 //     patterns become one (word, shift, width) entry per row -- Table III
 //     selectors (Sec 4.3), Eq. 2 length descriptors (Sec 5.2.3, 5.3.1),
 //     AFOR frame bytes (Sec 6.1), PFD frame headers (Sec 6.2 decoding
@@ -585,12 +587,14 @@ __device__ __noinline__ uint32_t look_back(const unsigned long long* lb, uint64_
       s = ld_acquire(lb + item - dist);
       if ((s >> 32) == 0) {
         const uint64_t t0 = now_ns();
+        uint32_t nap = 32;  // ns, doubling up to 1 us
         while ((s >> 32) == 0) {
           if (now_ns() - t0 > kWaitNs) {
             timed_out = true;
             break;
           }
-          __nanosleep(32);
+          __nanosleep(nap);
+          nap = nap < 1024u ? 2 * nap : 1024u;
           s = ld_acquire(lb + item - dist);
         }
       }
@@ -711,7 +715,18 @@ __device__ __noinline__ uint32_t line_bases_chain(const DecodeArgs& a, WarpSmem<
     if (dead) st_release(a.lb + item, kFlagPrefix);  // its error is reported
     if (needs_lb) st_release(a.lb + item, kFlagAgg | tot);
   }
-  for (uint32_t pend = __ballot_sync(kFull, needs_lb); pend; pend &= pend - 1) {
+  // every item whose tile just before has its inclusive prefix already
+  // takes it at once (one lane each); the others walk back together
+  bool walk = needs_lb;
+  if (needs_lb && a.lb) {
+    const unsigned long long sp = ld_acquire(a.lb + item - 1);
+    if ((sp & ~0xffffffffull) == kFlagPrefix) {
+      base = (uint32_t)sp;
+      st_release(a.lb + item, kFlagPrefix | (uint32_t)(base + tot));
+      walk = false;
+    }
+  }
+  for (uint32_t pend = __ballot_sync(kFull, walk); pend; pend &= pend - 1) {
     const uint32_t p = __ffs(pend) - 1;
     const uint32_t it = __shfl_sync(kFull, item, p);
     const uint32_t tl = __shfl_sync(kFull, tile, p);
@@ -1482,7 +1497,12 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
   const uint32_t lane = lane_id();
   uint64_t total = a.count[0];
   if (total > a.work_cap) total = a.work_cap;
-  const uint32_t claim = a.claim < 1u ? 1u : a.claim > (uint32_t)kChunk ? (uint32_t)kChunk : a.claim;
+  // With tiles that take their prefix by look-back, records are claimed one
+  // at a time and only once the ones before are placed: a claimed record
+  // that waits in a block's queue holds back every later tile of its list,
+  // in other blocks, until a decoding warp publishes its aggregate.
+  const bool ahead = a.count[1] == 0;
+  const uint32_t claim = !ahead ? 1u : a.claim < 1u ? 1u : a.claim > (uint32_t)kChunk ? (uint32_t)kChunk : a.claim;
   Ring r = {a.ring_bytes, 0, 0, 0, 0, 0, 0, 0};
   bool failed = false;
   uint32_t busy = 0;  // lane b < kNChunk: record buffer b is free once this many packs are given back
@@ -1492,11 +1512,15 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
     const uint32_t b = c % kNChunk;
     // the next claim goes to the next buffer once that buffer's packs are given back
     const uint32_t nb = (c + 1) % kNChunk;
-    const uint32_t nbusy = __shfl_sync(kFull, busy, nb);
-    while (!failed && r.tail < nbusy) failed = !ring_drain(h, r, S);
-    if (failed) break;
-    const uint2 cn = claim_records(a, h, nb, claim, total);
-    const uint32_t nx = cn.x, ncnt = cn.y;
+    uint32_t nx = 0, ncnt = 0;
+    if (ahead) {
+      const uint32_t nbusy = __shfl_sync(kFull, busy, nb);
+      while (!failed && r.tail < nbusy) failed = !ring_drain(h, r, S);
+      if (failed) break;
+      const uint2 cn = claim_records(a, h, nb, claim, total);
+      nx = cn.x;
+      ncnt = cn.y;
+    }
     if (!wait_warp(&h.recbar[b], (c / kNChunk) & 1u)) {
       failed = true;
       break;
@@ -1565,6 +1589,14 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
       if (++r.ps == S) r.ps = 0;
     }
     if (lane == b) busy = r.issued;
+    if (!ahead && !failed) {
+      const uint32_t nbusy = __shfl_sync(kFull, busy, nb);
+      while (!failed && r.tail < nbusy) failed = !ring_drain(h, r, S);
+      if (failed) break;
+      const uint2 cn = claim_records(a, h, nb, claim, total);
+      nx = cn.x;
+      ncnt = cn.y;
+    }
     x = nx;
     cnt = ncnt;
   }
@@ -1764,8 +1796,10 @@ __device__ __forceinline__ gc_list plan_list(const PlanArgs& a, uint64_t i) {
 }
 
 // Pass 1: one thread per list reserves a contiguous range of records for the
-// list's tiles (one atomic per warp) and writes (list, tile) into each. A
-// list's tiles are consecutive records.
+// list's tiles (one atomic per warp); then the warp writes (list, tile) into
+// the records of its lists, one list after another, 32 records per step. A
+// list's tiles are consecutive records. (A single list needs no writes: pass
+// 2 knows record i is its tile i.)
 __global__ void k_plan_reserve(PlanArgs a) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = lane_id();
@@ -1780,13 +1814,20 @@ __global__ void k_plan_reserve(PlanArgs a) {
   unsigned long long b = 0;
   if (lane == 31) b = atomicAdd(a.count, (unsigned long long)incl);
   const uint64_t base = __shfl_sync(kFull, b, 31) + incl - nt;
-  if (i >= a.nlists) return;
   const bool fits = base + nt <= a.cap;
-  if (!fits) report(a.status, GC_ERR_NOSPACE, (uint32_t)i);
-  for (uint64_t t = 0; t < nt && base + t < a.cap; ++t) {
-    gc_work* w = a.work + base + t;
-    w->tile = (uint32_t)t;
-    w->list = fits ? (uint32_t)i : 0xffffffffu;
+  if (i < a.nlists && !fits) report(a.status, GC_ERR_NOSPACE, (uint32_t)i);
+  if (!a.lists) return;
+  for (uint32_t m = __ballot_sync(kFull, i < a.nlists && nt > 0); m; m &= m - 1) {
+    const uint32_t src = __ffs(m) - 1;
+    const uint64_t lb0 = __shfl_sync(kFull, base, src);
+    const uint64_t ln = __shfl_sync(kFull, nt, src);
+    const uint32_t lid = __shfl_sync(kFull, (uint32_t)i, src);
+    const bool lf = __shfl_sync(kFull, fits, src);
+    for (uint64_t t = lane; t < ln && lb0 + t < a.cap; t += 32) {
+      gc_work* w = a.work + lb0 + t;
+      w->tile = (uint32_t)t;
+      w->list = lf ? lid : 0xffffffffu;
+    }
   }
 }
 
@@ -1813,8 +1854,14 @@ __global__ void k_plan_fill(PlanArgs a) {
   uint64_t total = a.count[0];
   if (total > a.cap) total = a.cap;
   if (i >= total) return;
-  gc_work w = a.work[i];
   const gc_work empty = {0, 0, 0, 0, 0, 0, 0xffffffffu, 0, 0, 0, 0, 0, 0};
+  gc_work w = empty;
+  if (a.lists) {
+    w = a.work[i];
+  } else if (a.count[0] <= a.cap) {  // (a single list that does not fit is not planned)
+    w.tile = (uint32_t)i;
+    w.list = 0;
+  }
   if (w.list == 0xffffffffu || w.list >= a.nlists) {
     a.work[i] = empty;
     return;
@@ -1933,6 +1980,20 @@ __global__ void k_plan_fill(PlanArgs a) {
   a.work[i] = w;
 }
 
+// The counts of a plan copied in from the host: [0] its records, [1] the
+// records that take their prefix by look-back (count zeroed before).
+__global__ void k_count_records(const gc_work* work, uint64_t nwork, unsigned long long* count) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) count[0] = nwork;
+  bool lb = false;
+  if (i < nwork) {
+    const gc_work& w = work[i];
+    lb = w.list != 0xffffffffu && w.tile > 0 && !(w.shape & GC_WORK_HAS_BASE);
+  }
+  const uint32_t m = __ballot_sync(kFull, lb);
+  if (m && lane_id() == (uint32_t)(__ffs(m) - 1)) atomicAdd(count + 1, (unsigned long long)__popc(m));
+}
+
 }  // namespace gcdev
 
 // ====================================================================== host
@@ -1964,6 +2025,15 @@ struct DevInfo {
 
 std::mutex g_launch_mu;
 DevInfo g_dev[64];
+uint32_t g_epoch = 1;  // advanced by gc_shutdown: per-kernel facts are looked up again
+
+// Launch shapes registered with gc_set_launch: per device, codec kind, k
+// (0: 4, 1: 32) and restore flag.
+struct Registered {
+  bool set = false;
+  Shape sh = {};
+};
+Registered g_reg[64][4][2][2];
 
 template <int KIND, int K, bool RESTORE>
 gc_status launch_t(DecodeArgs a, Shape sh, uint64_t work, cudaStream_t s) {
@@ -1973,10 +2043,16 @@ gc_status launch_t(DecodeArgs a, Shape sh, uint64_t work, cudaStream_t s) {
   static size_t smem_set[64] = {};
   static uint32_t occ_key[64][2] = {};
   static int occ_val[64] = {};
+  static uint32_t seen[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GC_ERR_CUDA;
   if (dev < 0 || dev >= 64) return GC_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_launch_mu);
+  if (seen[dev] != g_epoch) {
+    smem_set[dev] = 0;
+    occ_val[dev] = 0;
+    seen[dev] = g_epoch;
+  }
   DevInfo& di = g_dev[dev];
   if (di.optin == 0) {
     if (cudaDeviceGetAttribute(&di.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
@@ -2039,19 +2115,33 @@ gc_status launch_decode(uint32_t kind, uint32_t k, bool restore, const DecodeArg
   return restore ? launch_r<true>(kind, k, a, sh, work, s) : launch_r<false>(kind, k, a, sh, work, s);
 }
 
-// Launch shape from the caller's request (NULL = the library default for
-// this k, every field 0 = its default); GC_ERR_INVALID for a shape out of
-// range.
-gc_status launch_shape(const gc_codec& c, const gc_launch* l, Shape* sh) {
+// A caller's shape over the library default for this k (every field 0 =
+// its default); GC_ERR_INVALID for a shape out of range.
+gc_status fill_shape(const gc_codec& c, const gc_launch& l, Shape* sh) {
   *sh = default_shape(c.k);
-  if (!l) return GC_OK;
   const uint32_t max_warps = (c.k == 32 ? Geo<32>::THREADS : Geo<4>::THREADS) / 32 - 1;
-  if (l->warps_per_block > max_warps || l->items_per_claim > kMaxClaim || l->blocks_per_sm > 8)
-    return GC_ERR_INVALID;
-  if (l->warps_per_block) sh->warps = l->warps_per_block;
-  if (l->blocks_per_sm) sh->bps = l->blocks_per_sm;
-  if (l->items_per_claim) sh->claim = l->items_per_claim;
-  sh->stage = l->stage_bytes;
+  if (l.warps_per_block > max_warps || l.items_per_claim > kMaxClaim || l.blocks_per_sm > 8) return GC_ERR_INVALID;
+  if (l.warps_per_block) sh->warps = l.warps_per_block;
+  if (l.blocks_per_sm) sh->bps = l.blocks_per_sm;
+  if (l.items_per_claim) sh->claim = l.items_per_claim;
+  sh->stage = l.stage_bytes;
+  return GC_OK;
+}
+
+Registered* registered(const gc_codec& c, int restore) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  return &g_reg[dev][c.kind & 3u][c.k == 32 ? 1 : 0][restore ? 1 : 0];
+}
+
+// Launch shape from the caller's request: NULL = the shape registered for
+// this codec (gc_set_launch), else the library default for this k.
+gc_status launch_shape(const gc_codec& c, const gc_launch* l, Shape* sh, int restore) {
+  if (l) return fill_shape(c, *l, sh);
+  *sh = default_shape(c.k);
+  std::lock_guard<std::mutex> lock(g_launch_mu);
+  const Registered* r = registered(c, restore);
+  if (r && r->set) *sh = r->sh;
   return GC_OK;
 }
 
@@ -2332,7 +2422,7 @@ gc_status gc_decode_plan(const gc_codec* codec, const gc_work* d_work, const uin
   gc_decode_plan_scratch_size(work_cap, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
   Shape sh;
-  st = launch_shape(*codec, launch, &sh);
+  st = launch_shape(*codec, launch, &sh, restore_docids);
   if (st != GC_OK) return st;
   return decode_plan_impl(*codec, d_work, d_count, work_cap, d_ctrl_pool, ctrl_pool_bytes, d_data_pool,
                           data_pool_words, d_out_pool, out_pool_len, restore_docids, sh, (unsigned char*)d_scratch,
@@ -2367,7 +2457,7 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
   gc_decode_batch_scratch_size(nlists, max_tiles, &need);
   if (scratch_bytes < need) return GC_ERR_NOSPACE;
   Shape sh;
-  st = launch_shape(*codec, launch, &sh);
+  st = launch_shape(*codec, launch, &sh, restore_docids);
   if (st != GC_OK) return st;
   unsigned char* base = (unsigned char*)d_scratch;
   uint64_t* count = reinterpret_cast<uint64_t*>(base + 64);
@@ -2383,6 +2473,127 @@ gc_status gc_decode_batch(const gc_codec* codec, const gc_list* d_lists, uint64_
                         d_out_pool, out_pool_len, restore_docids, sh, rest, d_status, s);
   gc_host::count_launch(planned);
   return st;
+}
+
+// ------------------------------------------------ launch shapes, host buffers
+
+gc_status gc_set_launch(const gc_codec* codec, int restore_docids, const gc_launch* launch) {
+  gc_status st = gc_host::check_codec(codec);
+  if (st != GC_OK) return st;
+  Shape sh = default_shape(codec->k);
+  if (launch) {
+    st = fill_shape(*codec, *launch, &sh);
+    if (st != GC_OK) return st;
+  }
+  std::lock_guard<std::mutex> lock(g_launch_mu);
+  Registered* r = registered(*codec, restore_docids);
+  if (!r) return GC_ERR_CUDA;
+  r->set = launch != nullptr;
+  r->sh = sh;
+  return GC_OK;
+}
+
+gc_status gc_get_launch(const gc_codec* codec, int restore_docids, gc_launch* launch) {
+  gc_status st = gc_host::check_codec(codec);
+  if (st != GC_OK) return st;
+  if (!launch) return GC_ERR_INVALID;
+  Shape sh;
+  st = launch_shape(*codec, nullptr, &sh, restore_docids);
+  if (st != GC_OK) return st;
+  launch->warps_per_block = sh.warps;
+  launch->blocks_per_sm = sh.bps;
+  launch->items_per_claim = sh.claim;
+  launch->stage_bytes = sh.stage;
+  return GC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Where gc_decode_plan_host puts things in the caller's device buffer.
+struct HostLayout {
+  uint64_t scratch, count, work, ctrl, data, out, total;
+};
+
+HostLayout host_layout(uint64_t nwork, uint64_t ctrl_pool_bytes, uint64_t data_pool_words, uint64_t out_pool_len) {
+  HostLayout L;
+  uint64_t dec = 0;
+  gc_decode_plan_scratch_size(nwork, &dec);
+  L.scratch = 0;
+  L.count = gc_host::align_up(dec, 256);
+  L.work = L.count + 256;
+  L.ctrl = L.work + gc_host::align_up(nwork * sizeof(gc_work), 256);
+  L.data = L.ctrl + gc_host::align_up(ctrl_pool_bytes, 256);
+  L.out = L.data + gc_host::align_up(data_pool_words * 4, 256);
+  L.total = L.out + gc_host::align_up(out_pool_len * 4, 256);
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+gc_status gc_decode_plan_host_buffer_size(uint64_t nwork, uint64_t ctrl_pool_bytes, uint64_t data_pool_words,
+                                          uint64_t out_pool_len, uint64_t* bytes) {
+  if (!bytes) return GC_ERR_INVALID;
+  *bytes = host_layout(nwork, ctrl_pool_bytes, data_pool_words, out_pool_len).total;
+  return GC_OK;
+}
+
+gc_status gc_decode_plan_host(const gc_codec* codec, const gc_work* h_work, uint64_t nwork, const uint8_t* h_ctrl_pool,
+                              uint64_t ctrl_pool_bytes, const uint32_t* h_data_pool, uint64_t data_pool_words,
+                              uint32_t* h_out_pool, uint64_t out_pool_len, int restore_docids, const gc_launch* launch,
+                              void* d_buffers, uint64_t buffer_bytes, uint32_t* d_status, void* stream) {
+  gc_host::reset_launches();
+  gc_status st = gc_host::check_codec(codec);
+  if (st != GC_OK) return st;
+  if (nwork == 0) return GC_OK;
+  if (!h_work || (!h_ctrl_pool && ctrl_pool_bytes) || (!h_data_pool && data_pool_words) ||
+      (!h_out_pool && out_pool_len) || !d_buffers)
+    return GC_ERR_INVALID;
+  if (((uintptr_t)d_buffers & 255) != 0) return GC_ERR_INVALID;
+  if (nwork > kMaxWork) return GC_ERR_UNSUPPORTED;
+  const HostLayout L = host_layout(nwork, ctrl_pool_bytes, data_pool_words, out_pool_len);
+  if (buffer_bytes < L.total) return GC_ERR_NOSPACE;
+  Shape sh;
+  st = launch_shape(*codec, launch, &sh, restore_docids);
+  if (st != GC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* b = (unsigned char*)d_buffers;
+  gc_work* work = reinterpret_cast<gc_work*>(b + L.work);
+  uint64_t* count = reinterpret_cast<uint64_t*>(b + L.count);
+  uint8_t* ctrl = b + L.ctrl;
+  uint32_t* data = reinterpret_cast<uint32_t*>(b + L.data);
+  uint32_t* out = reinterpret_cast<uint32_t*>(b + L.out);
+  if (cudaMemcpyAsync(work, h_work, nwork * sizeof(gc_work), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      (ctrl_pool_bytes && cudaMemcpyAsync(ctrl, h_ctrl_pool, ctrl_pool_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+      (data_pool_words &&
+       cudaMemcpyAsync(data, h_data_pool, data_pool_words * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+      cudaMemsetAsync(count, 0, 16, s) != cudaSuccess ||
+      (out_pool_len && cudaMemsetAsync(out, 0, out_pool_len * 4, s) != cudaSuccess))
+    return GC_ERR_CUDA;
+  k_count_records<<<(unsigned)((nwork + 255) / 256), 256, 0, s>>>(work, nwork,
+                                                                  reinterpret_cast<unsigned long long*>(count));
+  if (cudaGetLastError() != cudaSuccess) return GC_ERR_CUDA;
+  st = decode_plan_impl(*codec, work, count, nwork, ctrl, ctrl_pool_bytes, data, data_pool_words, out, out_pool_len,
+                        restore_docids, sh, b + L.scratch, d_status, s);
+  gc_host::count_launch(1);
+  if (st != GC_OK) return st;
+  if (out_pool_len && cudaMemcpyAsync(h_out_pool, out, out_pool_len * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return GC_ERR_CUDA;
+  return GC_OK;
+}
+
+void gc_shutdown(void) {
+  std::lock_guard<std::mutex> lock(g_launch_mu);
+  for (auto& d : g_reg)
+    for (auto& kd : d)
+      for (auto& kk : kd)
+        for (auto& r : kk) r = Registered{};
+  for (auto& d : g_dev) d = DevInfo{};
+  ++g_epoch;
+  gc_host::forget_devices();
 }
 
 // ------------------------------------------------- decoding without scratch

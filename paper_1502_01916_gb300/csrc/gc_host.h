@@ -17,6 +17,8 @@ gc_status check_codec(const gc_codec* c);
 
 // Multiprocessors of the current device (cached per device).
 int sm_count();
+// Forget the device facts looked up so far (gc_shutdown).
+void forget_devices();
 
 // Kernel launches made by the current gc_* call on this thread.
 void reset_launches();

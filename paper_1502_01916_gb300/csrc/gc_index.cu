@@ -205,6 +205,16 @@ __global__ void __launch_bounds__(kIndexThreads) k_index_emit(IndexArgs a) {
   if (c < a.nchunks) walk_chunk(a, c, true, agg_add(a.block_sums[blockIdx.x], ex));
 }
 
+// The head of the paper's single buffer (Sec 4.3 step 1): the data area's
+// offset in 4-byte words, then, after the control area, zeros up to the
+// data area's 16-byte boundary. One thread per byte of the padding.
+__global__ void k_paper_head(uint8_t* buf, uint64_t ctrl_bytes, uint32_t off_words) {
+  const uint32_t i = threadIdx.x;
+  if (i == 0) *reinterpret_cast<uint32_t*>(buf) = off_words;
+  const uint64_t pad0 = 4 + ctrl_bytes, pad1 = 4ull * off_words;
+  if (pad0 + i < pad1) buf[pad0 + i] = 0;
+}
+
 }  // namespace gcidx
 
 namespace gc_host {
@@ -284,6 +294,52 @@ gc_status gc_build_tiles(const gc_codec* codec, const uint8_t* d_ctrl, uint64_t 
   if ((!d_ctrl && ctrl_bytes) || !d_tiles || !d_scratch) return GC_ERR_INVALID;
   if (scratch_bytes < gc_host::index_sums_bytes(*codec, n)) return GC_ERR_NOSPACE;
   return gc_host::build_tiles(*codec, d_ctrl, ctrl_bytes, n, d_tiles, d_scratch, d_status, (cudaStream_t)stream);
+}
+
+uint64_t gc_paper_bytes(uint64_t ctrl_bytes, uint64_t data_words) {
+  return gc_host::align_up(4 + ctrl_bytes, 16) + 4 * data_words;
+}
+
+gc_status gc_pack_paper(const uint8_t* d_ctrl, uint64_t ctrl_bytes, const uint32_t* d_data, uint64_t data_words,
+                        uint8_t* d_buf, uint64_t buf_bytes, void* stream) {
+  gc_host::reset_launches();
+  if ((!d_ctrl && ctrl_bytes) || (!d_data && data_words) || !d_buf) return GC_ERR_INVALID;
+  if (((uintptr_t)d_buf & 15) != 0) return GC_ERR_INVALID;
+  const uint64_t doff = gc_host::align_up(4 + ctrl_bytes, 16);
+  if (doff / 4 > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  if (buf_bytes < gc_paper_bytes(ctrl_bytes, data_words)) return GC_ERR_NOSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  gcidx::k_paper_head<<<1, 16, 0, s>>>(d_buf, ctrl_bytes, (uint32_t)(doff / 4));
+  gc_host::count_launch();
+  if (cudaGetLastError() != cudaSuccess) return GC_ERR_CUDA;
+  if (ctrl_bytes && cudaMemcpyAsync(d_buf + 4, d_ctrl, ctrl_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return GC_ERR_CUDA;
+  if (data_words && cudaMemcpyAsync(d_buf + doff, d_data, 4 * data_words, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return GC_ERR_CUDA;
+  return GC_OK;
+}
+
+gc_status gc_unpack_paper(const uint8_t* d_buf, uint64_t buf_bytes, uint8_t* d_ctrl, uint64_t ctrl_cap,
+                          uint32_t* d_data, uint64_t data_cap, uint64_t* ctrl_bytes, uint64_t* data_words,
+                          void* stream) {
+  gc_host::reset_launches();
+  if (!d_buf || buf_bytes < 4 || !ctrl_bytes || !data_words) return GC_ERR_INVALID;
+  if (((uintptr_t)d_buf & 15) != 0) return GC_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t off_words = 0;
+  if (cudaMemcpyAsync(&off_words, d_buf, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GC_ERR_CUDA;
+  const uint64_t doff = 4ull * off_words;
+  if (doff < 4 || doff > buf_bytes || (doff & 15)) return GC_ERR_CORRUPT;
+  const uint64_t cb = doff - 4, dw = (buf_bytes - doff) / 4;
+  *ctrl_bytes = cb;
+  *data_words = dw;
+  if (cb > ctrl_cap || dw > data_cap) return GC_ERR_NOSPACE;
+  if ((!d_ctrl && cb) || (!d_data && dw)) return GC_ERR_INVALID;
+  if (cb && cudaMemcpyAsync(d_ctrl, d_buf + 4, cb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GC_ERR_CUDA;
+  if (dw && cudaMemcpyAsync(d_data, d_buf + doff, 4 * dw, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return GC_ERR_CUDA;
+  return GC_OK;
 }
 
 }  // extern "C"

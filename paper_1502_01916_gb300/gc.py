@@ -36,7 +36,8 @@ __all__ = [
     "DECODE_STATIC_MAX_INTS",
     "gc_last_launch_count", "gc_version", "EncodedList", "Index", "encode", "decode",
     "build_tiles", "decode_paper", "encode_index", "decode_index", "new_status", "check_status",
-    "as_u32", "codec_name",
+    "as_u32", "codec_name", "gc_paper_bytes", "gc_pack_paper", "gc_unpack_paper", "pack_paper", "unpack_paper",
+    "gc_set_launch", "gc_get_launch", "gc_decode_plan_host_buffer_size", "gc_decode_plan_host", "gc_shutdown",
 ]
 
 SIMPLE, SCHEME, AFOR, PFD = 0, 1, 2, 3
@@ -155,6 +156,15 @@ def load():
             "gc_intersect_scratch_size": (_I, [_U64, _U64, _U64, _U64P]),
             "gc_intersect": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V, _V, _U64, _U64, _U64,
                                   _U64, _V, _V, _V, _U64, _V, _V]),
+            "gc_paper_bytes": (_U64, [_U64, _U64]),
+            "gc_pack_paper": (_I, [_V, _U64, _V, _U64, _V, _U64, _V]),
+            "gc_unpack_paper": (_I, [_V, _U64, _V, _U64, _V, _U64, _U64P, _U64P, _V]),
+            "gc_set_launch": (_I, [_CP, _I, ctypes.POINTER(gc_launch)]),
+            "gc_get_launch": (_I, [_CP, _I, ctypes.POINTER(gc_launch)]),
+            "gc_decode_plan_host_buffer_size": (_I, [_U64, _U64, _U64, _U64, _U64P]),
+            "gc_decode_plan_host": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I,
+                                         ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
+            "gc_shutdown": (None, []),
             "gc_last_launch_count": (_U32, []),
             "gc_version": (ctypes.c_char_p, []),
         }
@@ -347,6 +357,77 @@ def gc_decode_plan(codec, d_work, d_count, d_ctrl_pool, d_data_pool, d_out_pool,
            "gc_decode_plan")
 
 
+def gc_paper_bytes(ctrl_bytes: int, data_words: int) -> int:
+    return int(load().gc_paper_bytes(ctrl_bytes, data_words))
+
+
+def gc_pack_paper(d_ctrl, ctrl_bytes, d_data, data_words, d_buf, stream=None):
+    _check(load().gc_pack_paper(_ptr(d_ctrl), ctrl_bytes, _ptr(d_data), data_words, _ptr(d_buf),
+                                _n(d_buf, 1, "d_buf"), _stream(stream)), "gc_pack_paper")
+
+
+def gc_unpack_paper(d_buf, d_ctrl, d_data, stream=None):
+    """Returns (ctrl_bytes, data_words) of the buffer's areas."""
+    cb, dw = _U64(), _U64()
+    st = load().gc_unpack_paper(_ptr(d_buf), _n(d_buf, 1, "d_buf"), _ptr(d_ctrl),
+                                _n(d_ctrl, 1, "d_ctrl") if d_ctrl is not None else 0, _ptr(d_data),
+                                _n(d_data, 4, "d_data") if d_data is not None else 0, ctypes.byref(cb),
+                                ctypes.byref(dw), _stream(stream))
+    _check(st, "gc_unpack_paper")
+    return cb.value, dw.value
+
+
+def gc_set_launch(codec, restore_docids, launch):
+    lp = ctypes.byref(launch) if launch is not None else None
+    _check(load().gc_set_launch(ctypes.byref(codec), int(bool(restore_docids)), lp), "gc_set_launch")
+
+
+def gc_get_launch(codec, restore_docids) -> gc_launch:
+    l = gc_launch()
+    _check(load().gc_get_launch(ctypes.byref(codec), int(bool(restore_docids)), ctypes.byref(l)), "gc_get_launch")
+    return l
+
+
+def gc_decode_plan_host_buffer_size(nwork: int, ctrl_pool_bytes: int, data_pool_words: int,
+                                    out_pool_len: int) -> int:
+    b = _U64()
+    _check(load().gc_decode_plan_host_buffer_size(nwork, ctrl_pool_bytes, data_pool_words, out_pool_len,
+                                                  ctypes.byref(b)), "gc_decode_plan_host_buffer_size")
+    return b.value
+
+
+def _h(t, esize: int, what: str):
+    """(pointer, element count) of a host buffer: a contiguous CPU tensor or
+    numpy array of esize-byte elements."""
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"] or t.itemsize != esize:
+            raise ValueError(f"{what}: expected a contiguous array of {esize}-byte elements")
+        return t.ctypes.data, t.size
+    if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous() or t.element_size() != esize:
+        raise ValueError(f"{what}: expected a contiguous host tensor of {esize}-byte elements")
+    return t.data_ptr(), t.numel()
+
+
+def gc_decode_plan_host(codec, h_work, nwork, h_ctrl_pool, h_data_pool, h_out_pool, restore_docids, launch,
+                        d_buffers, d_status, stream=None):
+    """gc_decode_plan with the plan, pools and output in host memory (nwork
+    records of h_work are decoded)."""
+    wp, wb = _h(h_work, 1, "h_work")
+    if nwork * WORK_BYTES > wb:
+        raise ValueError("h_work holds fewer than nwork records")
+    cp, cn = _h(h_ctrl_pool, 1, "h_ctrl_pool")
+    dp, dn = _h(h_data_pool, 4, "h_data_pool")
+    op, on = _h(h_out_pool, 4, "h_out_pool")
+    lp = ctypes.byref(launch) if launch is not None else None
+    _check(load().gc_decode_plan_host(ctypes.byref(codec), wp, nwork, cp, cn, dp, dn, op, on,
+                                      int(bool(restore_docids)), lp, _ptr(d_buffers), _n(d_buffers, 1, "d_buffers"),
+                                      _ptr(d_status), _stream(stream)), "gc_decode_plan_host")
+
+
+def gc_shutdown():
+    load().gc_shutdown()
+
+
 def gc_last_launch_count() -> int:
     return int(load().gc_last_launch_count())
 
@@ -465,6 +546,25 @@ def decode_paper(codec: gc_codec, buf: torch.Tensor, n: int, restore_docids: boo
     gc_decode_paper(codec, buf, n, out, restore_docids, scratch, st, stream)
     check_status(st, "gc_decode_paper")
     return out[:n]
+
+
+def pack_paper(enc: "EncodedList", stream=None) -> torch.Tensor:
+    """The paper's single buffer of an encoded list (gc_pack_paper)."""
+    dev = enc.data.device
+    cb, dw = enc.ctrl_bytes, enc.data_words
+    buf = torch.empty(gc_paper_bytes(cb, dw), dtype=torch.uint8, device=dev)
+    gc_pack_paper(enc.ctrl, cb, enc.data, dw, buf, stream)
+    return buf
+
+
+def unpack_paper(buf: torch.Tensor, stream=None):
+    """(control bytes, data words) tensors of the paper's single buffer
+    (gc_unpack_paper); the control area includes its padding zeros."""
+    dev = buf.device
+    ctrl = torch.empty(max(16, buf.numel()), dtype=torch.uint8, device=dev)
+    data = _data_buffer(max(4, buf.numel() // 4), dev)
+    cb, dw = gc_unpack_paper(buf, ctrl, data, stream)
+    return ctrl[:cb], data[:dw]
 
 
 @dataclasses.dataclass

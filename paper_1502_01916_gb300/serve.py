@@ -8,7 +8,11 @@ resident on the GPU and serves requests of several lists each:
 
 - requests are admitted while the output arena (the device memory that holds
   decoded lists until the caller has read them) has room for their ints and
-  the batch's plan has room for their tiles;
+  the batch's plan has room for their tiles; by default the arena takes half
+  of the device memory free when the server starts, at most 4 GiB (the
+  paper sets no admission rule: this one bounds the server by the memory it
+  may hold, not by a request count). A request that has to wait for arena
+  room is counted as an admission stall;
 - whatever has arrived and fits is decoded as one batch: gc_plan_select
   builds the work records of exactly those lists, aimed at the requests'
   places in the arena, and gc_decode_plan decodes them in one persistent
@@ -89,20 +93,25 @@ class Request:
     tiles: int = 0
     out: int = -1               # offset of its first int in the arena
     done: float = -1.0          # completion time (seconds from the start)
+    waited: bool = False        # it once found the arena without room for it
 
 
 def form_batch(pending: deque, arena: RingArena, max_requests: int, max_lists: int, max_tiles: int):
     """Take requests from the head of `pending` (in arrival order) while they
     fit the batch limits and the room the arena has now; each gets its arena
     offset. Returns the requests taken (none when even the first does not fit
-    yet) and the arena units they hold."""
+    yet) and the arena units they hold. The first request left behind for
+    want of arena room is marked as having waited."""
     room = arena.available()
     taken, lists, tiles, need = [], 0, 0, 0
     while pending and len(taken) < max_requests:
         r = pending[0]
         if len(r.lists) > max_lists or r.tiles > max_tiles or r.ints > arena.size:
             raise ValueError(f"request {r.rid} is larger than one batch")
-        if lists + len(r.lists) > max_lists or tiles + r.tiles > max_tiles or need + r.ints > room:
+        if lists + len(r.lists) > max_lists or tiles + r.tiles > max_tiles:
+            break
+        if need + r.ints > room:
+            r.waited = True
             break
         taken.append(r)
         lists += len(r.lists)
@@ -160,13 +169,16 @@ class _Slot:
 class Server:
     """Serves decode requests over `index` (a resident gc.Index)."""
 
-    def __init__(self, index, arena_ints: int, streams: int = 3, max_requests: int = 2048,
+    def __init__(self, index, arena_ints: int | None = None, streams: int = 3, max_requests: int = 2048,
                  max_lists: int = 16384, max_tiles: int = 1 << 18, restore_docids: bool = True,
                  launch=None, device=None):
         import torch
         self.torch = torch
         self.index = index
         self.dev = index.data.device if device is None else torch.device(device)
+        if arena_ints is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            arena_ints = min(free // 2, 4 << 30) // 4
         self.k = index.codec.k
         self.tiles = tiles_of(index.lengths, self.k)
         self.arena = torch.empty(max(1, arena_ints), dtype=torch.int32, device=self.dev)
@@ -232,7 +244,7 @@ class Server:
         while self.order and self.order[0].batch[0][0].done >= 0:
             s = self.order.popleft()
             if on_complete is not None:
-                _gc.check_status(s.status, "served batch")
+                # (each slot's status is read once the run ends)
                 for r in s.batch[0]:
                     on_complete(r, self.arena[r.out:r.out + r.ints])
             self.alloc.free_oldest()
@@ -266,10 +278,14 @@ class Server:
         return time.perf_counter() - t0, requests
 
 
-def serve_one_launch_per_list(index, requests, restore_docids: bool = True, time_limit: float = 60.0):
+def serve_one_launch_per_list(index, requests, restore_docids: bool = True, time_limit: float = 60.0,
+                              issue_limit: float | None = None):
     """The baseline: each list of each request decoded by its own gc_decode
     call (one launch of the decoder per list) as requests arrive, on one
-    stream, into a reused output buffer. Returns (wall seconds, requests)."""
+    stream, into a reused output buffer. With issue_limit, no request is
+    issued after that many seconds (a saturated baseline then serves only
+    the requests issued by then). Returns (wall seconds, the requests
+    served)."""
     import ctypes
     import torch
     dev = index.data.device
@@ -292,10 +308,12 @@ def serve_one_launch_per_list(index, requests, restore_docids: bool = True, time
         now = time.perf_counter() - t0
         if now > time_limit:
             raise RuntimeError(f"per-list serving did not finish within {time_limit} s")
+        if issue_limit is not None and now > issue_limit and not inflight:
+            break
         while inflight and inflight[0][1].query():
             inflight.popleft()[0].done = now
             left -= 1
-        if i < len(order) and order[i].arrival <= now:
+        if i < len(order) and order[i].arrival <= now and (issue_limit is None or now <= issue_limit):
             r = order[i]
             i += 1
             for li in r.lists.tolist():
@@ -311,12 +329,17 @@ def serve_one_launch_per_list(index, requests, restore_docids: bool = True, time
             inflight.append((r, ev))
     torch.cuda.synchronize(dev)
     _gc.check_status(st, "per-list decode")
-    return time.perf_counter() - t0, requests
+    return time.perf_counter() - t0, [r for r in order if r.done >= 0]
 
 
-def latency_summary(requests, wall: float, lengths: np.ndarray):
-    lat = np.array([r.done - r.arrival for r in requests])
-    ints = int(sum(int(lengths[r.lists].sum(dtype=np.int64)) for r in requests))
-    return {"requests": len(requests), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
-            "ints": ints, "ints_per_s": ints / wall, "wall_s": wall}
+def latency_summary(requests, wall: float, lengths: np.ndarray, offered: int | None = None):
+    """p50/p99/max latency of the served requests, their ints per second,
+    and how many of them waited for arena room (admission stalls); offered
+    is how many requests the trace held (when fewer were served)."""
+    served = [r for r in requests if r.done >= 0]
+    lat = np.array([r.done - r.arrival for r in served]) if served else np.zeros(1)
+    ints = int(sum(int(lengths[r.lists].sum(dtype=np.int64)) for r in served))
+    return {"requests": len(requests) if offered is None else int(offered), "served": len(served),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3), "ints": ints, "ints_per_s": ints / wall, "wall_s": wall,
+            "admission_waits": int(sum(1 for r in served if r.waited))}

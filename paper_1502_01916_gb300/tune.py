@@ -7,7 +7,13 @@ plan records a block claims per atomic, and how deep the staging ring is
 times gc_decode_plan on the caller's resident index for a small grid of
 those shapes, keeps the fastest, and caches it in a JSON file keyed by the
 device, the codec and the workload class (how long the index's lists are),
-so that a server or benchmark tunes once per kind of index.
+so that a server or benchmark tunes once per kind of index. The chosen
+shape is registered with the library (gc_set_launch), so that later decode
+calls given no launch shape use it.
+
+The vector width k is a property of the encoded index, not of the launch:
+choose_k encodes the same lists at k = 4 and k = 32, tunes each, and
+reports both rates beside their sizes, for an index builder to pick from.
 """
 from __future__ import annotations
 
@@ -25,8 +31,6 @@ CANDIDATES = {
          (7, 3, 16, 0), (7, 3, 32, 16384)],
     4: [(7, 2, 32, 0), (7, 2, 32, 24576), (7, 2, 16, 0), (3, 4, 32, 0), (15, 1, 32, 0)],
 }
-
-
 
 
 def candidates_for(k: int):
@@ -76,9 +80,11 @@ def save_cache(path: str, cache: dict):
 
 
 def tune(index, plan=None, restore_docids: bool = True, candidates=None, reps: int = 3, cache_path: str | None = None,
-         use_cache: bool = True):
+         use_cache: bool = True, register: bool = True):
     """The fastest launch shape for decoding `index` (a gc.Index) and its
-    timings. Returns (gc_launch, {"key", "best_ms", "ms": {shape: ms}, "cached"})."""
+    timings; registered with the library for the index's codec unless
+    register is False. Returns (gc_launch, {"key", "best_ms", "ms": {shape:
+    ms}, "cached"})."""
     import torch
     dev = index.data.device
     name = torch.cuda.get_device_name(dev)
@@ -88,7 +94,10 @@ def tune(index, plan=None, restore_docids: bool = True, candidates=None, reps: i
         with _lock:
             hit = load_cache(path).get(key)
         if hit and len(hit.get("shape", ())) == 4:
-            return _gc.gc_launch(*hit["shape"]), {"key": key, "best_ms": hit["ms"], "ms": {}, "cached": True}
+            launch = _gc.gc_launch(*hit["shape"])
+            if register:
+                _gc.gc_set_launch(index.codec, restore_docids, launch)
+            return launch, {"key": key, "best_ms": hit["ms"], "ms": {}, "cached": True}
     plan = plan if plan is not None else _gc.plan_index(index)
     out = torch.empty(max(1, index.out_ints), dtype=torch.int32, device=dev)
     scratch = torch.empty(_gc.gc_decode_plan_scratch_size(index.max_tiles), dtype=torch.uint8, device=dev)
@@ -108,6 +117,8 @@ def tune(index, plan=None, restore_docids: bool = True, candidates=None, reps: i
         times[shape] = float(np.median([s.elapsed_time(e) for s, e in ev]))
     _gc.check_status(st, "tuning decode")
     best = min(times, key=times.get)
+    if register:
+        _gc.gc_set_launch(index.codec, restore_docids, _gc.gc_launch(*best))
     if use_cache:
         with _lock:
             cache = load_cache(path)
@@ -115,3 +126,26 @@ def tune(index, plan=None, restore_docids: bool = True, candidates=None, reps: i
             save_cache(path, cache)
     return _gc.gc_launch(*best), {"key": key, "best_ms": times[best],
                                   "ms": {"x".join(map(str, sh)): t for sh, t in times.items()}, "cached": False}
+
+
+def choose_k(kind: int, d_gaps, lengths, out_offsets=None, restore_docids: bool = True, reps: int = 3,
+             register: bool = True, **codec_kw):
+    """Encode the lists at k = 4 and at k = 32 (same codec kind and
+    parameters), tune the launch shape of each, and time each index's decode
+    with its best shape. Returns (k, {k: {"ms", "bits_per_int", "shape"}}),
+    k the faster one (the smaller index on a tie within 1%)."""
+    by_k = {}
+    for k in (4, 32):
+        idx = _gc.encode_index(_gc.make_codec(kind, k, **codec_kw), d_gaps, lengths, out_offsets=out_offsets)
+        plan = _gc.plan_index(idx)
+        launch, info = tune(idx, plan, restore_docids, reps=reps, use_cache=False, register=register)
+        by_k[k] = {"ms": info["best_ms"], "bits_per_int": 8.0 * idx.compressed_bytes() / max(1, idx.total_ints),
+                   "shape": [launch.warps_per_block, launch.blocks_per_sm, launch.items_per_claim,
+                             launch.stage_bytes]}
+        del idx, plan
+    a, b = by_k[4], by_k[32]
+    if abs(a["ms"] - b["ms"]) <= 0.01 * min(a["ms"], b["ms"]):
+        best = 4 if a["bits_per_int"] <= b["bits_per_int"] else 32
+    else:
+        best = 4 if a["ms"] < b["ms"] else 32
+    return best, by_k

@@ -35,8 +35,23 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("gc_encode", "gc_decode", "gc_decode_batch", "gc_build_tiles", "gc_decode_paper",
-                 "gc_max_encoded_size"):
+                 "gc_max_encoded_size", "gc_paper_bytes", "gc_pack_paper", "gc_unpack_paper", "gc_set_launch",
+                 "gc_get_launch", "gc_decode_plan_host", "gc_decode_plan_host_buffer_size", "gc_shutdown"):
         assert must in names
+
+
+@pytest.mark.parametrize("cb,dw", [(0, 0), (1, 0), (11, 3), (12, 8), (13, 4), (100, 1000)])
+def test_paper_buffer_size_agrees_with_oracle(gc, cb, dw):
+    """The single buffer of Sec 4.3 step 1: head, control, padding, data."""
+    rng = np.random.default_rng(cb * 1000 + dw)
+    ctrl = rng.integers(0, 256, cb, dtype=np.uint8)
+    data = rng.integers(0, 2**32, dw, dtype=np.uint64).astype(np.uint32)
+    assert gc.gc_paper_bytes(cb, dw) == len(O.paper_pack(ctrl, data))
+
+
+def test_shutdown_without_a_device_is_harmless(gc):
+    gc.gc_shutdown()
+    gc.gc_shutdown()
 
 
 def test_library_exports_every_declared_symbol(gc):

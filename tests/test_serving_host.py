@@ -85,11 +85,33 @@ def test_form_batch_waits_for_arena_space():
     arena = RingArena(1000)
     taken, _ = form_batch(pending, arena, 1, 100, 100)
     assert [r.rid for r in taken] == [0]
+    assert not taken[0].waited
     taken, units = form_batch(pending, arena, 1, 100, 100)
     assert taken == [] and units == 0 and len(pending) == 2  # no room until request 0 is given back
+    assert pending[0].waited and not pending[1].waited  # an admission stall, counted once per request
     arena.free_oldest()
     taken, _ = form_batch(pending, arena, 1, 100, 100)
-    assert [r.rid for r in taken] == [1]
+    assert [r.rid for r in taken] == [1] and taken[0].waited
+
+
+def test_batch_limits_are_not_admission_stalls():
+    """A request left for the next batch by the batch's list or tile limit
+    did not wait for arena room."""
+    pending = deque(_req(i, 2, 10, 1) for i in range(3))
+    taken, _ = form_batch(pending, RingArena(1000), 2, 100, 100)
+    assert [r.rid for r in taken] == [0, 1] and not pending[0].waited
+
+
+def test_latency_summary_counts_served_and_waits():
+    from paper_1502_01916_gb300.serve import latency_summary
+    rs = [_req(i, 2, 10, 1) for i in range(4)]
+    for i, r in enumerate(rs[:3]):
+        r.arrival, r.done = 0.0, 0.001 * (i + 1)
+    rs[1].waited = True
+    lengths = np.full(10, 5, np.uint32)
+    s = latency_summary(rs, 1.0, lengths, offered=4)
+    assert s["requests"] == 4 and s["served"] == 3 and s["admission_waits"] == 1
+    assert abs(s["max_ms"] - 3.0) < 1e-9
 
 
 def test_form_batch_never_asks_more_than_the_arena_holds():
