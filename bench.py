@@ -10,8 +10,17 @@ offset of the output (at most 3 ints of padding per list). One step decodes the 
 and restores docIDs (fused prefix sum): one CUDA-graph launch per codec.
 
 Prints one JSON line: decoded ints/s (all codecs, all ranks), the roofline of
-the decode kernel, the end-to-end rate through the C ABI with host buffers,
-the one-launch-per-list rate, the CPU oracle baseline and the SM clocks.
+the decode kernel, the end-to-end rate through the C ABI with host buffers
+(gc_decode_plan_host), the one-launch-per-list rate, the CPU oracle baseline
+and the SM clocks. Beside the headline, after its timed region and each
+checked against the host's prefix sums on its own: the single 65,536-docID
+list (latency, with its tile index and as the paper's single buffer), the
+2^26-gap list for every codec variant at k = 4 and k = 32, the headline
+index decoded without skip entries (decoupled look-back on the timed path),
+k = 4 against k = 32 on the headline lists, the clustered short-list index
+(zeta sweep, Group-Scheme 8-IU and 8-B, with and without Variable Byte),
+AND queries, TF streams and the serving loop at three request rates against
+one launch per list.
 `--impl reference` times the CPU oracle instead (the slow reference arm).
 """
 from __future__ import annotations
@@ -32,13 +41,14 @@ if ROOT not in sys.path:
 
 UNIVERSE = 25_000_000
 CODECS = {"simple": (0, "Group-Simple"), "pfd": (3, "Group-PFD")}
-# DRAM bytes (read + write) per decode launch of the default workload, from one
-# ncu capture (profiles/k_decode_zipf_index_dram.md), with the hash of the
-# kernel sources they were taken on; once the sources change, null.
-NCU_TRAFFIC = {
-    "simple": {"bytes": 2955671040 + 5949691392, "hash": "ac3384ca0960181e"},
-    "pfd": {"bytes": 2432133888 + 5944830208, "hash": "ac3384ca0960181e"},
-}
+# DRAM traffic (read + write) of one decode launch per algorithmic byte,
+# measured by ncu on the small Zipf index (100,000 lists, C = 3.0406e7, 1.8e8
+# docIDs), with the hash of the kernel sources it was taken on. The full-size
+# launch's traffic is reported as this ratio times its algorithmic bytes (the
+# decoder reads and writes each byte once, so traffic grows in proportion);
+# once the sources change, null. Multi-metric captures of the full-size
+# workload are not taken.
+NCU_TRAFFIC_RATIO = {}
 
 
 def parse():
@@ -67,8 +77,11 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the TF-stream and zeta = 0 decodes")
     p.add_argument("--no-and", action="store_true", help="skip the AND-query measurement")
     p.add_argument("--no-short", action="store_true", help="skip the short-list (Variable Byte rule) measurement")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the single-list, 2^26-list and look-back measurements")
+    p.add_argument("--no-k-choice", action="store_true", help="skip timing the index at k = 4 against k = 32")
     p.add_argument("--and-queries", type=int, default=4000, help="two-list AND queries in the timed batch")
-    p.add_argument("--serve-seconds", type=float, default=0.5, help="trace length per request rate")
+    p.add_argument("--serve-seconds", type=float, default=2.0, help="trace length per request rate")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="seconds of oracle work per codec")
     return p.parse_args()
 
@@ -412,88 +425,70 @@ def main():
                         "frac": alg / (ms / 1e3) / 1e9 / peak, "launches_per_graph": launches[n]}
     dom = max(per_codec, key=lambda n: per_codec[n]["ms_per_launch"])
     kh = kernel_hash()
-    traffic = NCU_TRAFFIC.get(dom)
-    default_workload = a.nlists == 1_000_000 and not a.zipf_c and a.k == 32 and a.zeta == 0.10
-    traffic = traffic["bytes"] if traffic and traffic.get("hash") == kh and default_workload else None
+    ratio = NCU_TRAFFIC_RATIO.get(dom)
+    traffic, traffic_source = None, "none: no ncu capture of these kernel sources"
+    if ratio and ratio.get("hash") == kh and a.k == 32 and a.zeta == 0.10:
+        traffic = ratio["ratio"] * per_codec[dom]["algorithmic_bytes"]
+        traffic_source = ("ncu dram__bytes_read.sum + dram__bytes_write.sum on the 1.8e8-docID Zipf index, "
+                          f"{ratio['ratio']:.4f} of its algorithmic bytes, scaled to this launch's")
     roofline = {"bound": "hbm", "kernel": f"k_decode<{CODECS[dom][1]}, k={a.k}, batched>",
                 "bytes_per_launch": per_codec[dom]["algorithmic_bytes"],
                 "achieved": per_codec[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                "frac": per_codec[dom]["frac"], "traffic": traffic, "peak_source": peak_src,
+                "frac": per_codec[dom]["frac"], "traffic": traffic, "traffic_source": traffic_source,
+                "peak_source": peak_src,
                 "timed_as": "graph launch (memset of the queue counter and look-back words + decode kernel)"}
 
-    # end to end through the C ABI with host buffers: every step copies each
-    # codec's plan and pools in from pinned host memory, decodes, and copies
-    # its docIDs out to pinned host memory. The steps are pipelined as a
-    # caller would: one stream copies in, one decodes, one copies out (the
-    # host link carries both directions at once); a codec's pools are copied
-    # again only after the kernel that read them, and its output is decoded
-    # into again only after it was copied out.
+    def list_ids(i):
+        return np.cumsum(gaps[int(off[i]):int(off[i]) + int(lengths[i])], dtype=np.uint32)
+
+    rng_s = np.random.default_rng(23)
+    sample = rng_s.choice(len(lengths), min(300, len(lengths)), replace=False).tolist()
+    sample += np.argsort(lengths)[-3:].tolist()  # and the longest lists
+
+    # end to end through the C ABI with host buffers: every step hands each
+    # codec's plan, pools and output, all in page-locked host memory, to
+    # gc_decode_plan_host, which copies them in, decodes and copies the
+    # docIDs back out on its stream; the two codecs use two streams, so one
+    # codec's copies overlap the other's decode.
     e2e = None
     if not a.no_e2e:
-        host = {}
+        hbuf, dbuf, sts = {}, {}, {}
         h2d = 0
         for n, idx in idxs.items():
-            pools = [plans[n].work, idx.ctrl, idx.data]
-            hp = [torch.empty(p.shape, dtype=p.dtype, pin_memory=True) for p in pools]
-            for h, p in zip(hp, pools):
-                h.copy_(p)
-                h2d += p.numel() * p.element_size()
-            host[n] = (hp, pools)
+            nwork = int(plans[n].count[0].item())
+            hw = torch.empty(nwork * gc.WORK_BYTES, dtype=torch.uint8, pin_memory=True)
+            hw.copy_(plans[n].work[:nwork * gc.WORK_BYTES])
+            hc = torch.empty(idx.ctrl.shape, dtype=idx.ctrl.dtype, pin_memory=True)
+            hc.copy_(idx.ctrl)
+            hd = torch.empty(idx.data.shape, dtype=idx.data.dtype, pin_memory=True)
+            hd.copy_(idx.data)
+            ho = torch.empty(out_len, dtype=torch.int32, pin_memory=True)
+            hbuf[n] = (hw, nwork, hc, hd, ho)
+            h2d += hw.numel() + hc.numel() + 4 * hd.numel()
+            size = gc.gc_decode_plan_host_buffer_size(nwork, hc.numel(), hd.numel(), out_len)
+            dbuf[n] = torch.empty(size, dtype=torch.uint8, device=dev)
+            sts[n] = torch.cuda.Stream(device=dev)
         d2h = 4 * out_len * len(idxs)
-        dout = {n: torch.empty(out_len, dtype=torch.int32, device=dev) for n in idxs}
-        hout = {n: torch.empty(out_len, dtype=torch.int32, pin_memory=True) for n in idxs}
-        s_in, s_dec, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
-        g_e2e = {}
-        for n, idx in idxs.items():
-            with torch.cuda.stream(s_dec):
-                gc.decode_index(idx, out=dout[n], scratch=scratch[n], status=status[n], launch=launches_cfg[n],
-                                check=False, plan=plans[n])
-            s_dec.synchronize()
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=s_dec, capture_error_mode="relaxed"):
-                gc.decode_index(idx, out=dout[n], scratch=scratch[n], status=status[n], launch=launches_cfg[n],
-                                check=False, plan=plans[n])
-            g_e2e[n] = g
         torch.cuda.synchronize()
-        k_done, o_done = {n: None for n in idxs}, {n: None for n in idxs}
 
         def e2e_step():
-            for n in idxs:
-                hp, pools = host[n]
-                if k_done[n] is not None:
-                    s_in.wait_event(k_done[n])
-                with torch.cuda.stream(s_in):
-                    for h, p in zip(hp, pools):
-                        p.copy_(h, non_blocking=True)
-                e_in = torch.cuda.Event()
-                e_in.record(s_in)
-                s_dec.wait_event(e_in)
-                if o_done[n] is not None:
-                    s_dec.wait_event(o_done[n])
-                with torch.cuda.stream(s_dec):
-                    g_e2e[n].replay()
-                e_k = torch.cuda.Event()
-                e_k.record(s_dec)
-                k_done[n] = e_k
-                s_out.wait_event(e_k)
-                with torch.cuda.stream(s_out):
-                    hout[n].copy_(dout[n], non_blocking=True)
-                e_o = torch.cuda.Event()
-                e_o.record(s_out)
-                o_done[n] = e_o
+            for n, idx in idxs.items():
+                hw, nwork, hc, hd, ho = hbuf[n]
+                gc.gc_decode_plan_host(idx.codec, hw, nwork, hc, hd, ho, True, launches_cfg[n], dbuf[n], status[n],
+                                       sts[n])
 
-        for _ in range(max(1, a.warmup)):
+        for _ in range(max(1, min(a.warmup, 2))):
             e2e_step()
         torch.cuda.synchronize()
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(cur)
-        for st_ in (s_in, s_dec, s_out):
+        for st_ in sts.values():
             st_.wait_event(f0)
         ksteps = max(1, min(a.steps, 5))
         for _ in range(ksteps):
             e2e_step()
-        for st_ in (s_in, s_dec, s_out):
+        for st_ in sts.values():
             e = torch.cuda.Event()
             e.record(st_)
             cur.wait_event(e)
@@ -505,37 +500,42 @@ def main():
             t = torch.tensor([ems], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
+        ok = True
         for n in idxs:
             gc.check_status(status[n], f"e2e decode {n}")
-        # each direction alone, for context: one codec's pools in, one output out
-        n0 = next(iter(idxs))
-        c0, c1, c2, c3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
-        c0.record(cur)
-        for h, p in zip(*host[n0]):
-            p.copy_(h, non_blocking=True)
-        c1.record(cur)
-        c2.record(cur)
-        hout[n0].copy_(dout[n0], non_blocking=True)
-        c3.record(cur)
-        torch.cuda.synchronize()
-        in_b = sum(p.numel() * p.element_size() for p in host[n0][1])
+            got = hbuf[n][4].numpy().view(np.uint32)
+            ok = ok and all(np.array_equal(got[int(off[i]):int(off[i]) + int(lengths[i])], list_ids(i))
+                            for i in sample)
         e2e = {"value": ints_per_step * ksteps * world / (ems / 1e3), "unit": "ints/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ksteps,
-               "pipelined": "copy-in, decode and copy-out streams",
-               "h2d_gbs_alone": in_b / (c0.elapsed_time(c1) / 1e3) / 1e9,
-               "d2h_gbs_alone": 4 * out_len / (c2.elapsed_time(c3) / 1e3) / 1e9}
-        del dout, hout, host, g_e2e
+               "api": "gc_decode_plan_host (plan, pools and output in page-locked host memory), one stream per codec",
+               "sample_verified": bool(ok), "sample_lists": len(sample)}
+        del hbuf, dbuf
 
     # one launch per list (gc_decode on each list of a sample)
     per_list = None
     if not a.no_per_list:
         per_list = per_list_rate(gc, idxs, lengths, dev)
 
+    # the other workloads' single-list paths and the headline index without
+    # skip entries (look-back on the timed path)
+    configs = None
+    if not a.no_configs:
+        configs = {"single_list_65536": single_list_latency(gc, dev, peak),
+                   "mixed_2_26": mixed_list_rates(gc, dev, peak),
+                   "lookback": lookback_rate(gc, idxs[dom], plans[dom], out, peak, total_ints, off, lengths,
+                                             list_ids, sample)}
+
+    # k = 4 against k = 32 on the same lists (the autotuner's index-build choice)
+    k_choice = None
+    if not a.no_k_choice and a.k == 32:
+        k_choice = k_choice_rates(gc, gaps, lengths, off, dev, [CODECS[n][0] for n in idxs])
+
     # serving: continuous batching over the resident index, Poisson arrivals
     serving = None
     if not a.no_serving:
         sn = "pfd" if "pfd" in idxs else next(iter(idxs))
-        serving = serving_rates(gc, idxs[sn], a.serve_seconds, launch=launches_cfg[sn])
+        serving = serving_rates(gc, idxs[sn], list_ids, a.serve_seconds, launch=launches_cfg[sn])
 
     # AND queries over the resident index (skip entries bound what is decoded)
     and_q = None
@@ -581,7 +581,7 @@ def main():
                    "autotuned": tuned or None,
                    "plan": "work plan (64 B per tile) built once per resident index, outside the timed region"},
         "roofline": roofline, "per_codec": per_codec, "e2e": e2e, "per_list_launch": per_list, "serving": serving,
-        "extras": extras, "and_queries": and_q, "short_lists": short,
+        "configs": configs, "k_choice": k_choice, "extras": extras, "and_queries": and_q, "short_lists": short,
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(sum(launches.values()) * a.steps),
         "verified_full_output": verified, "setup_s": {"generate": t_gen, "encode": t_enc},
@@ -653,11 +653,12 @@ def extra_rates(gc, lengths, off, gaps, dev, peak, reps=5, nsample=300, seed=5):
 def short_list_rates(gc, dev, reps=5, nsample=300, seed=17):
     """The clustered short-list index (4M lists over 50M documents,
     log-normal lengths with median 12, clustered docIDs; 87% of the lists
-    shorter than 64), encoded with Group-PFD and with Group-Scheme at byte
-    granularity (incomplete unary), each alone and with the paper's rule for
-    short lists (Variable Byte below 64 postings, Sec 7.5): compressed bits
-    per int and the decode time of the whole index (CUDA events; the plan of
-    the Group part built beforehand), checked on a sample of lists."""
+    shorter than 64), encoded with Group-PFD at zeta 0.01, 0.1 and 0.3 and
+    with Group-Scheme at byte granularity (incomplete unary and binary
+    descriptors), each alone and with the paper's rule for short lists
+    (Variable Byte below 64 postings, Sec 7.5): compressed bits per int and
+    the decode time of the whole index (CUDA events; the plan of the Group
+    part built beforehand), checked on a sample of lists."""
     import torch
     import synth
     gaps, off, lens = synth.clustered_short_index()
@@ -687,7 +688,9 @@ def short_list_rates(gc, dev, reps=5, nsample=300, seed=17):
         return float(np.median(ts)), ok
 
     res = {"lists": int(len(lens)), "ints": total, "short_share": float((lens < 64).mean())}
-    for name, kind, kw in (("pfd", 3, {"zeta": 0.10}), ("scheme_iu_cg8", 1, {"cg": 8, "ld": gc.LD_IU})):
+    for name, kind, kw in (("pfd_z0.01", 3, {"zeta": 0.01}), ("pfd", 3, {"zeta": 0.10}), ("pfd_z0.3", 3, {"zeta": 0.30}),
+                           ("scheme_iu_cg8", 1, {"cg": 8, "ld": gc.LD_IU}),
+                           ("scheme_b_cg8", 1, {"cg": 8, "ld": gc.LD_BINARY})):
         codec = gc.make_codec(kind, 32, **kw)
         idx = gc.encode_index(codec, d, lens)
         plan = gc.plan_index(idx)
@@ -758,25 +761,198 @@ def and_query_rates(gc, idx, lengths, off, gaps, dev, nq=4000, reps=5, nverify=2
             "launches_per_batch": gc.gc_last_launch_count()}
 
 
-def serving_rates(gc, idx, seconds, rates=(1e4, 5e4, 2e5), launch=None):
+def serving_rates(gc, idx, list_ids, seconds, rates=(1e4, 5e4, 2e5), launch=None, nverify=40, seed=31):
     """Requests of 2-8 lists (chosen with probability proportional to
-    length^0.5) arriving as a Poisson process, served by continuous batching
-    over the resident index; the lowest rate is also served with one decoder
-    launch per list. Latency is arrival to completion of the request's last
-    list."""
+    length^0.5) arriving as a Poisson process for `seconds`, served by
+    continuous batching over the resident index (arena: half the free device
+    memory, at most 4 GiB) and, on the same trace, by one decoder launch per
+    list (which stops issuing when the trace ends: a saturated baseline
+    serves fewer requests, and says so). Latency is arrival to completion of
+    the request's last list. A random sample of the batched requests'
+    docIDs is checked against the host's prefix sums."""
     from paper_1502_01916_gb300 import serve
     res = {"codec": gc.codec_name(idx.codec), "seconds": seconds, "rates": {}}
+    rng = np.random.default_rng(seed)
     for rate in rates:
         reqs = serve.poisson_trace(idx.lengths, rate, seconds, seed=int(rate))
-        srv = serve.Server(idx, arena_ints=1 << 29, streams=3, launch=launch)
-        wall, done = srv.run(reqs, time_limit=120.0)
+        check = set(rng.choice(len(reqs), min(nverify, len(reqs)), replace=False).tolist())
+        got = {}
+
+        def keep(r, view, check=check, got=got):
+            if r.rid in check:
+                got[r.rid] = gc.as_u32(view).copy()
+
+        srv = serve.Server(idx, streams=3, launch=launch)
+        wall, done = srv.run(reqs, on_complete=keep, time_limit=seconds + 120.0)
         summ = serve.latency_summary(done, wall, idx.lengths)
-        summ.update({"batches": srv.batches, "gpu_launches": srv.launches})
-        res["rates"][f"{int(rate)}"] = summ
-    rate = rates[0]
-    reqs = serve.poisson_trace(idx.lengths, rate, min(seconds, 0.2), seed=int(rate))
-    wall, done = serve.serve_one_launch_per_list(idx, reqs, time_limit=120.0)
-    res["one_launch_per_list"] = {"rate": int(rate), **serve.latency_summary(done, wall, idx.lengths)}
+        ok = len(got) == len(check) and all(
+            np.array_equal(got[r.rid], np.concatenate([list_ids(li) for li in r.lists.tolist()]))
+            for r in reqs if r.rid in check)
+        summ.update({"batches": srv.batches, "gpu_launches": srv.launches, "sample_verified": bool(ok),
+                     "arena_ints": srv.alloc.size})
+        del srv
+        base = serve.poisson_trace(idx.lengths, rate, seconds, seed=int(rate))
+        bwall, served = serve.serve_one_launch_per_list(idx, base, time_limit=seconds + 120.0, issue_limit=seconds)
+        bsum = serve.latency_summary(served, bwall, idx.lengths, offered=len(base))
+        bsum["saturated"] = len(served) < len(base) or bsum["p50_ms"] > 1e3 * seconds / 4
+        res["rates"][f"{int(rate)}"] = {"batched": summ, "one_launch_per_list": bsum}
+    return res
+
+
+def _timed(fn, reps=5, warm=3):
+    """Median milliseconds of fn() over reps runs (CUDA events on the current
+    stream, after warm runs)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def single_list_latency(gc, dev, peak, reps=50):
+    """One list of 65,536 docIDs (d-gaps geometric, mean 20), Group-Simple
+    at k = 4 (the paper's layout) and k = 32: the latency of one decode call
+    with its tile index (gc_decode) and, at k = 4, of the paper's single
+    buffer (gc_decode_paper: the tile index built from the control area, the
+    tiles joined by look-back; the call reads the buffer's head on the host,
+    so it synchronises once). Device time by CUDA events, host time by the
+    wall clock around call + synchronise; the list fits in L2."""
+    import torch
+    import synth
+    g = synth.single_list_geometric(65536, 20.0, 0)
+    want = np.cumsum(g, dtype=np.uint32)
+    n = len(g)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    st = gc.new_status(dev)
+    res = {"ints": n, "codec": "Group-Simple", "bound": "latency (L2-resident)"}
+    for k in (4, 32):
+        codec = gc.make_codec(gc.SIMPLE, k)
+        enc = gc.encode(codec, g)
+        scratch = torch.empty(gc.gc_decode_scratch_size(codec, n, True), dtype=torch.uint8, device=dev)
+
+        def call():
+            gc.gc_decode(codec, enc.ctrl, enc.ctrl_bytes, enc.data, enc.data_words, n, enc.tiles, out, True, scratch,
+                         st)
+
+        paths = [("with_tile_index", call)]
+        if k == 4:
+            buf = gc.pack_paper(enc)
+            pscratch = torch.empty(gc.gc_decode_scratch_size(codec, n, False), dtype=torch.uint8, device=dev)
+            paths.append(("paper_buffer", lambda: gc.gc_decode_paper(codec, buf, n, out, True, pscratch, st)))
+        for name, fn in paths:
+            out.fill_(0)
+            ms = _timed(fn, reps=reps)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+                torch.cuda.synchronize()
+            host_us = (time.perf_counter() - t0) / reps * 1e6
+            gc.check_status(st, f"single list {name}")
+            alg = enc.compressed_bytes() + 4 * n
+            res[f"k{k}_{name}"] = {"device_us": 1e3 * ms, "host_us": host_us, "ints_per_s": n / (ms / 1e3),
+                                   "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac": alg / (ms / 1e3) / 1e9 / peak,
+                                   "bits_per_int": 8.0 * enc.compressed_bytes() / n,
+                                   "verified": bool(np.array_equal(gc.as_u32(out), want))}
+    return res
+
+
+def mixed_list_rates(gc, dev, peak, reps=5):
+    """One list of 2^26 d-gaps (runs of 256: 90% geometric mean 8, 10%
+    uniform to 2^20), one decode call (plan + persistent decode, docIDs
+    restored) for every codec variant at k = 4 and k = 32; algorithmic
+    bytes = control + data + the tile index read (32 B per tile) + 4 B per
+    docID written. Every docID checked against the host's prefix sums."""
+    import torch
+    import synth
+    g = synth.single_list_mixed(1 << 26, 0)
+    n = len(g)
+    want = np.cumsum(g, dtype=np.uint32)
+    d = torch.from_numpy(g.view(np.int32)).to(dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    st = gc.new_status(dev)
+    variants = [("simple", gc.SIMPLE, {}), ("scheme_1B", gc.SCHEME, {"cg": 1, "ld": gc.LD_BINARY}),
+                ("scheme_1CU", gc.SCHEME, {"cg": 1, "ld": gc.LD_CU}),
+                ("scheme_8B", gc.SCHEME, {"cg": 8, "ld": gc.LD_BINARY}),
+                ("scheme_8IU", gc.SCHEME, {"cg": 8, "ld": gc.LD_IU}), ("afor", gc.AFOR, {}),
+                ("pfd", gc.PFD, {"zeta": 0.10})]
+    res = {"ints": n}
+    for k in (4, 32):
+        for name, kind, kw in variants:
+            codec = gc.make_codec(kind, k, **kw)
+            enc = gc.encode(codec, d)
+            scratch = torch.empty(gc.gc_decode_scratch_size(codec, n, True), dtype=torch.uint8, device=dev)
+            ms = _timed(lambda: gc.gc_decode(codec, enc.ctrl, enc.ctrl_bytes, enc.data, enc.data_words, n, enc.tiles,
+                                             out, True, scratch, st))
+            gc.check_status(st, f"2^26 list {name} k={k}")
+            alg = enc.compressed_bytes() + enc.tiles.numel() + 4 * n
+            res[f"{name}_k{k}"] = {"ms": ms, "ints_per_s": n / (ms / 1e3), "bits_per_int": 8.0 * enc.compressed_bytes() / n,
+                                   "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac": alg / (ms / 1e3) / 1e9 / peak,
+                                   "verified": bool(np.array_equal(gc.as_u32(out), want))}
+            del enc, scratch
+    del d, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def lookback_rate(gc, idx, plan, out, peak, total_ints, off, lengths, list_ids, sample, reps=5):
+    """The headline index decoded without skip entries: the plan's records
+    lose their bases (a list's first tile starts from 0), so every later
+    tile takes its prefix from the tiles before it by decoupled look-back
+    (claimed one record at a time). Timed like the headline, checked on a
+    sample of lists and the longest ones."""
+    import torch
+    dev = out.device
+    nwork = int(plan.count[0].item())
+    w = plan.work[:nwork * gc.WORK_BYTES].cpu().numpy().view(gc.WORK_DTYPE).copy()
+    w["shape"] &= np.uint32(~(gc.WORK_HAS_BASE | gc.WORK_PUBLISH) & 0xFFFFFFFF)
+    w["base"] = 0
+    first = w["tile"] == 0
+    w["shape"][first] |= np.uint32(gc.WORK_HAS_BASE)
+    nxt = np.zeros(nwork, bool)
+    nxt[:-1] = (w["list"][1:] == w["list"][:-1]) & (w["tile"][1:] > 0)
+    w["shape"][nxt & first] |= np.uint32(gc.WORK_PUBLISH)
+    nlb = int((~first & (w["list"] != 0xFFFFFFFF)).sum())
+    lplan = gc.Plan(torch.from_numpy(w.view(np.uint8).reshape(-1)).to(dev),
+                    torch.tensor([nwork, nlb], dtype=torch.int64, device=dev))
+    del w
+    scratch = torch.empty(gc.gc_decode_plan_scratch_size(nwork), dtype=torch.uint8, device=dev)
+    st = gc.new_status(dev)
+    ms = _timed(lambda: gc.decode_index(idx, out=out, scratch=scratch, status=st, plan=lplan, check=False), reps=reps)
+    gc.check_status(st, "look-back decode")
+    got = gc.as_u32(out)
+    ok = all(np.array_equal(got[int(off[i]):int(off[i]) + int(lengths[i])], list_ids(i)) for i in sample)
+    alg = idx.compressed_bytes() + lplan.nbytes() + 4 * total_ints
+    del lplan, scratch
+    return {"codec": gc.codec_name(idx.codec), "ms_per_launch": ms, "ints_per_s": total_ints / (ms / 1e3),
+            "look_back_tiles": nlb, "tiles": nwork, "achieved_gbs": alg / (ms / 1e3) / 1e9,
+            "frac": alg / (ms / 1e3) / 1e9 / peak, "sample_verified": bool(ok), "sample_lists": len(sample)}
+
+
+def k_choice_rates(gc, gaps, lengths, off, dev, kinds):
+    """The headline lists encoded at k = 4 and at k = 32 per codec, each
+    decode tuned and timed (tune.choose_k): bits per int beside the rate,
+    and which k the autotuner would build the index with."""
+    import torch
+    from paper_1502_01916_gb300.tune import choose_k
+    d = torch.from_numpy(gaps.view(np.int32)).to(dev)
+    res = {}
+    for kind in kinds:
+        k, by_k = choose_k(kind, d, lengths, out_offsets=off[:-1], reps=2, register=False)
+        total = int(lengths.sum(dtype=np.uint64))
+        for v in by_k.values():
+            v["ints_per_s"] = total / (v["ms"] / 1e3)
+        res[gc.codec_name(gc.make_codec(kind, 32))] = {"chosen_k": k, "by_k": {str(kk): v for kk, v in by_k.items()}}
+    del d
+    torch.cuda.empty_cache()
     return res
 
 
