@@ -553,7 +553,8 @@ def main():
     # after the timed region
     extras = None
     if not a.no_extras:
-        extras = extra_rates(gc, lengths, off, gaps, dev, peak)
+        extras = extra_rates(gc, lengths, off, gaps, dev, peak,
+                             ids_ms={n: per_codec[n]["ms_per_launch"] for n in per_codec})
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
@@ -592,7 +593,7 @@ def main():
         dist.destroy_process_group()
 
 
-def extra_rates(gc, lengths, off, gaps, dev, peak, reps=5, nsample=300, seed=5):
+def extra_rates(gc, lengths, off, gaps, dev, peak, ids_ms=None, reps=5, nsample=300, seed=5):
     """Decode rates beyond the main workload, each on the same lists and
     output layout, timed like the main decode (CUDA events, library default
     launch shape) and checked on a random sample of lists:
@@ -600,7 +601,12 @@ def extra_rates(gc, lengths, off, gaps, dev, peak, reps=5, nsample=300, seed=5):
       decoded without the prefix sum (restore_docids = 0);
     - bp_k<k>: Group-PFD with no exception rows (zeta = 0), i.e. SIMD-BP128's
       fixed-width frames (Sec 6.3), on the d-gaps, docIDs restored; k = 4 is
-      the paper's 128-int frame, k = 32 the GPU layout."""
+      the paper's 128-int frame, k = 32 the GPU layout;
+    - tf_interleaved_<codec>: each list's docIDs and TFs from one index
+      (d-gap lists, then TF lists) in one launch, the two streams' tiles
+      planned alternately (gc_plan_interleave, restore_docids =
+      GC_RESTORE_PER_RECORD), against the two decodes apart (the headline's
+      docID decode + the tf_<codec> decode)."""
     import torch
     import synth
     rng = np.random.default_rng(seed)
@@ -638,7 +644,36 @@ def extra_rates(gc, lengths, off, gaps, dev, peak, reps=5, nsample=300, seed=5):
         idx = gc.encode_index(gc.make_codec(kind, 32, zeta=0.10), d, lengths, out_offsets=off[:-1])
         res[f"tf_{name}"] = run(idx, False, lambda i: tfs[int(off[i]):int(off[i]) + int(lengths[i])])
         del idx
-    del d, tfs
+    # docIDs and TFs interleaved: one index of both streams, one launch
+    L, N = int(off[-1]), len(lengths)
+    both = torch.cat([torch.from_numpy(gaps.view(np.int32)).to(dev), d])
+    del d
+    starts = np.concatenate([off[:-1], L + off[:-1]]).astype(np.uint64)
+    pairs = np.stack([np.arange(N), N + np.arange(N)], axis=1)
+    out2 = torch.empty(2 * L, dtype=torch.int32, device=dev)
+    for name, kind in (("simple", CODECS["simple"][0]), ("pfd", CODECS["pfd"][0])):
+        idx = gc.encode_index(gc.make_codec(kind, 32, zeta=0.10), both, np.concatenate([lengths, lengths]),
+                              out_offsets=starts)
+        plan = gc.plan_interleave(idx, pairs, starts.reshape(2, N).T)
+        scratch = torch.empty(gc.gc_decode_plan_scratch_size(int(plan.count[0].item())), dtype=torch.uint8,
+                              device=dev)
+        st = gc.new_status(dev)
+        ms = _timed(lambda: gc.decode_index(idx, out=out2, restore_docids=gc.RESTORE_PER_RECORD, scratch=scratch,
+                                            status=st, plan=plan, check=False), reps=reps)
+        gc.check_status(st, "interleaved decode")
+        got = gc.as_u32(out2)
+        ok = all(np.array_equal(got[int(off[i]):int(off[i]) + int(lengths[i])],
+                                np.cumsum(gaps[int(off[i]):int(off[i]) + int(lengths[i])], dtype=np.uint32)) and
+                 np.array_equal(got[L + int(off[i]):L + int(off[i]) + int(lengths[i])],
+                                tfs[int(off[i]):int(off[i]) + int(lengths[i])]) for i in ids)
+        alg = idx.compressed_bytes() + plan.nbytes() + 8 * total
+        sep = (ids_ms or {}).get(name)
+        res[f"tf_interleaved_{name}"] = {
+            "ms_per_launch": ms, "ints_per_s": 2 * total / (ms / 1e3), "achieved_gbs": alg / (ms / 1e3) / 1e9,
+            "frac": alg / (ms / 1e3) / 1e9 / peak, "sample_verified": bool(ok),
+            "apart_ms": (sep + res[f"tf_{name}"]["ms_per_launch"]) if sep else None}
+        del idx, plan, scratch
+    del both, out2, tfs
     d = torch.from_numpy(gaps.view(np.int32)).to(dev)
     for k in (4, 32):
         idx = gc.encode_index(gc.make_codec(CODECS["pfd"][0], k, zeta=0.0), d, lengths, out_offsets=off[:-1])

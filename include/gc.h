@@ -153,7 +153,9 @@ typedef struct gc_work {
  * (k words each) to stage from data_at; 19-23 the lane bit of the tile's
  * first row within the first staged word; 24-28 rows of the tile's first
  * unit before the tile; bit 29 base is valid; bit 30 a later tile without
- * a base takes its prefix from this tile. */
+ * a base takes its prefix from this tile; bit 31 (GC_WORK_RAW) the tile's
+ * values are written as they are, without the prefix sum, by a decode with
+ * restore_docids = GC_RESTORE_PER_RECORD. */
 enum {
   GC_WORK_VEC_SHIFT = 10,
   GC_WORK_BIT_SHIFT = 19,
@@ -161,6 +163,13 @@ enum {
   GC_WORK_HAS_BASE = 1u << 29,
   GC_WORK_PUBLISH = 1u << 30
 };
+#define GC_WORK_RAW 0x80000000u
+
+/* restore_docids of gc_decode_plan: 0 writes every tile's values (d-gaps,
+ * TFs), 1 restores docIDs (Sec 2.1.1) for every tile, and
+ * GC_RESTORE_PER_RECORD restores docIDs except in tiles whose record carries
+ * GC_WORK_RAW (the TF tiles of an interleaved plan, gc_plan_interleave). */
+#define GC_RESTORE_PER_RECORD 2
 
 /* Launch shape of the persistent decoder (NULL = the shape registered with
  * gc_set_launch, else the library default; a field left 0 takes its
@@ -342,6 +351,28 @@ gc_status gc_plan_select(const gc_codec* codec, const gc_list* d_lists, uint64_t
                          const uint64_t* d_out_offs, uint64_t nsel, const gc_tile* d_tile_pool,
                          uint64_t tile_pool_len, const uint8_t* d_ctrl_pool, uint64_t ctrl_pool_bytes,
                          gc_work* d_work, uint64_t work_cap, uint64_t* d_count, uint32_t* d_status, void* stream);
+
+/* The interleaved plan of a list's docID and term-frequency streams (the
+ * paper's TF columns, Sec 7.3, Tables VII and IX): for each pair p < npairs,
+ * index list d_sel_pairs[2p] holds a list's d-gaps and list
+ * d_sel_pairs[2p + 1] its TFs (the same number of ints). Their tiles are
+ * planned alternately -- d-gap tile 0, TF tile 0, d-gap tile 1, ... -- so one
+ * decode of the plan with restore_docids = GC_RESTORE_PER_RECORD writes the
+ * pair's docIDs to d_out_pairs[2p] and its TFs, without the prefix sum (the
+ * TF records carry GC_WORK_RAW), to d_out_pairs[2p + 1]: the two streams of
+ * a posting share the launch, the claim and, mostly, the block that decodes
+ * them. The d-gap tiles of a pair are not consecutive records, so none of
+ * them can take its prefix by look-back: every d-gap tile after a list's
+ * first must carry its skip entry (GC_TILE_BASE, which gc_encode_batch
+ * writes), else GC_ERR_UNSUPPORTED in d_status and the record is emptied. A
+ * pair whose lists differ in length reports GC_ERR_INVALID and plans
+ * nothing. Other arguments, results and errors as for gc_plan_select (2 *
+ * npairs entries); asynchronous on `stream`, graph-capturable. */
+gc_status gc_plan_interleave(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists,
+                             const uint32_t* d_sel_pairs, const uint64_t* d_out_pairs, uint64_t npairs,
+                             const gc_tile* d_tile_pool, uint64_t tile_pool_len, const uint8_t* d_ctrl_pool,
+                             uint64_t ctrl_pool_bytes, gc_work* d_work, uint64_t work_cap, uint64_t* d_count,
+                             uint32_t* d_status, void* stream);
 
 /* Scratch bytes gc_decode_plan needs for a plan of up to work_cap tiles. */
 gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes);

@@ -1455,9 +1455,11 @@ __device__ __noinline__ uint2 claim_records(const DecodeArgs& a, BlockSmem& h, u
 // from record 0 by following next, found by pointer doubling in five
 // rounds. v packs (lines | ring bytes / 16 << 11 | vectors << 32, the
 // vectors only at k = 4, whose sums then need 64 bits); returns the mask of
-// pack starts, P is each lane's inclusive sum of v and nxt its next_i.
-template <int K, class U>
-__device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_t& nxt) {
+// pack starts, P is each lane's inclusive sum of v and nxt its next_i. With
+// PER, a pack also never mixes records with and without GC_WORK_RAW (rawm:
+// one bit per record).
+template <int K, class U, bool PER = false>
+__device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_t& nxt, uint32_t rawm = 0) {
   const uint32_t lane = lane_id();
   P = warp_incl_sum(v);
   const U Pex = P - v;
@@ -1468,6 +1470,12 @@ __device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_
     const U s = __shfl_sync(kFull, P, j < 32 ? j : 31u) - Pex;
     bool fits = j < cnt && (uint32_t)(s & 2047u) <= 32u && (uint32_t)((s >> 11) & 0x1fffffu) * 16u <= (uint32_t)kPackCap;
     if constexpr (K == 4) fits = fits && (uint64_t)(s >> 32) <= (uint64_t)kPadVec4;
+    if constexpr (PER) {
+      // records lane .. j all raw or all not
+      const uint32_t jj = j < 31u ? j : 31u;
+      const uint32_t span = (jj == 31u ? 0xffffffffu : (2u << jj) - 1u) & ~((1u << lane) - 1u);
+      fits = fits && ((rawm & span) == 0u || (rawm & span) == span);
+    }
     if (fits) len += step;
   }
   nxt = lane < cnt ? lane + (len ? len : 1u) : 32u;
@@ -1492,7 +1500,7 @@ __device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_
 // pack its slot descriptor, then one arrival on the slot's mbarrier tells
 // its decoding warp, which copies the pack's bytes in itself. After the
 // last record, one empty pack per decoding warp tells it to stop.
-template <int KIND, int K>
+template <int KIND, int K, bool PER>
 __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t S) {
   const uint32_t lane = lane_id();
   uint64_t total = a.count[0];
@@ -1542,7 +1550,9 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
     const U v = valid ? (U)lines | (U)need16 << 11 | (K == 4 ? (U)((uint64_t)nv << 32) : (U)0) : (U)0;
     U P;
     uint32_t nxt;
-    const uint32_t starts = pack_starts<K, U>(v, cnt, P, nxt);
+    uint32_t rawm = 0;
+    if constexpr (PER) rawm = __ballot_sync(kFull, valid && (rec_of(h, rs).shape & GC_WORK_RAW));
+    const uint32_t starts = pack_starts<K, U, PER>(v, cnt, P, nxt, rawm);
     const U Pex = P - v;
     // each record's offset from its pack's start; at a pack's first record,
     // the pack's ring bytes / 16, records and lines
@@ -1578,7 +1588,7 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
       }
       if (failed) break;
       if (lane == 0) {
-        h.pk[r.ps] = (b * kChunk + sp) | ((pi >> 16) & 255u) << 8 | (pi >> 24) << 16;
+        h.pk[r.ps] = (b * kChunk + sp) | ((pi >> 16) & 255u) << 8 | (pi >> 24) << 16 | ((rawm >> sp) & 1u) << 24;
         h.prel[r.ps] = pad + B;
         h.ppos[r.ps] = off;
         mbar_arrive(&h.full[r.ps]);
@@ -1678,7 +1688,7 @@ __device__ __forceinline__ void copy_pack(const DecodeArgs& a, BlockSmem& h, uin
 // has placed it already; it never waits for the next pack before decoding
 // the current one (the staging warp may need the current pack's ring bytes
 // back first).
-template <int KIND, int K, bool RESTORE>
+template <int KIND, int K, bool RESTORE, bool PER>
 __device__ void consume(const DecodeArgs& a, BlockSmem& h, WarpSmem<K>& ws, uint8_t* ring, uint32_t w,
                         uint32_t W, uint32_t S) {
   const uint32_t lane = lane_id();
@@ -1717,9 +1727,22 @@ __device__ void consume(const DecodeArgs& a, BlockSmem& h, WarpSmem<K>& ws, uint
       cp_async_wait<0>();
     }
     __syncwarp();
-    const uint32_t s0 = d & 255u, np = (d >> 8) & 255u, nl = d >> 16;
-    if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
-    else decode_pack4<KIND, RESTORE>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+    const uint32_t s0 = d & 255u, np = (d >> 8) & 255u;
+    if constexpr (PER) {
+      // a pack of raw records (bit 24) decodes without the prefix sum
+      const uint32_t nl = (d >> 16) & 255u;
+      if ((d >> 24) & 1u) {
+        if constexpr (K == 32) decode_pack32<KIND, false>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+        else decode_pack4<KIND, false>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+      } else {
+        if constexpr (K == 32) decode_pack32<KIND, true>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+        else decode_pack4<KIND, true>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+      }
+    } else {
+      const uint32_t nl = d >> 16;
+      if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+      else decode_pack4<KIND, RESTORE>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+    }
     slot = nslot;
     par = npar;
     if (!pre) {
@@ -1741,7 +1764,7 @@ __device__ void consume(const DecodeArgs& a, BlockSmem& h, WarpSmem<K>& ws, uint
 
 // The persistent decoder: warp 0 stages, warps 1 .. W decode. Dynamic
 // shared memory: BlockSmem, W WarpSmem<K>, then the ring (a.ring_bytes).
-template <int KIND, int K, bool RESTORE>
+template <int KIND, int K, bool RESTORE, bool PER>
 __global__ void __launch_bounds__(Geo<K>::THREADS, 1) k_decode(DecodeArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   BlockSmem& h = *reinterpret_cast<BlockSmem*>(smem_raw);
@@ -1759,8 +1782,8 @@ __global__ void __launch_bounds__(Geo<K>::THREADS, 1) k_decode(DecodeArgs a) {
     fence_mbar_init();
   }
   __syncthreads();
-  if (warp == 0) produce<KIND, K>(a, h, W, S);
-  else consume<KIND, K, RESTORE>(a, h, ws[warp - 1], ring, warp - 1, W, S);
+  if (warp == 0) produce<KIND, K, PER>(a, h, W, S);
+  else consume<KIND, K, RESTORE, PER>(a, h, ws[warp - 1], ring, warp - 1, W, S);
 }
 
 // --------------------------------------------------------------- the plan
@@ -1781,6 +1804,7 @@ struct PlanArgs {
   uint64_t cap;
   unsigned long long* count;  // [0] records, [1] records needing look-back
   uint32_t* status;
+  uint32_t pairs;             // interleaved plan: entries 2i (docIDs) and 2i + 1 (raw) tile by tile
 };
 
 // The descriptor of planned list i (a selected list takes its output offset
@@ -1803,21 +1827,29 @@ __device__ __forceinline__ gc_list plan_list(const PlanArgs& a, uint64_t i) {
 __global__ void k_plan_reserve(PlanArgs a) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = lane_id();
+  // an interleaved plan reserves per pair of entries (2i, 2i + 1), two
+  // records per tile
+  const uint64_t units = a.pairs ? a.nlists / 2 : a.nlists;
+  const uint32_t per = a.pairs ? 2u : 1u;
   uint64_t nt = 0;
-  if (i < a.nlists) {
-    const uint64_t n = plan_list(a, i).n;
+  if (i < units) {
+    const uint64_t n = plan_list(a, per * i).n;
     const uint64_t R = (n + a.k - 1) / a.k;
     const uint64_t tr = kTileInts / a.k;
-    nt = (R + tr - 1) / tr;
+    nt = per * ((R + tr - 1) / tr);
+    if (a.pairs && plan_list(a, per * i + 1).n != n) {
+      report(a.status, GC_ERR_INVALID, (uint32_t)i);
+      nt = 0;
+    }
   }
   const uint64_t incl = warp_incl_sum(nt);
   unsigned long long b = 0;
   if (lane == 31) b = atomicAdd(a.count, (unsigned long long)incl);
   const uint64_t base = __shfl_sync(kFull, b, 31) + incl - nt;
   const bool fits = base + nt <= a.cap;
-  if (i < a.nlists && !fits) report(a.status, GC_ERR_NOSPACE, (uint32_t)i);
+  if (i < units && !fits) report(a.status, GC_ERR_NOSPACE, (uint32_t)i);
   if (!a.lists) return;
-  for (uint32_t m = __ballot_sync(kFull, i < a.nlists && nt > 0); m; m &= m - 1) {
+  for (uint32_t m = __ballot_sync(kFull, i < units && nt > 0); m; m &= m - 1) {
     const uint32_t src = __ffs(m) - 1;
     const uint64_t lb0 = __shfl_sync(kFull, base, src);
     const uint64_t ln = __shfl_sync(kFull, nt, src);
@@ -1825,8 +1857,8 @@ __global__ void k_plan_reserve(PlanArgs a) {
     const bool lf = __shfl_sync(kFull, fits, src);
     for (uint64_t t = lane; t < ln && lb0 + t < a.cap; t += 32) {
       gc_work* w = a.work + lb0 + t;
-      w->tile = (uint32_t)t;
-      w->list = lf ? lid : 0xffffffffu;
+      w->tile = (uint32_t)(t / per);
+      w->list = lf ? per * lid + (uint32_t)(t % per) : 0xffffffffu;
     }
   }
 }
@@ -1956,9 +1988,17 @@ __global__ void k_plan_fill(PlanArgs a) {
     a.work[i] = empty;
     return;
   }
-  const bool has_base = (r0.flags & GC_TILE_BASE) != 0;
-  const bool publish = !last && !(r1.flags & GC_TILE_BASE);
-  if (t > 0 && !has_base) {
+  // an interleaved plan: odd entries are written raw; an even entry's tiles
+  // are not consecutive records, so each one after the first needs its base
+  const bool raw = a.pairs && (w.list & 1u);
+  const bool has_base = (r0.flags & GC_TILE_BASE) != 0 && !raw;
+  const bool publish = !a.pairs && !last && !(r1.flags & GC_TILE_BASE);
+  if (a.pairs && !raw && t > 0 && !has_base) {
+    report(a.status, GC_ERR_UNSUPPORTED, a.sel ? a.sel[w.list] : w.list);
+    a.work[i] = empty;
+    return;
+  }
+  if (!raw && t > 0 && !has_base) {
     // warp-aggregated count of records that take their prefix by look-back
     atomicAdd(a.count + 1, 1ull);
   }
@@ -1976,7 +2016,7 @@ __global__ void k_plan_fill(PlanArgs a) {
   if (a.sel) w.list = a.sel[w.list];  // records name the index's list
   w.shape = (nint - 1) | ((uint32_t)(v1 - v0) << GC_WORK_VEC_SHIFT) | ((uint32_t)(first_bit & 31) << GC_WORK_BIT_SHIFT) |
             ((r0.row_skip & 31u) << GC_WORK_SKIP_SHIFT) | (has_base ? (uint32_t)GC_WORK_HAS_BASE : 0u) |
-            (publish ? (uint32_t)GC_WORK_PUBLISH : 0u);
+            (publish ? (uint32_t)GC_WORK_PUBLISH : 0u) | (raw ? (uint32_t)GC_WORK_RAW : 0u);
   a.work[i] = w;
 }
 
@@ -2035,9 +2075,9 @@ struct Registered {
 };
 Registered g_reg[64][4][2][2];
 
-template <int KIND, int K, bool RESTORE>
+template <int KIND, int K, bool RESTORE, bool PER>
 gc_status launch_t(DecodeArgs a, Shape sh, uint64_t work, cudaStream_t s) {
-  auto fn = k_decode<KIND, K, RESTORE>;
+  auto fn = k_decode<KIND, K, RESTORE, PER>;
   // per device: the opted-in shared-memory size of this kernel (it only
   // grows) and the occupancy of the last shape asked for
   static size_t smem_set[64] = {};
@@ -2095,12 +2135,12 @@ gc_status launch_t(DecodeArgs a, Shape sh, uint64_t work, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? GC_OK : GC_ERR_CUDA;
 }
 
-template <bool RESTORE>
+template <bool RESTORE, bool PER>
 gc_status launch_r(uint32_t kind, uint32_t k, const DecodeArgs& a, Shape sh, uint64_t work, cudaStream_t s) {
 #define GC_DISPATCH(KIND)                                                 \
   if (kind == KIND) {                                                      \
-    if (k == 4) return launch_t<KIND, 4, RESTORE>(a, sh, work, s);         \
-    return launch_t<KIND, 32, RESTORE>(a, sh, work, s);                    \
+    if (k == 4) return launch_t<KIND, 4, RESTORE, PER>(a, sh, work, s);    \
+    return launch_t<KIND, 32, RESTORE, PER>(a, sh, work, s);               \
   }
   GC_DISPATCH(GC_SIMPLE)
   GC_DISPATCH(GC_SCHEME)
@@ -2110,9 +2150,11 @@ gc_status launch_r(uint32_t kind, uint32_t k, const DecodeArgs& a, Shape sh, uin
   return GC_ERR_INVALID;
 }
 
-gc_status launch_decode(uint32_t kind, uint32_t k, bool restore, const DecodeArgs& a, Shape sh, uint64_t work,
+// restore: 0 values, 1 docIDs, GC_RESTORE_PER_RECORD docIDs except GC_WORK_RAW records
+gc_status launch_decode(uint32_t kind, uint32_t k, int restore, const DecodeArgs& a, Shape sh, uint64_t work,
                         cudaStream_t s) {
-  return restore ? launch_r<true>(kind, k, a, sh, work, s) : launch_r<false>(kind, k, a, sh, work, s);
+  if (restore == GC_RESTORE_PER_RECORD) return launch_r<true, true>(kind, k, a, sh, work, s);
+  return restore ? launch_r<true, false>(kind, k, a, sh, work, s) : launch_r<false, false>(kind, k, a, sh, work, s);
 }
 
 // A caller's shape over the library default for this k (every field 0 =
@@ -2148,7 +2190,8 @@ gc_status launch_shape(const gc_codec& c, const gc_launch* l, Shape* sh, int res
 gc_status plan_impl(const gc_codec& c, const gc_list* lists, const gc_list* one, uint64_t nlists,
                     const gc_tile* tiles, uint64_t ntiles, const uint8_t* ctrl_pool, uint64_t ctrl_pool_bytes,
                     gc_work* work, uint64_t cap, uint64_t* count, uint32_t* status, cudaStream_t s,
-                    const uint32_t* sel = nullptr, const uint64_t* outs = nullptr, uint64_t nall = 0) {
+                    const uint32_t* sel = nullptr, const uint64_t* outs = nullptr, uint64_t nall = 0,
+                    bool pairs = false) {
   if (cudaMemsetAsync(count, 0, 16, s) != cudaSuccess) return GC_ERR_CUDA;
   if (nlists == 0) return GC_OK;
   PlanArgs a = {};
@@ -2170,6 +2213,7 @@ gc_status plan_impl(const gc_codec& c, const gc_list* lists, const gc_list* one,
   a.cap = cap;
   a.count = reinterpret_cast<unsigned long long*>(count);
   a.status = status;
+  a.pairs = pairs ? 1u : 0u;
   k_plan_reserve<<<(unsigned)((nlists + 255) / 256), 256, 0, s>>>(a);
   gc_host::count_launch();
   if (cap) {
@@ -2234,7 +2278,7 @@ gc_status decode_plan_impl(const gc_codec& c, const gc_work* work, const uint64_
   a.cg = c.cg;
   a.ld = c.ld;
   a.status = status;
-  return launch_decode(c.kind, c.k, restore != 0, a, sh, work_cap, s);
+  return launch_decode(c.kind, c.k, restore, a, sh, work_cap, s);
 }
 
 uint64_t tiles_of(const gc_codec& c, uint64_t n) {
@@ -2395,6 +2439,21 @@ gc_status gc_plan_select(const gc_codec* codec, const gc_list* d_lists, uint64_t
   if (((uintptr_t)d_work & 15) != 0) return GC_ERR_INVALID;
   return plan_impl(*codec, d_lists, nullptr, nsel, d_tile_pool, tile_pool_len, d_ctrl_pool, ctrl_pool_bytes, d_work,
                    work_cap, d_count, d_status, (cudaStream_t)stream, d_sel, d_out_offs, nlists);
+}
+
+gc_status gc_plan_interleave(const gc_codec* codec, const gc_list* d_lists, uint64_t nlists,
+                             const uint32_t* d_sel_pairs, const uint64_t* d_out_pairs, uint64_t npairs,
+                             const gc_tile* d_tile_pool, uint64_t tile_pool_len, const uint8_t* d_ctrl_pool,
+                             uint64_t ctrl_pool_bytes, gc_work* d_work, uint64_t work_cap, uint64_t* d_count,
+                             uint32_t* d_status, void* stream) {
+  gc_host::reset_launches();
+  gc_status st = gc_host::check_codec(codec);
+  if (st != GC_OK) return st;
+  if (!d_count || (npairs && (!d_lists || !d_sel_pairs || !d_out_pairs || !d_work))) return GC_ERR_INVALID;
+  if (nlists > 0xffffffffull || npairs > 0x7fffffffull || work_cap > 0xffffffffull) return GC_ERR_UNSUPPORTED;
+  if (((uintptr_t)d_work & 15) != 0) return GC_ERR_INVALID;
+  return plan_impl(*codec, d_lists, nullptr, 2 * npairs, d_tile_pool, tile_pool_len, d_ctrl_pool, ctrl_pool_bytes,
+                   d_work, work_cap, d_count, d_status, (cudaStream_t)stream, d_sel_pairs, d_out_pairs, nlists, true);
 }
 
 gc_status gc_decode_plan_scratch_size(uint64_t work_cap, uint64_t* bytes) {

@@ -38,6 +38,7 @@ __all__ = [
     "build_tiles", "decode_paper", "encode_index", "decode_index", "new_status", "check_status",
     "as_u32", "codec_name", "gc_paper_bytes", "gc_pack_paper", "gc_unpack_paper", "pack_paper", "unpack_paper",
     "gc_set_launch", "gc_get_launch", "gc_decode_plan_host_buffer_size", "gc_decode_plan_host", "gc_shutdown",
+    "gc_plan_interleave", "RESTORE_PER_RECORD", "plan_interleave", "WORK_RAW",
 ]
 
 SIMPLE, SCHEME, AFOR, PFD = 0, 1, 2, 3
@@ -93,7 +94,7 @@ class gc_work(ctypes.Structure):
 
 TILE_BASE = 1
 WORK_VEC_SHIFT, WORK_BIT_SHIFT, WORK_SKIP_SHIFT = 10, 19, 24
-WORK_HAS_BASE, WORK_PUBLISH = 1 << 29, 1 << 30
+WORK_HAS_BASE, WORK_PUBLISH, WORK_RAW = 1 << 29, 1 << 30, 1 << 31
 TILE_DTYPE = np.dtype([("lane_bit", "<u8"), ("ctrl_bit", "<u8"), ("exc_off", "<u4"), ("row_skip", "<u4"),
                        ("base", "<u4"), ("flags", "<u4")])
 LIST_DTYPE = np.dtype([("ctrl_off", "<u8"), ("data_off", "<u8"), ("out_off", "<u8"), ("n", "<u4"),
@@ -147,6 +148,7 @@ def load():
                                      ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
             "gc_plan_batch": (_I, [_CP, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V]),
             "gc_plan_select": (_I, [_CP, _V, _U64, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V]),
+            "gc_plan_interleave": (_I, [_CP, _V, _U64, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _V, _V, _V]),
             "gc_decode_plan_scratch_size": (_I, [_U64, _U64P]),
             "gc_decode_plan": (_I, [_CP, _V, _V, _U64, _V, _U64, _V, _U64, _V, _U64, _I,
                                     ctypes.POINTER(gc_launch), _V, _U64, _V, _V]),
@@ -196,6 +198,10 @@ def _n(t, esize: int, what: str) -> int:
     if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.element_size() != esize:
         raise ValueError(f"{what}: expected a contiguous CUDA tensor of {esize}-byte elements")
     return t.numel()
+
+
+def _restore(r) -> int:
+    return RESTORE_PER_RECORD if (not isinstance(r, bool) and r == RESTORE_PER_RECORD) else int(bool(r))
 
 
 def _stream(stream=None) -> int:
@@ -339,6 +345,20 @@ def gc_plan_select(codec, d_lists, nlists, d_sel, d_out_offs, nsel, d_tile_pool,
            "gc_plan_select")
 
 
+def gc_plan_interleave(codec, d_lists, nlists, d_sel_pairs, d_out_pairs, npairs, d_tile_pool, d_ctrl_pool, d_work,
+                       d_count, d_status, stream=None):
+    tile_len = _n(d_tile_pool, 1, "d_tile_pool") // TILE_BYTES if d_tile_pool is not None else 0
+    if npairs and (_n(d_sel_pairs, 4, "d_sel_pairs") < 2 * npairs or _n(d_out_pairs, 8, "d_out_pairs") < 2 * npairs):
+        raise ValueError("d_sel_pairs / d_out_pairs hold fewer than 2 * npairs entries")
+    _check(load().gc_plan_interleave(ctypes.byref(codec), _ptr(d_lists), nlists, _ptr(d_sel_pairs),
+                                     _ptr(d_out_pairs), npairs, _ptr(d_tile_pool), tile_len, _ptr(d_ctrl_pool),
+                                     _n(d_ctrl_pool, 1, "d_ctrl_pool"), _ptr(d_work), _n(d_work, 1, "d_work") // WORK_BYTES,
+                                     _ptr(d_count), _ptr(d_status), _stream(stream)), "gc_plan_interleave")
+
+
+RESTORE_PER_RECORD = 2
+
+
 def gc_decode_plan_scratch_size(work_cap: int) -> int:
     b = _U64()
     _check(load().gc_decode_plan_scratch_size(work_cap, ctypes.byref(b)), "gc_decode_plan_scratch_size")
@@ -347,12 +367,13 @@ def gc_decode_plan_scratch_size(work_cap: int) -> int:
 
 def gc_decode_plan(codec, d_work, d_count, d_ctrl_pool, d_data_pool, d_out_pool, restore_docids, launch, d_scratch,
                    d_status, stream=None):
+    """restore_docids: 0 values, 1 docIDs, RESTORE_PER_RECORD docIDs except raw (TF) records."""
     lp = ctypes.byref(launch) if launch is not None else None
     _check(load().gc_decode_plan(ctypes.byref(codec), _ptr(d_work), _ptr(d_count),
                                  _n(d_work, 1, "d_work") // WORK_BYTES, _ptr(d_ctrl_pool),
                                  _n(d_ctrl_pool, 1, "d_ctrl_pool"), _ptr(d_data_pool),
                                  _n(d_data_pool, 4, "d_data_pool"), _ptr(d_out_pool), _n(d_out_pool, 4, "d_out_pool"),
-                                 int(bool(restore_docids)), lp, _ptr(d_scratch), _n(d_scratch, 1, "d_scratch"),
+                                 _restore(restore_docids), lp, _ptr(d_scratch), _n(d_scratch, 1, "d_scratch"),
                                  _ptr(d_status), _stream(stream)),
            "gc_decode_plan")
 
@@ -420,7 +441,7 @@ def gc_decode_plan_host(codec, h_work, nwork, h_ctrl_pool, h_data_pool, h_out_po
     op, on = _h(h_out_pool, 4, "h_out_pool")
     lp = ctypes.byref(launch) if launch is not None else None
     _check(load().gc_decode_plan_host(ctypes.byref(codec), wp, nwork, cp, cn, dp, dn, op, on,
-                                      int(bool(restore_docids)), lp, _ptr(d_buffers), _n(d_buffers, 1, "d_buffers"),
+                                      _restore(restore_docids), lp, _ptr(d_buffers), _n(d_buffers, 1, "d_buffers"),
                                       _ptr(d_status), _stream(stream)), "gc_decode_plan_host")
 
 
@@ -660,6 +681,34 @@ class Plan:
 
     def nbytes(self) -> int:
         return self.work.numel()
+
+
+def tiles_of(codec: gc_codec, lengths) -> np.ndarray:
+    """Tiles (1024 ints, whole rows of k) of lists of these lengths."""
+    rows = (np.asarray(lengths, np.int64) + codec.k - 1) // codec.k
+    tr = TILE_INTS // codec.k
+    return (rows + tr - 1) // tr
+
+
+def plan_interleave(index: Index, pairs, out_pairs, status=None, stream=None) -> Plan:
+    """The interleaved plan (gc_plan_interleave) of (d-gap list, TF list)
+    pairs of `index`: pairs is (npairs, 2) list indexes, out_pairs (npairs,
+    2) output offsets (docIDs, TFs). Decode it with decode_index(...,
+    restore_docids=RESTORE_PER_RECORD, plan=...)."""
+    dev = index.data.device
+    pairs = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
+    outs = np.ascontiguousarray(out_pairs, np.uint64).reshape(-1, 2)
+    ntile = tiles_of(index.codec, index.lengths)
+    cap = max(1, 2 * int(ntile[pairs[:, 0]].sum())) if len(pairs) else 1
+    work = torch.empty(cap * WORK_BYTES, dtype=torch.uint8, device=dev)
+    count = torch.zeros(2, dtype=torch.int64, device=dev)
+    d_sel = torch.from_numpy(pairs.reshape(-1).view(np.int32).copy()).to(dev)
+    d_out = torch.from_numpy(outs.reshape(-1).view(np.int64).copy()).to(dev)
+    st = new_status(dev) if status is None else status
+    gc_plan_interleave(index.codec, index.lists, index.nlists, d_sel, d_out, len(pairs), index.tiles, index.ctrl, work,
+                       count, st, stream)
+    check_status(st, "gc_plan_interleave")
+    return Plan(work, count)
 
 
 def plan_index(index: Index, status=None, stream=None) -> Plan:
