@@ -110,6 +110,7 @@ struct __align__(128) WarpSmem {
   uint32_t ibase[32];                    // item: its docID base
   uint32_t irec[32];                     // item: its record slot
   uint32_t lnv[32];                      // line: ints it holds
+  uint32_t emask[32];                    // (Group-PFD, k = 32) line: its exception columns
 };
 
 struct DecodeArgs {
@@ -994,10 +995,13 @@ __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4
 // chunks fall in eight different 16-byte bank groups. Each value is a
 // funnel shift and a mask; with SUM the running sum (the prefix within the
 // line) replaces it, and R ends as the line's total. The results go to the
-// line's 16-byte chunks in the transpose buffer, chunk c at c ^ swz.
-template <int KIND, bool SUM>
+// line's 16-byte chunks in the transpose buffer, chunk c at c ^ swz. With
+// PATCH, the Group-PFD exceptions of the line are already in the buffer at
+// their own places and column j's value is taken from there where bit j of
+// em is set (Sec 6.2 decoding Step 3), before the running sum.
+template <int KIND, bool SUM, bool PATCH = false>
 __device__ __forceinline__ void extract_line32(const uint4* P, uint32_t sh, uint32_t msk, bool cross, uint4* T,
-                                               uint32_t swz, uint32_t& R) {
+                                               uint32_t swz, uint32_t& R, uint32_t em = 0) {
   R = 0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -1008,6 +1012,16 @@ __device__ __forceinline__ void extract_line32(const uint4* P, uint32_t sh, uint
     uint32_t v1 = __funnelshift_r(lo.y, hi.y, sh) & msk;
     uint32_t v2 = __funnelshift_r(lo.z, hi.z, sh) & msk;
     uint32_t v3 = __funnelshift_r(lo.w, hi.w, sh) & msk;
+    if (PATCH) {
+      const uint32_t m4 = (em >> (4 * c)) & 15u;
+      if (m4) {
+        const uint4 x = T[c ^ swz];
+        v0 = (m4 & 1u) ? x.x : v0;
+        v1 = (m4 & 2u) ? x.y : v1;
+        v2 = (m4 & 4u) ? x.z : v2;
+        v3 = (m4 & 8u) ? x.w : v3;
+      }
+    }
     if (SUM) {
       v0 += R;
       v1 += v0;
@@ -1078,14 +1092,15 @@ __device__ __forceinline__ void parse_simple_pack32(const DecodeArgs& a, const B
   if (!ok) report(a.status, GC_ERR_CORRUPT, w.list);
 }
 
-// Group-PFD, k = 32: one tile's exceptions overwrite their slots in the
+// Group-PFD, k = 32: one tile's exceptions go to their slots' places in the
 // pack's line-major buffer (line l at words 32 l .. 32 l + 31, its 16-byte
-// chunk c at chunk c ^ (l & 7)): e 16-bit positions at rp, then e values of
-// wb bytes (Sec 6.2, decoding Step 3); the tile's first line is hl, its
-// frame holds lim ints. A position outside the frame, or one that does not
-// increase on the one before, is reported.
-__device__ __forceinline__ void pfd_patch(const DecodeArgs& a, uint32_t* tb, uint32_t lane, uint32_t hl, uint32_t e,
-                                          uint32_t lim, uint32_t wb, const uint8_t* rp, uint32_t list) {
+// chunk c at chunk c ^ (l & 7)), and each one's column to its line's mask
+// in em: e 16-bit positions at rp, then e values of wb bytes (Sec 6.2,
+// decoding Step 3); the tile's first line is hl, its frame holds lim ints.
+// A position outside the frame, or one that does not increase on the one
+// before, is reported (and not patched).
+__device__ __forceinline__ void pfd_patch(const DecodeArgs& a, uint32_t* tb, uint32_t* em, uint32_t lane, uint32_t hl,
+                                          uint32_t e, uint32_t lim, uint32_t wb, const uint8_t* rp, uint32_t list) {
   const uint8_t* vp = rp + (size_t)e * 2;
   uint32_t last = 0;  // the position before this round's first
 #pragma unroll 1
@@ -1106,6 +1121,7 @@ __device__ __forceinline__ void pfd_patch(const DecodeArgs& a, uint32_t* tb, uin
     if (wb > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
     const uint32_t line = hl + (pos >> 5), col = pos & 31u;
     tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
+    atomicOr(em + line, 1u << col);
   }
 }
 
@@ -1177,10 +1193,10 @@ __device__ __forceinline__ void parse_pfd_pack32(const DecodeArgs& a, const Bloc
   x.list = w.list;
 }
 
-// Group-PFD, k = 32: the exceptions of every tile of the pack over their
-// slots.
-__device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, uint32_t* tb, uint32_t lane, uint32_t heads,
-                                                 const PfdExc& x) {
+// Group-PFD, k = 32: the exceptions of every tile of the pack at their
+// slots' places, and every line's exception columns.
+__device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, uint32_t* tb, uint32_t* em, uint32_t lane,
+                                                 uint32_t heads, const PfdExc& x) {
   for (uint32_t hm = heads; hm; hm &= hm - 1) {
     const uint32_t hl = __ffs(hm) - 1;  // the tile's first line
     const uint32_t e = __shfl_sync(kFull, x.e, hl);
@@ -1188,7 +1204,7 @@ __device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, uint32_t* 
     const uint32_t wb = __shfl_sync(kFull, x.wb, hl);
     const uint32_t list = __shfl_sync(kFull, x.list, hl);
     const uint8_t* rp = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, (unsigned long long)x.rp, hl));
-    pfd_patch(a, tb, lane, hl, e, lim, wb, rp, list);
+    pfd_patch(a, tb, em, lane, hl, e, lim, wb, rp, list);
   }
 }
 
@@ -1277,30 +1293,20 @@ __device__ void decode_pack32(const DecodeArgs& a, const BlockSmem& h, WarpSmem<
   if (KIND != GC_PFD) {
     extract_line32<KIND, RESTORE>(P, sh, msk, cross, T, swz, R);
   } else {
-    // Group-PFD: without exceptions in the pack, the running sums at once;
-    // with them, the slots' values, the exceptions over them, then the
-    // running sum over the patched line
+    // Group-PFD: when a tile of the pack has exceptions, they first go to
+    // their places in the buffer and their columns to each line's mask;
+    // one extraction then takes a masked column's value from the buffer
+    // instead of its slot (no mask: every value from its slot)
     const bool pp = (__ballot_sync(kFull, px.e != 0) & t.heads) != 0;
-    if (RESTORE && !pp) extract_line32<KIND, true>(P, sh, msk, cross, T, swz, R);
-    else extract_line32<KIND, false>(P, sh, msk, cross, T, swz, R);
+    uint32_t em = 0;
     if (pp) {
+      ws.emask[lane] = 0;
       __syncwarp();
-      pfd_patch_pack32(a, ws.tb, lane, t.heads, px);
+      pfd_patch_pack32(a, ws.tb, ws.emask, lane, t.heads, px);
       __syncwarp();
+      em = ws.emask[lane];
     }
-    if (RESTORE && pp) {
-      R = 0;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        uint4 v = T[c ^ swz];
-        v.x += R;
-        v.y += v.x;
-        v.z += v.y;
-        v.w += v.z;
-        R = v.w;
-        T[c ^ swz] = v;
-      }
-    }
+    extract_line32<KIND, RESTORE, true>(P, sh, msk, cross, T, swz, R, em);
   }
   // the pack's staged bytes are read: give its ring bytes back
   __syncwarp();
@@ -1638,10 +1644,12 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // A decoding warp copies a pack's bytes into the ring (the places the
-// staging warp gave its records), tile by tile: lane j takes 16-byte chunks
-// j, j + 32, ... of the tile's data vectors (at the ring's pitch), then of
-// its control and exception windows. Each lane's copies are its own
-// cp.async group once committed.
+// staging warp gave its records), tile by tile: lane j takes 16-byte chunk
+// j % C of data vectors j / C, j / C + 32 / C, ... (C chunks per vector,
+// each vector at the ring's pitch), then chunks j, j + 32, ... of the
+// tile's control window and exception window, which lie back to back after
+// its vectors. Each lane's copies are its own cp.async group once
+// committed.
 template <int K>
 __device__ __forceinline__ void copy_pack(const DecodeArgs& a, BlockSmem& h, uint8_t* ring, uint32_t d, uint32_t slot) {
   const uint32_t lane = lane_id();
@@ -1653,31 +1661,25 @@ __device__ __forceinline__ void copy_pack(const DecodeArgs& a, BlockSmem& h, uin
   }
   __syncwarp();
   constexpr uint32_t CPV = K * 4 / 16;  // 16-byte chunks per data vector
+  constexpr uint32_t VPS = 32 / CPV;    // vectors per step of the warp
   for (uint32_t p = 0; p < np; ++p) {
     const uint32_t s = rslot(s0 + p);
-    const uint32_t nvp = h.fvecs[s], cbp = h.cst[s], xbp = h.xst[s];
-    const uint32_t dch = nvp * CPV, cch = cbp >> 4, tch = dch + cch + (xbp >> 4);
-    if (tch == 0) continue;
+    const uint32_t nvp = h.fvecs[s], ch = (h.cst[s] + h.xst[s]) >> 4;
     const gc_work& w = rec_of(h, s);
     const uint32_t atp = h.at[s];
-    const uint8_t* dsrc = reinterpret_cast<const uint8_t*>(a.data_pool + w.data_at);
-    const uint8_t* csrc = a.ctrl_pool + (w.ctrl_at + w.win_at);
-    const uint8_t* xsrc = a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull);
-    for (uint32_t j = lane; j < tch; j += 32) {
-      const uint8_t* src;
-      uint32_t dst;
-      if (j < dch) {
-        const uint32_t v = j / CPV, c = j % CPV;
-        dst = atp + v * (uint32_t)Geo<K>::VB + 16 * c;
-        src = dsrc + (size_t)v * (K * 4) + 16 * c;
-      } else if (j < dch + cch) {
-        dst = atp + nvp * (uint32_t)Geo<K>::VB + 16 * (j - dch);
-        src = csrc + 16 * (j - dch);
-      } else {
-        dst = atp + nvp * (uint32_t)Geo<K>::VB + cbp + 16 * (j - dch - cch);
-        src = xsrc + 16 * (j - dch - cch);
-      }
-      cp_async16(ring + dst, src);
+    uint32_t v = lane / CPV;
+    const uint32_t c16 = 16 * (lane % CPV);
+    uint8_t* dst = ring + atp + v * (uint32_t)Geo<K>::VB + c16;
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(a.data_pool + w.data_at) + (size_t)v * (K * 4) + c16;
+#pragma unroll 1
+    for (; v < nvp; v += VPS, dst += VPS * Geo<K>::VB, src += VPS * K * 4) cp_async16(dst, src);
+    if (ch) {
+      const uint32_t cch = h.cst[s] >> 4;
+      const uint8_t* csrc = a.ctrl_pool + (w.ctrl_at + w.win_at);
+      const uint8_t* xsrc = a.ctrl_pool + ((w.ctrl_at + w.exc_at) & ~15ull) - 16ull * cch;
+      uint8_t* cdst = ring + atp + nvp * (uint32_t)Geo<K>::VB;
+#pragma unroll 1
+      for (uint32_t j = lane; j < ch; j += 32) cp_async16(cdst + 16 * j, (j < cch ? csrc : xsrc) + 16 * j);
     }
   }
 }

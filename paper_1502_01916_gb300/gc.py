@@ -38,7 +38,7 @@ __all__ = [
     "build_tiles", "decode_paper", "encode_index", "decode_index", "new_status", "check_status",
     "as_u32", "codec_name", "gc_paper_bytes", "gc_pack_paper", "gc_unpack_paper", "pack_paper", "unpack_paper",
     "gc_set_launch", "gc_get_launch", "gc_decode_plan_host_buffer_size", "gc_decode_plan_host", "gc_shutdown",
-    "gc_plan_interleave", "RESTORE_PER_RECORD", "plan_interleave", "WORK_RAW",
+    "gc_plan_interleave", "RESTORE_PER_RECORD", "plan_interleave", "WORK_RAW", "tiles_of",
 ]
 
 SIMPLE, SCHEME, AFOR, PFD = 0, 1, 2, 3
