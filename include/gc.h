@@ -60,7 +60,9 @@ enum { GC_LD_BINARY = 0, GC_LD_CU = 1, GC_LD_IU = 2 };
  *         only with cg 4 or 8, Sec 5.2.1(a)).
  *   pfd_exc_rows: Group-PFD, the most rows of a 32-row frame that may hold
  *         exceptions (the ratio threshold zeta of Sec 6.2 Step 2 as an
- *         integer; gc_pfd_rows_for_zeta converts). */
+ *         integer; gc_pfd_rows_for_zeta converts). A list's last frame of
+ *         r < 32 rows may hold floor(pfd_exc_rows * r / 32) (its own
+ *         exception ratio stays below zeta). */
 typedef struct gc_codec {
   uint32_t kind;
   uint32_t k;

@@ -197,7 +197,8 @@ def afor_partition(maxarr, k: int) -> np.ndarray:
 
 def pfd_rows_for_zeta(zeta: float) -> int:
     """The ratio rule of Section 6.2 as an integer: the most exception rows
-    (out of a frame's 32) whose ratio stays strictly below zeta."""
+    (out of a frame's 32) whose ratio stays strictly below zeta. A list's
+    last frame of r < 32 rows may have this many times r / 32, rounded down."""
     return int(_load().orc_pfd_rows_for_zeta(float(zeta)))
 
 

@@ -543,7 +543,9 @@ static int pfd_encode(const uint32_t* g, uint64_t n, uint32_t k, uint32_t max_ro
   for (uint64_t f = 0; f < nf; ++f) {
     const uint64_t r0 = f * PFD_FRAME_ROWS;
     const uint64_t rows = (R - r0) < PFD_FRAME_ROWS ? (R - r0) : PFD_FRAME_ROWS;
-    const uint32_t b = orc_pfd_frame_b(mx + r0, rows, max_rows);
+    /* the exception ratio is the frame's own: a list's last frame of fewer
+     * than 32 rows may have the whole frame's budget scaled to its rows */
+    const uint32_t b = orc_pfd_frame_b(mx + r0, rows, (uint32_t)((uint64_t)max_rows * rows / PFD_FRAME_ROWS));
     uint32_t e = 0, vmax = 0;
     for (uint64_t r = r0; r < r0 + rows; ++r) {
       if ((uint64_t)mx[r] <= mask64(b)) continue;

@@ -287,9 +287,12 @@ __global__ void k_pfd_frames(Enc e) {
   const uint64_t r0 = f * kPfdFrameRows;
   const uint32_t frows = (uint32_t)min64(kPfdFrameRows, R - r0);
   const uint32_t myb = lane < frows ? e.eb[e.rowbase[L] + r0 + lane] : 0u;
+  // the frame's own exception ratio: a list's last frame of fewer rows may
+  // have the 32-row budget scaled to its rows (rounded down)
+  const uint32_t budget = e.T * frows / kPfdFrameRows;
   uint32_t b = 0;
   for (; b < 32; ++b)
-    if ((uint32_t)__popc(__ballot_sync(kFull, myb > b)) <= e.T) break;
+    if ((uint32_t)__popc(__ballot_sync(kFull, myb > b)) <= budget) break;
   // exceptions: ints above 2^b - 1 in rows whose max is above it
   uint32_t rowsx = __ballot_sync(kFull, myb > b);
   uint32_t cnt = 0, vmax = 0;

@@ -8,6 +8,8 @@ import itertools
 import os
 from fractions import Fraction
 
+import math
+
 import numpy as np
 import pytest
 
@@ -331,23 +333,31 @@ def _pfd_headers(ctrl, nf):
 
 @pytest.mark.parametrize("k,zeta,seed", [(4, 0.1, 0), (4, 0.3, 1), (4, 0.01, 2), (32, 0.1, 3),
                                          (32, 0.3, 4), (4, 0.1, 5)])
-def test_pfd_b_minimal_and_exceptions(k, zeta, seed):
-    """b is the minimum width whose exception rows stay below zeta (b - 1
-    would break the ratio); exceptions are exactly the ints above 2^b - 1;
+@pytest.mark.parametrize("tail_rows", [1, 5, 21, 31])
+def test_pfd_b_minimal_and_exceptions(k, zeta, seed, tail_rows):
+    """Section 6.2 Step 2: b is the minimum width whose exception rows keep
+    the frame's exception ratio below zeta (b - 1 would break it). A whole
+    frame's budget is the most rows c with c / 32 < zeta; a list's last frame
+    of r < 32 rows has that budget times r / 32, rounded down (so its own
+    ratio stays below zeta). Exceptions are exactly the ints above 2^b - 1;
     the exception width is the smallest of 8, 16, 32 bits that holds them."""
-    n = 32 * k * 6 + 17
+    n = 32 * k * 6 + (tail_rows - 1) * k + 3
     g = synth.mixed_runs(seed, n, 64, 8.0, 0.15, 1 << 20)
     c = O.Codec(O.PFD, k, zeta=zeta)
     ctrl, data = O.encode(c, g)
     R = (n + k - 1) // k
+    assert R % 32 == tail_rows
     nf = (R + 31) // 32
     mx = O.rowmax(g, k)
-    lim = Fraction(zeta).limit_denominator(10**9) * 32
+    z = Fraction(zeta).limit_denominator(10**9)
+    c32 = max(0, min(31, math.ceil(z * 32) - 1))  # the most rows c with c / 32 < zeta
+    assert Fraction(c32, 32) < z and (c32 == 31 or not Fraction(c32 + 1, 32) < z)
     for f, (b, wcode, e) in enumerate(_pfd_headers(ctrl, nf)):
         fm = mx[32 * f:32 * f + 32]
+        budget = c32 * len(fm) // 32
         cnt = lambda bb: sum(1 for m in fm if int(m) >= (1 << bb))
-        assert cnt(b) < lim
-        assert b == 0 or not cnt(b - 1) < lim
+        assert cnt(b) <= budget and Fraction(cnt(b), len(fm)) < z
+        assert b == 0 or cnt(b - 1) > budget
         vals = [int(v) for v in g[32 * k * f:32 * k * (f + 1)] if int(v) >= (1 << b)]
         assert e == len(vals)
         if e:
