@@ -772,7 +772,7 @@ __device__ __forceinline__ uint32_t line_bases(const DecodeArgs& a, WarpSmem<K>&
 // components each) in natural order. Group-PFD exceptions are patched into
 // the line-major buffer before the running sum. The pack's ring bytes are
 // given back (`empty`) once the data and control bytes are read.
-template <int KIND, bool RESTORE>
+template <int KIND, bool RESTORE, bool PER = false>
 __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4>& ws, const uint8_t* ring,
                              uint32_t s0, uint32_t np, uint32_t nl, unsigned long long* empty) {
   constexpr uint32_t RPL = Geo<4>::RPL;  // rows per line (8)
@@ -851,6 +851,10 @@ __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4
   const uint32_t upto = t.heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
   const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;    // its item among the decoded ones
   const uint32_t lhead = act ? 31u - __clz(upto) : 0u;            // the item's first line
+  // (per-record mode) a line of a GC_WORK_RAW record is written without the
+  // running sum; its total then counts 0, and the record's base is 0
+  bool sum = RESTORE;
+  if constexpr (PER) sum = !act || !(rec_of(h, rslot(ws.irec[rank])).shape & GC_WORK_RAW);
   uint32_t r[32];
   uint32_t R = 0;
 #pragma unroll
@@ -916,7 +920,7 @@ __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4
   // the pack's staged bytes are read: give its ring bytes back
   __syncwarp();
   if (lane == 0) mbar_arrive(empty);
-  if (RESTORE) {
+  if (sum) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       R += r[j];
@@ -1001,7 +1005,7 @@ __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4
 // em is set (Sec 6.2 decoding Step 3), before the running sum.
 template <int KIND, bool SUM, bool PATCH = false>
 __device__ __forceinline__ void extract_line32(const uint4* P, uint32_t sh, uint32_t msk, bool cross, uint4* T,
-                                               uint32_t swz, uint32_t& R, uint32_t em = 0) {
+                                               uint32_t swz, uint32_t& R, uint32_t em = 0, bool rsum = true) {
   R = 0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -1022,7 +1026,7 @@ __device__ __forceinline__ void extract_line32(const uint4* P, uint32_t sh, uint
         v3 = (m4 & 8u) ? x.w : v3;
       }
     }
-    if (SUM) {
+    if (SUM && rsum) {
       v0 += R;
       v1 += v0;
       v2 += v1;
@@ -1214,7 +1218,7 @@ __device__ __forceinline__ void pfd_patch_pack32(const DecodeArgs& a, uint32_t* 
 // of the line totals gives each line's base, which is added as the buffer
 // goes out in 16-byte chunks. The pack's ring bytes are given back
 // (`empty`) once they are read.
-template <int KIND, bool RESTORE>
+template <int KIND, bool RESTORE, bool PER = false>
 __device__ void decode_pack32(const DecodeArgs& a, const BlockSmem& h, WarpSmem<32>& ws, const uint8_t* ring,
                               uint32_t s0, uint32_t np, uint32_t nl, unsigned long long* empty) {
   const uint32_t lane = lane_id();
@@ -1267,6 +1271,10 @@ __device__ void decode_pack32(const DecodeArgs& a, const BlockSmem& h, WarpSmem<
   const uint32_t upto = t.heads & (0xffffffffu >> (31u - lane));  // item heads at lines <= l
   const uint32_t rank = act ? (uint32_t)__popc(upto) - 1u : 0u;    // its item among the decoded ones
   const uint32_t lhead = act ? 31u - __clz(upto) : 0u;            // the item's first line
+  // (per-record mode) a line of a GC_WORK_RAW record is written without the
+  // running sum; its total then counts 0, and the record's base is 0
+  bool sum = RESTORE;
+  if constexpr (PER) sum = !act || !(rec_of(h, rslot(ws.irec[rank])).shape & GC_WORK_RAW);
   uint32_t ent, sw;
   PfdExc px;
   if (KIND == GC_SIMPLE) {
@@ -1291,7 +1299,7 @@ __device__ void decode_pack32(const DecodeArgs& a, const BlockSmem& h, WarpSmem<
   const uint32_t swz = lane & 7u;
   uint32_t R = 0;
   if (KIND != GC_PFD) {
-    extract_line32<KIND, RESTORE>(P, sh, msk, cross, T, swz, R);
+    extract_line32<KIND, RESTORE>(P, sh, msk, cross, T, swz, R, 0u, sum);
   } else {
     // Group-PFD: when a tile of the pack has exceptions, they first go to
     // their places in the buffer and their columns to each line's mask;
@@ -1306,7 +1314,7 @@ __device__ void decode_pack32(const DecodeArgs& a, const BlockSmem& h, WarpSmem<
       __syncwarp();
       em = ws.emask[lane];
     }
-    extract_line32<KIND, RESTORE, true>(P, sh, msk, cross, T, swz, R, em);
+    extract_line32<KIND, RESTORE, true>(P, sh, msk, cross, T, swz, R, em, sum);
   }
   // the pack's staged bytes are read: give its ring bytes back
   __syncwarp();
@@ -1452,6 +1460,30 @@ __device__ __noinline__ uint2 claim_records(const DecodeArgs& a, BlockSmem& h, u
   return make_uint2(x, cnt);
 }
 
+// A plan with look-back records: the block's c-th claim is records
+// blockIdx.x + gridDim.x * (32 c + j), j = 0 .. 31 (the blocks take the
+// records in turn, so a tile's predecessor is decoded by the block before,
+// at about the same time), loaded by the lanes into record buffer b.
+// Returns the claim's first record and count (x, y; lane-uniform).
+__device__ __noinline__ uint2 claim_strided(const DecodeArgs& a, BlockSmem& h, uint32_t b, uint32_t c,
+                                            uint64_t total) {
+  const uint32_t lane = lane_id();
+  const uint64_t r = blockIdx.x + (uint64_t)gridDim.x * (32ull * c + lane);
+  const bool valid = r < total;
+  if (valid) {
+    const uint4* src = reinterpret_cast<const uint4*>(a.work + r);
+    uint4* dst = h.rec[b * kChunk + lane];
+    const uint4 q0 = src[0], q1 = src[1], q2 = src[2], q3 = src[3];
+    dst[0] = q0;
+    dst[1] = q1;
+    dst[2] = q2;
+    dst[3] = q3;
+  }
+  __syncwarp();
+  const uint32_t cnt = __popc(__ballot_sync(kFull, valid));
+  return make_uint2((uint32_t)(blockIdx.x + (uint64_t)gridDim.x * 32ull * c), cnt);
+}
+
 // Group the claim's records (lanes 0 .. cnt - 1) into packs: a pack is a run
 // of consecutive records whose lines fit 32, whose ring bytes fit kPackCap
 // and, at k = 4, whose data vectors fit the re-lay buffer; packs are formed
@@ -1461,11 +1493,9 @@ __device__ __noinline__ uint2 claim_records(const DecodeArgs& a, BlockSmem& h, u
 // from record 0 by following next, found by pointer doubling in five
 // rounds. v packs (lines | ring bytes / 16 << 11 | vectors << 32, the
 // vectors only at k = 4, whose sums then need 64 bits); returns the mask of
-// pack starts, P is each lane's inclusive sum of v and nxt its next_i. With
-// PER, a pack also never mixes records with and without GC_WORK_RAW (rawm:
-// one bit per record).
-template <int K, class U, bool PER = false>
-__device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_t& nxt, uint32_t rawm = 0) {
+// pack starts, P is each lane's inclusive sum of v and nxt its next_i.
+template <int K, class U>
+__device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_t& nxt) {
   const uint32_t lane = lane_id();
   P = warp_incl_sum(v);
   const U Pex = P - v;
@@ -1476,12 +1506,6 @@ __device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_
     const U s = __shfl_sync(kFull, P, j < 32 ? j : 31u) - Pex;
     bool fits = j < cnt && (uint32_t)(s & 2047u) <= 32u && (uint32_t)((s >> 11) & 0x1fffffu) * 16u <= (uint32_t)kPackCap;
     if constexpr (K == 4) fits = fits && (uint64_t)(s >> 32) <= (uint64_t)kPadVec4;
-    if constexpr (PER) {
-      // records lane .. j all raw or all not
-      const uint32_t jj = j < 31u ? j : 31u;
-      const uint32_t span = (jj == 31u ? 0xffffffffu : (2u << jj) - 1u) & ~((1u << lane) - 1u);
-      fits = fits && ((rawm & span) == 0u || (rawm & span) == span);
-    }
     if (fits) len += step;
   }
   nxt = lane < cnt ? lane + (len ? len : 1u) : 32u;
@@ -1506,21 +1530,22 @@ __device__ __forceinline__ uint32_t pack_starts(U v, uint32_t cnt, U& P, uint32_
 // pack its slot descriptor, then one arrival on the slot's mbarrier tells
 // its decoding warp, which copies the pack's bytes in itself. After the
 // last record, one empty pack per decoding warp tells it to stop.
-template <int KIND, int K, bool PER>
+template <int KIND, int K>
 __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t S) {
   const uint32_t lane = lane_id();
   uint64_t total = a.count[0];
   if (total > a.work_cap) total = a.work_cap;
-  // With tiles that take their prefix by look-back, records are claimed one
-  // at a time and only once the ones before are placed: a claimed record
-  // that waits in a block's queue holds back every later tile of its list,
-  // in other blocks, until a decoding warp publishes its aggregate.
+  // With tiles that take their prefix by look-back, the blocks take the
+  // records in turn (claim_strided) and a claim is made only once the one
+  // before is placed: a tile's predecessor is then decoded by another block
+  // at about the same time, so a decoding warp seldom waits for it.
   const bool ahead = a.count[1] == 0;
-  const uint32_t claim = !ahead ? 1u : a.claim < 1u ? 1u : a.claim > (uint32_t)kChunk ? (uint32_t)kChunk : a.claim;
+  const uint32_t claim = a.claim < 1u ? 1u : a.claim > (uint32_t)kChunk ? (uint32_t)kChunk : a.claim;
+  const uint32_t stride = ahead ? 1u : gridDim.x;  // between the records of a claim
   Ring r = {a.ring_bytes, 0, 0, 0, 0, 0, 0, 0};
   bool failed = false;
   uint32_t busy = 0;  // lane b < kNChunk: record buffer b is free once this many packs are given back
-  const uint2 c0 = claim_records(a, h, 0, claim, total);
+  const uint2 c0 = ahead ? claim_records(a, h, 0, claim, total) : claim_strided(a, h, 0, 0, total);
   uint32_t x = c0.x, cnt = c0.y;
   for (uint32_t c = 0; cnt && !failed; ++c) {
     const uint32_t b = c % kNChunk;
@@ -1535,7 +1560,7 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
       nx = cn.x;
       ncnt = cn.y;
     }
-    if (!wait_warp(&h.recbar[b], (c / kNChunk) & 1u)) {
+    if (ahead && !wait_warp(&h.recbar[b], (c / kNChunk) & 1u)) {
       failed = true;
       break;
     }
@@ -1544,7 +1569,7 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
     const uint32_t rs = b * kChunk + lane;
     uint32_t lines = 0, nv = 0, cb = 0, xb = 0;
     if (valid) {
-      h.item[rs] = x + lane;
+      h.item[rs] = x + lane * stride;
       stage_sizes<KIND, K>(rec_of(h, rs), a, lines, nv, cb, xb);
       h.fvecs[rs] = (uint16_t)nv;
       h.cst[rs] = (uint16_t)cb;
@@ -1556,9 +1581,7 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
     const U v = valid ? (U)lines | (U)need16 << 11 | (K == 4 ? (U)((uint64_t)nv << 32) : (U)0) : (U)0;
     U P;
     uint32_t nxt;
-    uint32_t rawm = 0;
-    if constexpr (PER) rawm = __ballot_sync(kFull, valid && (rec_of(h, rs).shape & GC_WORK_RAW));
-    const uint32_t starts = pack_starts<K, U, PER>(v, cnt, P, nxt, rawm);
+    const uint32_t starts = pack_starts<K, U>(v, cnt, P, nxt);
     const U Pex = P - v;
     // each record's offset from its pack's start; at a pack's first record,
     // the pack's ring bytes / 16, records and lines
@@ -1594,7 +1617,7 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
       }
       if (failed) break;
       if (lane == 0) {
-        h.pk[r.ps] = (b * kChunk + sp) | ((pi >> 16) & 255u) << 8 | (pi >> 24) << 16 | ((rawm >> sp) & 1u) << 24;
+        h.pk[r.ps] = (b * kChunk + sp) | ((pi >> 16) & 255u) << 8 | (pi >> 24) << 16;
         h.prel[r.ps] = pad + B;
         h.ppos[r.ps] = off;
         mbar_arrive(&h.full[r.ps]);
@@ -1609,7 +1632,7 @@ __device__ void produce(const DecodeArgs& a, BlockSmem& h, uint32_t W, uint32_t 
       const uint32_t nbusy = __shfl_sync(kFull, busy, nb);
       while (!failed && r.tail < nbusy) failed = !ring_drain(h, r, S);
       if (failed) break;
-      const uint2 cn = claim_records(a, h, nb, claim, total);
+      const uint2 cn = claim_strided(a, h, nb, c + 1, total);
       nx = cn.x;
       ncnt = cn.y;
     }
@@ -1731,15 +1754,10 @@ __device__ void consume(const DecodeArgs& a, BlockSmem& h, WarpSmem<K>& ws, uint
     __syncwarp();
     const uint32_t s0 = d & 255u, np = (d >> 8) & 255u;
     if constexpr (PER) {
-      // a pack of raw records (bit 24) decodes without the prefix sum
-      const uint32_t nl = (d >> 16) & 255u;
-      if ((d >> 24) & 1u) {
-        if constexpr (K == 32) decode_pack32<KIND, false>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
-        else decode_pack4<KIND, false>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
-      } else {
-        if constexpr (K == 32) decode_pack32<KIND, true>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
-        else decode_pack4<KIND, true>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
-      }
+      // GC_WORK_RAW records' lines decode without the prefix sum
+      const uint32_t nl = d >> 16;
+      if constexpr (K == 32) decode_pack32<KIND, true, true>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
+      else decode_pack4<KIND, true, true>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
     } else {
       const uint32_t nl = d >> 16;
       if constexpr (K == 32) decode_pack32<KIND, RESTORE>(a, h, ws, ring, s0, np, nl, &h.empty[slot]);
@@ -1784,7 +1802,7 @@ __global__ void __launch_bounds__(Geo<K>::THREADS, 1) k_decode(DecodeArgs a) {
     fence_mbar_init();
   }
   __syncthreads();
-  if (warp == 0) produce<KIND, K, PER>(a, h, W, S);
+  if (warp == 0) produce<KIND, K>(a, h, W, S);
   else consume<KIND, K, RESTORE, PER>(a, h, ws[warp - 1], ring, warp - 1, W, S);
 }
 
@@ -1990,10 +2008,11 @@ __global__ void k_plan_fill(PlanArgs a) {
     a.work[i] = empty;
     return;
   }
-  // an interleaved plan: odd entries are written raw; an even entry's tiles
-  // are not consecutive records, so each one after the first needs its base
+  // an interleaved plan: odd entries are written raw (with base 0: their
+  // lines' totals count 0); an even entry's tiles are not consecutive
+  // records, so each one after the first needs its base
   const bool raw = a.pairs && (w.list & 1u);
-  const bool has_base = (r0.flags & GC_TILE_BASE) != 0 && !raw;
+  const bool has_base = raw || (r0.flags & GC_TILE_BASE) != 0;
   const bool publish = !a.pairs && !last && !(r1.flags & GC_TILE_BASE);
   if (a.pairs && !raw && t > 0 && !has_base) {
     report(a.status, GC_ERR_UNSUPPORTED, a.sel ? a.sel[w.list] : w.list);
@@ -2010,7 +2029,7 @@ __global__ void k_plan_fill(PlanArgs a) {
   w.out_at = d.out_off + t * kTileInts;
   w.ctrl_bit = r0.ctrl_bit;
   w.ctrl_bytes = (uint32_t)cbytes;
-  w.base = has_base ? r0.base : 0;
+  w.base = has_base && !raw ? r0.base : 0;
   w.exc_at = (uint32_t)xs;
   w.win_at = (int32_t)((int64_t)wlo - (int64_t)d.ctrl_off);
   w.win_len = (uint16_t)min64(whi - wlo, 0xfff0);
