@@ -41,14 +41,20 @@ if ROOT not in sys.path:
 
 UNIVERSE = 25_000_000
 CODECS = {"simple": (0, "Group-Simple"), "pfd": (3, "Group-PFD")}
-# DRAM traffic (read + write) of one decode launch per algorithmic byte,
-# measured by ncu on the small Zipf index (100,000 lists, C = 3.0406e7, 1.8e8
-# docIDs), with the hash of the kernel sources it was taken on. The full-size
-# launch's traffic is reported as this ratio times its algorithmic bytes (the
-# decoder reads and writes each byte once, so traffic grows in proportion);
-# once the sources change, null. Multi-metric captures of the full-size
-# workload are not taken.
-NCU_TRAFFIC_RATIO = {}
+# DRAM traffic of one decode launch per algorithmic byte, reads (of the
+# compressed streams and the plan) and writes (of the docIDs) apart, measured
+# by ncu (dram__bytes_read.sum, dram__bytes_write.sum) on the small Zipf
+# index (100,000 lists, C = 3.0406e7, 1.8e8 docIDs), with the hash of the
+# kernel sources it was taken on. The full-size launch's traffic is reported
+# as these ratios times its own algorithmic reads and writes (the decoder
+# reads and writes each byte once, so traffic grows in proportion); once the
+# sources change, null. The small launch ends with about 57 MB of its
+# 725 MB of docIDs still in L2, so its write ratio is low by that much.
+# Multi-metric captures of the full-size workload are not taken.
+NCU_TRAFFIC_RATIO = {
+    "simple": {"read": 350874880 / 348266713, "write": 667677952 / 724566460, "hash": "3194e45552628068"},
+    "pfd": {"read": 283171840 / 280634604, "write": 666430208 / 724566460, "hash": "3194e45552628068"},
+}
 
 
 def parse():
@@ -428,9 +434,11 @@ def main():
     ratio = NCU_TRAFFIC_RATIO.get(dom)
     traffic, traffic_source = None, "none: no ncu capture of these kernel sources"
     if ratio and ratio.get("hash") == kh and a.k == 32 and a.zeta == 0.10:
-        traffic = ratio["ratio"] * per_codec[dom]["algorithmic_bytes"]
-        traffic_source = ("ncu dram__bytes_read.sum + dram__bytes_write.sum on the 1.8e8-docID Zipf index, "
-                          f"{ratio['ratio']:.4f} of its algorithmic bytes, scaled to this launch's")
+        wr = 4 * total_ints
+        traffic = ratio["read"] * (per_codec[dom]["algorithmic_bytes"] - wr) + ratio["write"] * wr
+        traffic_source = ("ncu dram__bytes_read.sum and dram__bytes_write.sum on the 1.8e8-docID Zipf index: "
+                          f"{ratio['read']:.4f} of its algorithmic reads, {ratio['write']:.4f} of its writes "
+                          "(the last ~57 MB of docIDs still in L2 when that launch ends), scaled to this launch's")
     roofline = {"bound": "hbm", "kernel": f"k_decode<{CODECS[dom][1]}, k={a.k}, batched>",
                 "bytes_per_launch": per_codec[dom]["algorithmic_bytes"],
                 "achieved": per_codec[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
