@@ -762,6 +762,75 @@ __device__ __forceinline__ uint32_t line_bases(const DecodeArgs& a, WarpSmem<K>&
                              t.item, t.list, t.rank);
 }
 
+// Group-PFD at k = 4 (Sec 6.2 decoding Step 1, pack-wide): line l of the
+// pack is rows 8 q .. 8 q + 7 of its tile (q = l - its tile's first line),
+// which lie in frame q / 4 (a frame is 32 rows, a tile 8 whole frames).
+// Every line reads its frame's header; one scan of 32 b over the lines that
+// begin a frame, less the scan before the tile's first line, gives where
+// each frame's rows start in the tile's lane streams, so row r of the frame
+// is at that start + r b. A malformed header, an exception record past the
+// control area or rows past the staged vectors are reported. Returns
+// whether a frame of the pack has exceptions.
+struct Pfd4Line {
+  uint32_t rb0;    // lane bit of the line's first row (from the tile's first staged word)
+  uint32_t b;      // its frame's width
+  uint32_t v0;     // the tile's first vector in the pack's re-laid buffer
+  uint32_t q0;     // the line's first row in the tile
+  uint32_t rows;   // rows of the tile
+  uint32_t vbits;  // 32 * the tile's staged vectors
+};
+
+__device__ __forceinline__ bool pfd_line4(const DecodeArgs& a, const BlockSmem& h, const WarpSmem<4>& ws,
+                                          const uint8_t* ring, const Items& t, uint32_t s0, bool act,
+                                          uint32_t lane, uint32_t rank, uint32_t lhead, Pfd4Line& pl) {
+  const uint32_t sp = rslot(ws.irec[act ? rank : 0u]);
+  const gc_work& w = rec_of(h, sp);
+  const uint32_t vecs = h.fvecs[sp];
+  const uint32_t lq = act ? lane - lhead : 0u;  // line in the tile
+  const uint32_t f = lq >> 2;                    // frame in the tile
+  const uint32_t rows = (w_nint(w.shape) + 3) / 4;
+  const uint32_t at = h.at[sp];
+  CtrlView C;
+  C.g = a.ctrl_pool + w.ctrl_at;
+  C.size = w.ctrl_bytes;
+  C.s1 = ring + at + vecs * 16;
+  C.lo1 = w.win_at;
+  C.len1 = h.cst[sp];
+  C.s2 = C.s1 + h.cst[sp];
+  C.lo2 = (int64_t)((w.ctrl_at + w.exc_at) & ~15ull) - (int64_t)w.ctrl_at;
+  C.len2 = h.xst[sp];
+  const uint64_t hp = 4ull * ((uint64_t)w.tile * (Geo<4>::TR / kPfdFrameRows) + f);
+  bool ok = hp + 4 <= C.size;
+  const uint32_t hdr = act && ok ? C.le4(hp) : 0u;
+  uint32_t b = hdr & 63u, wcode = (hdr >> 6) & 3u, e = hdr >> 8;
+  const uint32_t frows = rows > 32u * f ? min(32u, rows - 32u * f) : 0u;
+  if (b > 32 || wcode > 2 || e > frows * 4) {
+    ok = false;
+    b = 0;
+    e = 0;
+  }
+  const bool fh = act && (lq & 3u) == 0;  // the line begins its frame
+  const uint32_t Vb = warp_incl_sum(fh ? 32u * b : 0u);
+  const uint32_t xb = fh ? e * (1u + (1u << wcode)) : 0u;
+  const uint32_t Vx = warp_incl_sum(xb);
+  const uint32_t fl = lhead + 4 * f;  // the frame's first line
+  const uint32_t bF = __shfl_sync(kFull, Vb, (fl - 1u) & 31u), bT = __shfl_sync(kFull, Vb, (lhead - 1u) & 31u);
+  const uint32_t xF = __shfl_sync(kFull, Vx, (fl - 1u) & 31u), xT = __shfl_sync(kFull, Vx, (lhead - 1u) & 31u);
+  const uint32_t start = (fl ? bF : 0u) - (lhead ? bT : 0u);  // the frame's first lane bit in the tile
+  if (fh && xb && w.exc_at + (uint64_t)((fl ? xF : 0u) - (lhead ? xT : 0u)) + xb > C.size) ok = false;
+  pl.q0 = 8 * lq;
+  pl.rows = rows;
+  pl.b = b;
+  pl.rb0 = w_bit0(w.shape) + start + 8 * (lq & 3u) * b;
+  pl.vbits = 32 * vecs;
+  pl.v0 = __shfl_sync(kFull, t.vec0, (sp - s0) & 31u);
+  // rows that lie past the staged vectors
+  const uint32_t nr = act && pl.q0 < rows ? min(8u, rows - pl.q0) : 0u;
+  if (nr && pl.rb0 + nr * b > pl.vbits) ok = false;
+  if (act && !ok) report(a.status, GC_ERR_CORRUPT, w.list);
+  return __any_sync(kFull, act && e != 0);
+}
+
 // The k = 4 pack decoder (the paper's own layout): records s0 .. s0 + np - 1
 // of the block (staged, the pack's mbarrier complete), `nl` lines in all.
 // Each staged tile's 16-byte vectors are re-laid in the warp's buffer,
@@ -805,6 +874,7 @@ __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4
         d[3] = x.w;
       }
     }
+    if constexpr (KIND == GC_PFD) continue;  // (its rows come from the frame headers in step 2)
     const uint32_t dbytes = vecs * 16;
     CtrlView C;
     C.g = a.ctrl_pool + w.ctrl_at;
@@ -833,9 +903,7 @@ __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4
     } else if (KIND == GC_AFOR) {
       ok = parse_afor<4>(C, w.ctrl_bit, w_skip(w.shape), rows, out);
     } else {
-      bool x;
-      ok = parse_pfd4(C, row0 / kPfdFrameRows, w.exc_at, rows, out, x);
-      exc |= x;
+      ok = true;
     }
     // rows of the last line past the tile's end read nothing
     if (lane < lines * RPL - rows) {
@@ -855,13 +923,24 @@ __device__ void decode_pack4(const DecodeArgs& a, const BlockSmem& h, WarpSmem<4
   // running sum; its total then counts 0, and the record's base is 0
   bool sum = RESTORE;
   if constexpr (PER) sum = !act || !(rec_of(h, rslot(ws.irec[rank])).shape & GC_WORK_RAW);
+  // Group-PFD: the line's rows straight from its frame's header
+  Pfd4Line pl;
+  if constexpr (KIND == GC_PFD) exc = pfd_line4(a, h, ws, ring, t, s0, act, lane, rank, lhead, pl);
   uint32_t r[32];
   uint32_t R = 0;
 #pragma unroll
   for (int rr = 0; rr < (int)RPL; ++rr) {
-    const uint32_t row = act ? lane * RPL + rr : 0u;
-    const uint32_t vi = act ? ws.rw[row] : 0u;
-    const uint32_t sw = act ? ws.rs[row] : 0u;
+    uint32_t vi, sw;
+    if constexpr (KIND == GC_PFD) {
+      const uint32_t rb = pl.rb0 + (uint32_t)rr * pl.b;
+      const bool live = act && pl.q0 + (uint32_t)rr < pl.rows && rb + pl.b <= pl.vbits;
+      vi = pl.v0 + (live ? rb >> 5 : 0u);
+      sw = live ? (rb & 31u) | (pl.b << 8) : 0u;
+    } else {
+      const uint32_t row = act ? lane * RPL + rr : 0u;
+      vi = act ? ws.rw[row] : 0u;
+      sw = act ? ws.rs[row] : 0u;
+    }
     const uint32_t sh = sw & 31u, wd = sw >> 8;
     const uint32_t msk = low_mask(wd);
     const bool cross = sh + wd > 32;
