@@ -474,57 +474,12 @@ __device__ __forceinline__ bool parse_afor(const CtrlView& C, uint64_t ctrl_bit,
   return __all_sync(kFull, ok);
 }
 
-// Group-PFD at k = 4, decoding Step 1: per 32-row frame (128 ints) the
-// header (b, exception width code, exception count e); the tile's frames'
-// exception records follow one another from exc_at (e 8-bit positions, then
-// e values of wb bytes). Rows go to the sink; every header and record is
-// checked to lie inside the list (the exceptions themselves are patched in
-// after the rows are decoded, pfd_patch4).
-__device__ __forceinline__ bool parse_pfd4(const CtrlView& C, uint64_t f0, uint64_t exc_at, uint32_t rows,
-                                           const RowSink<4>& out, bool& exc) {
-  const uint32_t lane = lane_id();
-  const uint32_t nfr = (rows + kPfdFrameRows - 1) / kPfdFrameRows;
-  bool ok = true;
-  uint32_t b = 0, xb = 0;
-  if (lane < nfr) {
-    const uint64_t f = f0 + lane;
-    if (4 * f + 4 > C.size) ok = false;
-    const uint32_t hdr = ok ? C.le(4 * f, 4) : 0u;
-    b = hdr & 63u;
-    const uint32_t wcode = (hdr >> 6) & 3u;
-    uint32_t e = hdr >> 8;
-    if (b > 32 || wcode > 2) {
-      ok = false;
-      b = 0;
-      e = 0;
-    }
-    const uint32_t frows = rows - 32 * lane < 32 ? rows - 32 * lane : 32;
-    if (e > frows * 4) {
-      ok = false;
-      e = 0;
-    }
-    xb = e * (1u + (1u << wcode));
-  }
-  const uint64_t xrec0 = exc_at + (warp_incl_sum(xb) - xb);
-  if (lane < nfr && xb && xrec0 + xb > C.size) ok = false;
-  exc = __any_sync(kFull, xb != 0);
-  const uint32_t inclL = warp_incl_sum(32u * b);
-  const uint32_t lstart = inclL - 32u * b;
-  for (uint32_t fl = 0; fl < nfr; ++fl) {
-    const uint32_t bf = __shfl_sync(kFull, b, fl);
-    const uint32_t ls = __shfl_sync(kFull, lstart, fl);
-    const uint32_t q = fl * 32 + lane;
-    if (q < rows) out.put(q, ls + lane * bf, bf, ok);
-  }
-  return __all_sync(kFull, ok);
-}
-
 // Group-PFD at k = 4, decoding Step 3: every exception of a tile's frames
 // overwrites its slot in the pack's line-major buffer (line l at words
 // 32 l .., 16-byte chunk c at chunk c ^ (l & 7)); the tile's first line is
-// line0. Headers and records were checked by parse_pfd4; a position
-// outside its frame, or one that does not increase on the one before, is
-// reported.
+// line0. Headers and records were checked by pfd_line4; a position outside
+// its frame, or one that does not increase on the one before, is reported
+// (and not patched).
 __device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, uint32_t* tb, const CtrlView& C, uint64_t f0,
                                            uint64_t exc_at, uint32_t rows, uint32_t line0, uint32_t list) {
   const uint32_t lane = lane_id();
@@ -543,28 +498,36 @@ __device__ __forceinline__ void pfd_patch4(const DecodeArgs& a, uint32_t* tb, co
   }
   const uint64_t rec = exc_at + (warp_incl_sum(xb) - xb);
   if (lane < nfr && xb && rec + xb > C.size) e = 0;
-  for (uint32_t fl = 0; fl < nfr; ++fl) {
-    const uint32_t ef = __shfl_sync(kFull, e, fl);
-    if (ef == 0) continue;
-    const uint32_t wbf = __shfl_sync(kFull, wb, fl);
-    const uint32_t limf = __shfl_sync(kFull, lim, fl);
+  // the tile's exceptions, numbered frame after frame, 32 at a time: a
+  // lane's frame is the first whose running count passes its number
+  const uint32_t Ei = warp_incl_sum(lane < nfr ? e : 0u);
+  const uint32_t E = __shfl_sync(kFull, Ei, 31);
+#pragma unroll 1
+  for (uint32_t x0 = 0; x0 < E; x0 += 32) {
+    const uint32_t xg = x0 + lane;
+    uint32_t fl = 0;
+#pragma unroll
+    for (uint32_t step = 4; step; step >>= 1)  // (a tile has at most 8 frames)
+      if (__shfl_sync(kFull, Ei, fl + step - 1) <= xg) fl += step;
+    fl &= 7u;
+    const uint32_t ef = __shfl_sync(kFull, e, fl), wbf = __shfl_sync(kFull, wb, fl);
+    const uint32_t limf = __shfl_sync(kFull, lim, fl), ei = __shfl_sync(kFull, Ei, fl);
     const uint64_t rf = __shfl_sync(kFull, rec, fl);
+    if (xg >= E) continue;
+    const uint32_t x = xg - (ei - ef);  // its number in its frame
     const uint8_t* rp = C.addr(rf, (uint64_t)ef * (1 + wbf));
-    const uint8_t* vp = rp + ef;
-    for (uint32_t x = lane; x < ef; x += 32) {
-      const uint32_t pos = rp[x];
-      if (pos >= limf || (x && rp[x - 1] >= pos)) {
-        report(a.status, GC_ERR_CORRUPT, list);
-        continue;
-      }
-      const uint8_t* v8 = vp + (size_t)x * wbf;
-      uint32_t v = v8[0];
-      if (wbf > 1) v |= (uint32_t)v8[1] << 8;
-      if (wbf > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
-      const uint32_t i = fl * 128 + pos;  // int of the tile
-      const uint32_t line = line0 + (i >> 5), col = i & 31u;
-      tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
+    const uint32_t pos = rp[x];
+    if (pos >= limf || (x && rp[x - 1] >= pos)) {
+      report(a.status, GC_ERR_CORRUPT, list);
+      continue;
     }
+    const uint8_t* v8 = rp + ef + (size_t)x * wbf;
+    uint32_t v = v8[0];
+    if (wbf > 1) v |= (uint32_t)v8[1] << 8;
+    if (wbf > 2) v |= ((uint32_t)v8[2] << 16) | ((uint32_t)v8[3] << 24);
+    const uint32_t i = fl * 128 + pos;  // int of the tile
+    const uint32_t line = line0 + (i >> 5), col = i & 31u;
+    tb[line * 32 + ((4u * (col >> 2)) ^ (4u * (line & 7u))) + (col & 3u)] = v;
   }
 }
 // ------------------------------------------------------------ look-back
