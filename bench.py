@@ -52,8 +52,8 @@ CODECS = {"simple": (0, "Group-Simple"), "pfd": (3, "Group-PFD")}
 # 725 MB of docIDs still in L2, so its write ratio is low by that much.
 # Multi-metric captures of the full-size workload are not taken.
 NCU_TRAFFIC_RATIO = {
-    "simple": {"read": 350874880 / 348266713, "write": 667677952 / 724566460, "hash": "3194e45552628068"},
-    "pfd": {"read": 283171840 / 280634604, "write": 666430208 / 724566460, "hash": "3194e45552628068"},
+    "simple": {"read": 350758912 / 348266713, "write": 668499456 / 724566460, "hash": "b7fafb21786a88f5"},
+    "pfd": {"read": 283119360 / 280634604, "write": 665709056 / 724566460, "hash": "b7fafb21786a88f5"},
 }
 
 
