@@ -143,9 +143,13 @@ def choose_k(kind: int, d_gaps, lengths, out_offsets=None, restore_docids: bool 
                    "shape": [launch.warps_per_block, launch.blocks_per_sm, launch.items_per_claim,
                              launch.stage_bytes]}
         del idx, plan
+    return pick_k(by_k), by_k
+
+
+def pick_k(by_k: dict) -> int:
+    """The k of the faster decode ({k: {"ms", "bits_per_int"}} for k = 4
+    and 32); within 1% of each other, the smaller index."""
     a, b = by_k[4], by_k[32]
     if abs(a["ms"] - b["ms"]) <= 0.01 * min(a["ms"], b["ms"]):
-        best = 4 if a["bits_per_int"] <= b["bits_per_int"] else 32
-    else:
-        best = 4 if a["ms"] < b["ms"] else 32
-    return best, by_k
+        return 4 if a["bits_per_int"] <= b["bits_per_int"] else 32
+    return 4 if a["ms"] < b["ms"] else 32

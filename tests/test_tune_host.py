@@ -1,10 +1,11 @@
-"""Autotuner host logic (no GPU): workload classes and the JSON cache."""
+"""Autotuner host logic (no GPU): workload classes, the JSON cache, the k choice rule and the candidate shapes."""
 import json
 
 import numpy as np
 
 from paper_1502_01916_gb300 import make_codec, SIMPLE
-from paper_1502_01916_gb300.tune import cache_key, load_cache, save_cache, workload_class
+from paper_1502_01916_gb300.tune import (CANDIDATES, cache_key, candidates_for, load_cache, pick_k, save_cache,
+                                         workload_class)
 
 
 def test_workload_classes():
@@ -24,3 +25,27 @@ def test_cache_round_trip(tmp_path):
     with open(path, "w") as f:
         f.write("not json")
     assert load_cache(path) == {}
+
+
+def test_pick_k_prefers_speed_then_size():
+    fast4 = {4: {"ms": 1.0, "bits_per_int": 14.0}, 32: {"ms": 2.0, "bits_per_int": 12.0}}
+    assert pick_k(fast4) == 4
+    fast32 = {4: {"ms": 2.0, "bits_per_int": 11.0}, 32: {"ms": 1.7, "bits_per_int": 12.0}}
+    assert pick_k(fast32) == 32
+    tie = {4: {"ms": 1.000, "bits_per_int": 11.0}, 32: {"ms": 1.005, "bits_per_int": 12.0}}
+    assert pick_k(tie) == 4  # within 1%: the smaller index
+    tie32 = {4: {"ms": 1.005, "bits_per_int": 13.0}, 32: {"ms": 1.000, "bits_per_int": 12.0}}
+    assert pick_k(tie32) == 32
+
+
+def test_candidate_shapes_are_in_range():
+    """Every candidate is a valid launch shape for its k (gc.h: 1..23 decoding
+    warps at k = 32, 1..15 at k = 4; 1..8 blocks per SM; 1..32 records per
+    claim; a ring of 0 (all that fits) or at least 12 KB), and the library
+    default is among them."""
+    for k, limit in ((32, 23), (4, 15)):
+        shapes = candidates_for(k)
+        assert shapes is CANDIDATES[k] and len(set(shapes)) == len(shapes)
+        for w, b, c, st in shapes:
+            assert 1 <= w <= limit and 1 <= b <= 8 and 1 <= c <= 32 and (st == 0 or st >= 12288)
+    assert (7, 3, 32, 0) in candidates_for(32) and (7, 2, 32, 0) in candidates_for(4)
