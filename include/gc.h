@@ -187,9 +187,11 @@ enum {
  *     block takes 1/blocks_per_sm of the SM's shared memory.
  *   items_per_claim: 1..32 plan records a block takes from the shared
  *     counter per atomic (default 32). A plan with records that take their
- *     prefix by look-back (its count[1] > 0) is claimed one record at a
- *     time whatever this says: a record queued in one block would hold back
- *     the later tiles of its list in the others.
+ *     prefix by look-back (its count[1] > 0) is dealt to the blocks in turn
+ *     instead (block b takes records b, b + G, b + 2G, ... of a grid of G
+ *     blocks), whatever this says: records claimed from the counter and
+ *     queued in one block would hold back the later tiles of their lists in
+ *     the others.
  *   stage_bytes: bytes of the block's staging ring (the staging depth:
  *     how much compressed data is in flight per block); 0 = all the
  *     shared memory the block's share leaves. A shape whose ring would be
