@@ -188,3 +188,40 @@ def test_binding_refuses_buffers_of_the_wrong_kind(gc):
     from paper_1502_01916_gb300 import gc as binding
     with pytest.raises(ValueError):
         binding._n(torch.zeros(4, dtype=torch.int64), 4, "d_out")
+
+
+def test_service_calls_validate_on_the_host(gc):
+    """The boundary's service calls refuse bad arguments before any device
+    call: a launch shape out of range, a misaligned or short paper buffer, a
+    head-less buffer, a misaligned host-decode buffer or one too small."""
+    lib = gc.load()
+    c = gc.make_codec(gc.PFD, 32)
+    for bad in (gc.gc_launch(24, 1, 1), gc.gc_launch(1, 9, 1), gc.gc_launch(1, 1, 33)):
+        assert lib.gc_set_launch(ctypes.byref(c), 1, ctypes.byref(bad)) == 1
+    buf = (ctypes.c_uint8 * 256)()
+    base = (ctypes.addressof(buf) + 15) // 16 * 16
+    # paper buffer: misaligned, then too small for head + 20 control bytes + 8 words
+    assert lib.gc_pack_paper(base, 20, base, 8, base + 4, 200, None) == 1
+    assert lib.gc_pack_paper(base, 20, base, 8, base, gc.gc_paper_bytes(20, 8) - 1, None) == 2
+    cb, dw = ctypes.c_uint64(), ctypes.c_uint64()
+    assert lib.gc_unpack_paper(base, 3, base, 16, base, 4, ctypes.byref(cb), ctypes.byref(dw), None) == 1
+    # host-buffer decode: NULL device buffer, misaligned one, one smaller than it needs
+    need = gc.gc_decode_plan_host_buffer_size(10, 64, 64, 1000)
+    assert need >= 10 * gc.WORK_BYTES + 64 + 4 * 64 + 4 * 1000
+    args = (ctypes.byref(c), base, 10, base, 64, base, 64, base, 1000, 1, None)
+    assert lib.gc_decode_plan_host(*args, None, need, None, None) == 1
+    assert lib.gc_decode_plan_host(*args, base + 16, need, None, None) == 1
+    assert lib.gc_decode_plan_host(*args, (base + 255) // 256 * 256, need - 1, None, None) == 2
+    # nothing to decode is a no-op
+    assert lib.gc_decode_plan_host(ctypes.byref(c), None, 0, None, 0, None, 0, None, 0, 1, None, None, 0, None,
+                                   None) == 0
+
+
+def test_interleaved_plan_validates_on_the_host(gc):
+    lib = gc.load()
+    c = gc.make_codec(gc.SIMPLE, 32)
+    cnt = (ctypes.c_uint64 * 2)()
+    # pairs without selection arrays
+    assert lib.gc_plan_interleave(ctypes.byref(c), 1, 4, None, None, 2, None, 0, None, 0, 1, 8,
+                                  ctypes.byref(cnt), None, None) == 1
+    assert gc.RESTORE_PER_RECORD == 2 and gc.WORK_RAW == 1 << 31
