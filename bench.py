@@ -293,7 +293,14 @@ def main():
     import torch.distributed as dist
 
     from paper_1502_01916_gb300 import build as gcbuild
-    gcbuild.build()
+    if local == 0:
+        gcbuild.build()
+    else:
+        # the other ranks of this node load what local rank 0 builds (two
+        # builds at once would write the same object files)
+        deadline = time.time() + 900
+        while not os.path.exists(gcbuild.LIB) and time.time() < deadline:
+            time.sleep(1.0)
     import paper_1502_01916_gb300 as gc
 
     torch.cuda.set_device(local)
